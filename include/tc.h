@@ -1,0 +1,233 @@
+/*
+ * tc.h -- C ABI of libtc, a GB300 (sm_103a) library for the unitary evolution
+ * of a Tavis-Cummings cavity-QED system (arXiv 2403.06937, "Distributed
+ * computing quantum unitary evolution").
+ *
+ * The library computes, on one GPU:
+ *   H  -- the dense Hamiltonian of Eq. 4 on the basis of Eq. 2;
+ *   U  -- e^{-iH dt} by a scaled Taylor polynomial (Eqs. 6-8, 10), dense FP64;
+ *   rho <- U rho U^dag step after step (Eqs. 6 and 12), on FP64 DMMA or on
+ *          tcgen05 tensor cores in split-BF16 / TF32 arithmetic;
+ *   observables read from rho by reduction (populations, the photon-number
+ *          probabilities of Eq. 13, trace, purity, energy);
+ *   the gradient of a diagonal observable at the final time with respect to
+ *          the couplings and frequencies (reverse mode through Eq. 6).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - n atoms, N = 2^n (Eq. 2).  Basis index s: atom i (1-based) is bit (n-i)
+ *    of s (atom 1 = most significant bit).  Photon number p(s) = n - popcount(s)
+ *    (closed system, Sec. II).  hbar = 1.
+ *  - Matrices are row-major.  "c128" means interleaved complex double
+ *    (re, im), the layout of std::complex<double> and torch.complex128.
+ *  - Device pointers are owned by the caller; the library never frees or
+ *    keeps them after the call returns.  No call allocates device memory:
+ *    scratch space is the caller's `work` buffer, sized by tc_workspace_size
+ *    and aligned to 256 bytes.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Every call is stream-ordered and returns once its work is
+ *    enqueued; host arguments (tc_params and its g array) are read before the
+ *    call returns.
+ *  - Errors: every call returns a tc_status.  TC_OK means the work was
+ *    enqueued.  Argument and device errors are detected before any launch and
+ *    leave the outputs untouched.  Device-side conditions (non-finite trace,
+ *    timeouts of bounded waits) are recorded in a device status word and
+ *    reported by tc_sync_status.  tc_last_error() gives a message for the
+ *    last non-OK status of the calling thread.
+ *  - There is no CPU fallback: without an sm_103 device every compute call
+ *    returns TC_ERR_UNSUPPORTED_DEVICE.
+ */
+#ifndef TC_H_
+#define TC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define TC_API __attribute__((visibility("default")))
+#else
+#define TC_API
+#endif
+
+typedef enum tc_status {
+    TC_OK = 0,
+    TC_ERR_INVALID_ARG = 1,         /* bad size, null pointer, unknown enum   */
+    TC_ERR_UNSUPPORTED_DEVICE = 2,  /* current device is not sm_103           */
+    TC_ERR_WORKSPACE = 3,           /* work buffer missing, short or misaligned */
+    TC_ERR_CUDA = 4,                /* a CUDA runtime call failed             */
+    TC_ERR_TIMEOUT = 5,             /* a bounded device wait gave up          */
+    TC_ERR_NUMERIC = 6              /* non-finite or non-positive trace       */
+} tc_status;
+
+/* Arithmetic of the rho <- U rho U^dag products (the tensor-core path).
+ *  TC_FP64   : FP64 DMMA (mma.sync .f64), rho stored in FP64.
+ *  TC_BF16X3 : each FP32 operand split in three BF16 parts, six BF16 products
+ *              accumulated in FP32 in tensor memory (tcgen05 kind::f16).
+ *  TC_TF32   : one TF32 product, FP32 accumulate (tcgen05 kind::tf32).
+ *  TC_TF32X3 : big/small TF32 split, three products (kind::tf32).
+ * In all low-precision forms U is computed in FP64 and rho is stored in FP32
+ * between steps. */
+typedef enum tc_precision {
+    TC_FP64 = 0,
+    TC_BF16X3 = 1,
+    TC_TF32 = 2,
+    TC_TF32X3 = 3
+} tc_precision;
+
+/* Coupling matrix element between s_e (atom i excited, p photons) and s_g
+ * (atom i relaxed, p + 1 photons).
+ *  TC_COUPLING_BOSONIC      : g_i sqrt(p(s_e) + 1), one bosonic cavity mode
+ *                             (Eq. 4, a^dag |p> = sqrt(p+1) |p+1>).
+ *  TC_COUPLING_QUBIT_PHOTON : g_i, the reading of Eq. 1 in which each atom
+ *                             owns one photon qubit. */
+typedef enum tc_coupling {
+    TC_COUPLING_BOSONIC = 0,
+    TC_COUPLING_QUBIT_PHOTON = 1
+} tc_coupling;
+
+/* Model parameters of Eq. 4.  g points to n host doubles (g_1..g_n). */
+typedef struct tc_params {
+    int n;              /* 1 <= n <= 16 */
+    const double* g;    /* host, n values */
+    double omega_a;     /* atomic transition frequency */
+    double omega_c;     /* cavity frequency */
+    int coupling;       /* tc_coupling */
+} tc_params;
+
+/* Taylor plan of tc_expm.  The paper's Eq. 10 is {10, 0, 0}. */
+typedef struct tc_expm_opts {
+    int taylor_degree;  /* 0 = smallest degree meeting FP64 accuracy; else 1..30 */
+    int squarings;      /* -1 = chosen with the degree; else 0..40 */
+    int shift;          /* 1 = subtract the mean diagonal before the series */
+} tc_expm_opts;
+
+/* Observable row written per time point, TC_OBS_STRIDE(n) doubles:
+ *  [0 .. n-1]        P_i = sum_s rho_ss l_i(s), excited population of atom i
+ *  [n]               <p> = sum_s rho_ss p(s), mean free-photon number
+ *  [n+1 .. 2n+1]     P(m), m = 0..n: probability of m free photons, the
+ *                    projector onto popcount(s) = n - m (Eq. 13)
+ *  [2n+2]            Tr rho
+ *  [2n+3]            Tr rho^2 = sum_ij |rho_ij|^2 (purity)
+ *  [2n+4]            E = Tr(H rho)                                          */
+#define TC_OBS_STRIDE(n) (2 * (n) + 5)
+
+/* Operation selectors for tc_workspace_size (may be OR-ed). */
+#define TC_OP_EXPM 1
+#define TC_OP_EVOLVE 2
+#define TC_OP_OBSERVABLES 4
+#define TC_OP_BACKWARD 8
+
+/* ------------------------------------------------------------------ misc */
+
+/* Library version string (static storage). */
+TC_API const char* tc_version(void);
+
+/* Message for the last non-OK status returned on this thread (static,
+ * thread-local storage; valid until the next failing call on the thread). */
+TC_API const char* tc_last_error(void);
+
+/* TC_OK if the current CUDA device is an sm_103 GPU the kernels were built for. */
+TC_API tc_status tc_device_check(void);
+
+/* Bytes of `work` needed by the operations in `ops` (TC_OP_*) for n atoms at
+ * the given precision.  For TC_OP_BACKWARD, `steps` and `ckpt_every` size the
+ * checkpoint store; elsewhere they are ignored.  Returns 0 for invalid n. */
+TC_API size_t tc_workspace_size(int n, int precision, int ops, int steps, int ckpt_every);
+
+/* ------------------------------------------------------------- the path */
+
+/* tc_build_hamiltonian -- dense H of Eq. 4 (Sec. II) on the basis of Eq. 2.
+ *  H : device, N*N doubles, row-major, 16-byte aligned, written in full.
+ *      H[s][s]   = omega_c * p(s) + omega_a * popcount(s)
+ *      H[s_g][s_e] = H[s_e][s_g] = coupling element (tc_coupling)
+ *      every other entry 0.
+ *  Each entry is formed by one IEEE multiply/add sequence without
+ *  contraction, so the result is reproducible bit for bit.
+ *  Errors: TC_ERR_INVALID_ARG (n outside 1..16, null or misaligned pointers,
+ *          g not finite). */
+TC_API tc_status tc_build_hamiltonian(const tc_params* params, double* H, void* stream);
+
+/* tc_expm -- U = e^{-i H dt} for a real symmetric H (Sec. III.A, Eqs. 6-8,
+ * 10).  With B = (H - mu I) dt, mu = Tr H / N (when opts->shift), the series
+ * of Eq. 7 splits into the real polynomials C = cos B and S = sin B, each
+ * evaluated by Paterson-Stockmeyer with dense FP64 products; `squarings`
+ * complex squarings follow; U = e^{-i mu dt} (C - i S), then U <- (U + U^T)/2
+ * (U is complex symmetric because H is real symmetric).
+ *  H    : device, N*N doubles (row-major), read only.
+ *  U    : device, N*N c128, written (H and U 16-byte aligned).
+ *  opts : NULL = automatic plan; {10, 0, 0} reproduces Eq. 10 (k_max = 10,
+ *         no scaling, no shift).
+ *  work : device, >= tc_workspace_size(n, TC_FP64, TC_OP_EXPM, 0, 0) bytes.
+ *  The plan is made on the host from Tr H and ||H - mu I||_1, read back from
+ *  the device: this call synchronises `stream` (twice with the shift).
+ *  Errors: TC_ERR_INVALID_ARG (dt not finite or <= 0, bad opts),
+ *          TC_ERR_WORKSPACE (short/misaligned work). */
+TC_API tc_status tc_expm(const double* H, int n, double dt, const tc_expm_opts* opts,
+                         void* U, void* work, size_t work_bytes, void* stream);
+
+/* tc_evolve -- `steps` steps of rho <- U rho U^dag (Eq. 6, evaluated as the
+ * two products of Eq. 12: X = U rho, then rho' = X U^dag).  U must be
+ * complex symmetric (as returned by tc_expm), so U^dag = conj(U).  The second
+ * product computes the lower block triangle only and writes its conjugate
+ * transpose to the upper one, so rho stays exactly Hermitian.
+ *  U        : device, N*N c128, read only, 16-byte aligned.
+ *  rho      : device, N*N c128, in/out (rho_0 in, rho_steps out); Hermitian;
+ *             16-byte aligned.
+ *  precision: tc_precision of the products.
+ *  renorm_every: 0 = never; k > 0 = after every k-th step, rho <- rho / Tr rho
+ *             with the trace taken in FP64.
+ *  params   : model parameters, used only for the energy column; NULL writes
+ *             0 there.
+ *  obs      : device, (steps + 1) * TC_OBS_STRIDE(n) doubles, or NULL.  Row 0
+ *             is rho_0, row k is rho after step k.
+ *  work     : device, >= tc_workspace_size(n, precision, TC_OP_EVOLVE, 0, 0).
+ *  Errors: TC_ERR_INVALID_ARG, TC_ERR_WORKSPACE, TC_ERR_CUDA. */
+TC_API tc_status tc_evolve(const void* U, void* rho, int n, int steps, int precision,
+                           int renorm_every, const tc_params* params, double* obs,
+                           void* work, size_t work_bytes, void* stream);
+
+/* tc_observables -- one observable row (layout above) of a density matrix.
+ *  rho  : device, N*N c128, read only.
+ *  params: for the energy column (NULL writes 0).
+ *  out  : device, TC_OBS_STRIDE(n) doubles.
+ *  work : device, >= tc_workspace_size(n, *, TC_OP_OBSERVABLES, 0, 0); holds
+ *         per-block partial sums, reduced in a fixed order (the result is
+ *         bitwise reproducible run to run).
+ *  Errors: TC_ERR_INVALID_ARG, TC_ERR_WORKSPACE. */
+TC_API tc_status tc_observables(const void* rho, int n, const tc_params* params,
+                                double* out, void* work, size_t work_bytes, void* stream);
+
+/* tc_evolve_backward -- gradient of L = Tr(O rho_K), O = diag(O_diag), with
+ * rho_K = U^K rho_0 U^-K and U = e^{-iH dt}, with respect to
+ * theta = (g_1..g_n, omega_a, omega_c).  Reverse mode through Eq. 6:
+ * Lambda_K = O, Lambda_k = U^dag Lambda_{k+1} U; W = sum_{k<K} rho_k Lambda_k;
+ * M = W U^dag; G = L_exp(-iH dt, M) (Frechet derivative of the exponential);
+ * dL/dtheta_j = 2 dt Im Tr(dH/dtheta_j G).  rho_k is recomputed from
+ * checkpoints stored every `ckpt_every` steps.
+ *  rho0   : device, N*N c128 (Hermitian, read only).
+ *  U      : device, N*N c128, e^{-iH dt} of the same params and dt.
+ *  O_diag : device, N doubles.
+ *  grad   : host, n + 2 doubles, written when the call returns (this call
+ *           synchronises `stream`).
+ *  loss   : host, 1 double (may be NULL), L at the final time.
+ *  work   : device, >= tc_workspace_size(n, TC_FP64, TC_OP_BACKWARD, steps,
+ *           ckpt_every).
+ *  Errors: TC_ERR_INVALID_ARG, TC_ERR_WORKSPACE, TC_ERR_CUDA, TC_ERR_NUMERIC. */
+TC_API tc_status tc_evolve_backward(const tc_params* params, double dt, int steps,
+                                    const void* rho0, const void* U, int ckpt_every,
+                                    const double* O_diag, double* grad, double* loss,
+                                    void* work, size_t work_bytes, void* stream);
+
+/* tc_sync_status -- synchronise `stream`, then report (and clear) the device
+ * status word: TC_ERR_TIMEOUT or TC_ERR_NUMERIC if a kernel recorded one,
+ * TC_ERR_CUDA on an asynchronous CUDA error, else TC_OK. */
+TC_API tc_status tc_sync_status(void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TC_H_ */

@@ -1,0 +1,131 @@
+"""Tavis-Cummings unitary evolution on GB300 (arXiv 2403.06937).
+
+Thin torch-facing binding over libtc's C ABI (``include/tc.h``).  Every step of
+the computation runs in the library's CUDA kernels; this module only allocates
+tensors with torch (device memory, caching allocator, streams) and passes
+pointers.  It never computes a result itself and has no CPU path.
+
+    import paper_2403_06937_gb300 as tc
+    H = tc.build_hamiltonian(n, g, omega_a, omega_c)
+    U = tc.expm(H, n, dt)
+    rho, obs = tc.evolve(U, rho0, n, steps, precision="bf16x3", params=p)
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import torch
+
+from . import _abi
+from ._abi import (TC_BF16X3, TC_COUPLING_BOSONIC, TC_COUPLING_QUBIT_PHOTON, TC_FP64, TC_OP_BACKWARD,
+                   TC_OP_EVOLVE, TC_OP_EXPM, TC_OP_OBSERVABLES, TC_TF32, TC_TF32X3, TCError)
+
+PRECISIONS = {"fp64": TC_FP64, "bf16x3": TC_BF16X3, "tf32": TC_TF32, "tf32x3": TC_TF32X3}
+
+
+@dataclass
+class Params:
+    """Model parameters of Eq. 4: n atoms, couplings g_1..g_n, frequencies."""
+    n: int
+    g: Sequence[float]
+    omega_a: float = 1.0
+    omega_c: float = 1.0
+    coupling: int = TC_COUPLING_BOSONIC
+
+    def c(self):
+        return _abi.make_params(self.n, self.g, self.omega_a, self.omega_c, self.coupling)
+
+
+def obs_stride(n: int) -> int:
+    return 2 * n + 5
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _work(nbytes: int, device) -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def workspace_size(n: int, precision: int = TC_FP64, ops: int = TC_OP_EVOLVE, steps: int = 0,
+                   ckpt_every: int = 0) -> int:
+    return int(_abi.load().tc_workspace_size(n, precision, ops, steps, ckpt_every))
+
+
+def device_check() -> None:
+    _abi.call("tc_device_check")
+
+
+def build_hamiltonian(params: Params, device="cuda", stream=None) -> torch.Tensor:
+    """tc_build_hamiltonian: dense real H (N x N float64) of Eq. 4."""
+    N = 1 << params.n
+    H = torch.empty((N, N), dtype=torch.float64, device=device)
+    p = params.c()
+    _abi.call("tc_build_hamiltonian", ctypes.byref(p), _ptr(H), ctypes.c_void_p(_stream(stream)))
+    return H
+
+
+def expm(H: torch.Tensor, n: int, dt: float, taylor_degree: int = 0, squarings: int = -1, shift: bool = True,
+         stream=None, work: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """tc_expm: U = e^{-iH dt} (N x N complex128); {10, 0, False} is the paper's Eq. 10."""
+    N = 1 << n
+    assert H.dtype == torch.float64 and H.is_contiguous() and H.shape == (N, N)
+    U = torch.empty((N, N), dtype=torch.complex128, device=H.device)
+    need = workspace_size(n, TC_FP64, TC_OP_EXPM)
+    if work is None or work.numel() < need:
+        work = _work(need, H.device)
+    opts = _abi.tc_expm_opts(int(taylor_degree), int(squarings), int(bool(shift)))
+    _abi.call("tc_expm", _ptr(H), n, float(dt), ctypes.byref(opts), _ptr(U), _ptr(work), work.numel(),
+              ctypes.c_void_p(_stream(stream)))
+    return U
+
+
+def evolve(U: torch.Tensor, rho: torch.Tensor, n: int, steps: int, precision="fp64", renorm_every: int = 0,
+           params: Optional[Params] = None, observe: bool = True, inplace: bool = False, stream=None,
+           work: Optional[torch.Tensor] = None):
+    """tc_evolve: `steps` steps of rho <- U rho U^dag.  Returns (rho_T, obs or None)."""
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    N = 1 << n
+    assert U.dtype == torch.complex128 and U.is_contiguous() and U.shape == (N, N)
+    assert rho.dtype == torch.complex128 and rho.is_contiguous() and rho.shape == (N, N)
+    out = rho if inplace else rho.clone()
+    obs = torch.empty((steps + 1, obs_stride(n)), dtype=torch.float64, device=rho.device) if observe else None
+    need = workspace_size(n, prec, TC_OP_EVOLVE)
+    if work is None or work.numel() < need:
+        work = _work(need, rho.device)
+    p = params.c() if params is not None else None
+    _abi.call("tc_evolve", _ptr(U), _ptr(out), n, int(steps), prec, int(renorm_every),
+              ctypes.byref(p) if p is not None else None, _ptr(obs), _ptr(work), work.numel(),
+              ctypes.c_void_p(_stream(stream)))
+    return out, obs
+
+
+def observables(rho: torch.Tensor, n: int, params: Optional[Params] = None, stream=None) -> torch.Tensor:
+    """tc_observables: [P_1..P_n, <p>, P(0..n), Tr rho, Tr rho^2, E] of a density matrix."""
+    N = 1 << n
+    assert rho.dtype == torch.complex128 and rho.is_contiguous() and rho.shape == (N, N)
+    out = torch.empty(obs_stride(n), dtype=torch.float64, device=rho.device)
+    work = _work(workspace_size(n, TC_FP64, TC_OP_OBSERVABLES), rho.device)
+    p = params.c() if params is not None else None
+    _abi.call("tc_observables", _ptr(rho), n, ctypes.byref(p) if p is not None else None, _ptr(out), _ptr(work),
+              work.numel(), ctypes.c_void_p(_stream(stream)))
+    return out
+
+
+def sync_status(stream=None) -> None:
+    _abi.call("tc_sync_status", ctypes.c_void_p(_stream(stream)))
+
+
+__all__ = ["Params", "TCError", "build_hamiltonian", "expm", "evolve", "observables", "workspace_size",
+           "device_check", "sync_status", "obs_stride", "PRECISIONS", "TC_FP64", "TC_BF16X3", "TC_TF32",
+           "TC_TF32X3", "TC_COUPLING_BOSONIC", "TC_COUPLING_QUBIT_PHOTON", "TC_OP_EXPM", "TC_OP_EVOLVE",
+           "TC_OP_OBSERVABLES", "TC_OP_BACKWARD"]

@@ -1,0 +1,103 @@
+"""ctypes view of libtc's C ABI (include/tc.h).  Marshalling only.
+
+Each function here has the name and argument order of the C entry point.
+Pointers are passed as integers (device addresses from torch tensors or host
+addresses), streams as integers (cudaStream_t).  A non-zero status raises
+TCError with the library's message.  There is no fallback: if the library is
+not built, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libtc.so")
+
+TC_OK = 0
+STATUS_NAMES = {0: "TC_OK", 1: "TC_ERR_INVALID_ARG", 2: "TC_ERR_UNSUPPORTED_DEVICE", 3: "TC_ERR_WORKSPACE",
+                4: "TC_ERR_CUDA", 5: "TC_ERR_TIMEOUT", 6: "TC_ERR_NUMERIC"}
+
+TC_FP64, TC_BF16X3, TC_TF32, TC_TF32X3 = 0, 1, 2, 3
+TC_COUPLING_BOSONIC, TC_COUPLING_QUBIT_PHOTON = 0, 1
+TC_OP_EXPM, TC_OP_EVOLVE, TC_OP_OBSERVABLES, TC_OP_BACKWARD = 1, 2, 4, 8
+
+
+class TCError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__("%s: %s (%s)" % (where, msg, STATUS_NAMES.get(status, status)))
+        self.status = status
+
+
+class tc_params(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("g", ctypes.POINTER(ctypes.c_double)), ("omega_a", ctypes.c_double),
+                ("omega_c", ctypes.c_double), ("coupling", ctypes.c_int)]
+
+
+class tc_expm_opts(ctypes.Structure):
+    _fields_ = [("taylor_degree", ctypes.c_int), ("squarings", ctypes.c_int), ("shift", ctypes.c_int)]
+
+
+VP = ctypes.c_void_p
+SZ = ctypes.c_size_t
+I = ctypes.c_int
+D = ctypes.c_double
+DP = ctypes.POINTER(ctypes.c_double)
+
+# name -> (restype, argtypes); the order of include/tc.h
+SIGNATURES = {
+    "tc_version": (ctypes.c_char_p, []),
+    "tc_last_error": (ctypes.c_char_p, []),
+    "tc_device_check": (I, []),
+    "tc_workspace_size": (SZ, [I, I, I, I, I]),
+    "tc_build_hamiltonian": (I, [ctypes.POINTER(tc_params), VP, VP]),
+    "tc_expm": (I, [VP, I, D, ctypes.POINTER(tc_expm_opts), VP, VP, SZ, VP]),
+    "tc_evolve": (I, [VP, VP, I, I, I, I, ctypes.POINTER(tc_params), VP, VP, SZ, VP]),
+    "tc_observables": (I, [VP, I, ctypes.POINTER(tc_params), VP, VP, SZ, VP]),
+    "tc_evolve_backward": (I, [ctypes.POINTER(tc_params), D, I, VP, VP, I, VP, DP, DP, VP, SZ, VP]),
+    "tc_sync_status": (I, [VP]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libtc.so (built by paper_2403_06937_gb300.build); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libtc.so is not built (%s); run `python -m paper_2403_06937_gb300.build` "
+                           "or __graft_entry__.build() -- there is no CPU fallback" % path)
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def last_error() -> str:
+    return load().tc_last_error().decode()
+
+
+def check(status: int, where: str) -> None:
+    if status != TC_OK:
+        raise TCError(status, where, last_error())
+
+
+def make_params(n: int, g, omega_a: float, omega_c: float, coupling: int = TC_COUPLING_BOSONIC):
+    """tc_params plus the ctypes array that keeps g alive."""
+    arr = (ctypes.c_double * n)(*[float(x) for x in g])
+    p = tc_params(n, ctypes.cast(arr, ctypes.POINTER(ctypes.c_double)), float(omega_a), float(omega_c),
+                  int(coupling))
+    p._keep = arr
+    return p
+
+
+def call(name: str, *args) -> int:
+    """Call the C entry point `name` and raise on a non-OK status."""
+    st = getattr(load(), name)(*args)
+    check(st, name)
+    return st

@@ -1,0 +1,19 @@
+// evolve_lowp.cu -- placeholder until the tcgen05 path lands.
+#include "paths.cuh"
+
+namespace tc {
+
+size_t evolve_lowp_bytes(int n, int precision) { (void)n; (void)precision; return 0; }
+
+tc_status evolve_lowp(const double*, double*, int, int, int, int, const Model*, double*, Arena&, cudaStream_t) {
+    return fail(TC_ERR_INVALID_ARG, "low-precision evolution is not built yet");
+}
+
+size_t backward_bytes(int n, int steps, int ckpt_every) { (void)n; (void)steps; (void)ckpt_every; return 0; }
+
+}  // namespace tc
+
+extern "C" TC_API tc_status tc_evolve_backward(const tc_params*, double, int, const void*, const void*, int,
+                                               const double*, double*, double*, void*, size_t, void*) {
+    return tc::fail(TC_ERR_INVALID_ARG, "tc_evolve_backward is not built yet");
+}

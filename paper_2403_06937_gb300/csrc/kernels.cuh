@@ -1,0 +1,60 @@
+// kernels.cuh -- launchers shared between the C-ABI layer and the kernels.
+#pragma once
+
+#include "common.cuh"
+
+namespace tc {
+
+// ---------------------------------------------------------------- H (Eq. 4)
+tc_status launch_build_h(const Model& m, double* H, cudaStream_t s);
+
+// ---------------------------------------------------------------- layout
+// interleaved c128 <-> planar (re, im) FP64 / FP32
+tc_status launch_split_c128(const double* src, double* re, double* im, size_t count, cudaStream_t s);
+tc_status launch_join_c128(const double* re, const double* im, double* dst, size_t count, cudaStream_t s);
+tc_status launch_split_c128_f32(const double* src, float* re, float* im, size_t count, cudaStream_t s);
+tc_status launch_join_c128_f32(const float* re, const float* im, double* dst, size_t count, cudaStream_t s);
+
+// ---------------------------------------------------------------- FP64 GEMM
+// C = alpha * op(A) op(B) + beta * C on planar row-major operands.
+//   A[m][k] at m*lda + k, B[k][n] at k*ldb + n, C[m][n] at m*ldc + n.
+//   conjA/conjB negate the imaginary plane of the operand.
+//   cplx = false: real product of the re planes only (im pointers unused).
+//   herm_lower: M == N, only block-lower tiles are computed and the
+//   conjugate transpose is written to the mirrored tile (result Hermitian).
+struct GemmF64 {
+    int M, N, K;
+    const double* Ar; const double* Ai; long lda;
+    const double* Br; const double* Bi; long ldb;
+    double* Cr; double* Ci; long ldc;
+    double alpha, beta;
+    int conjA, conjB;
+    int cplx;
+    int herm_lower;
+};
+tc_status gemm_f64(const GemmF64& g, cudaStream_t s);
+
+// ---------------------------------------------------------------- elementwise
+// out = c0*I + sum_j c[j] * M_j (real N x N, up to 4 terms; M_j may alias out)
+tc_status launch_lincomb(int N, double c_identity, int terms, const double* const* mats,
+                         const double* coef, double* out, cudaStream_t s);
+// out[i][j] = (A[i][j] + A[j][i]) / 2 for planar complex, then optional phase
+// multiply by (cr + i ci) and interleaved write.  Used at the end of expm.
+tc_status launch_expm_finish(int N, const double* Cm, const double* Sm, double phase_re,
+                             double phase_im, double* U, cudaStream_t s);
+// B = (H - mu I) * dt  (real)
+tc_status launch_shift_scale(int N, const double* H, double mu, double dt, double* B, cudaStream_t s);
+// diag sum and max column abs sum of (H - mu I) on device -> host via stream sync
+tc_status matrix_trace_and_norm1(int N, const double* H, double mu_for_norm, double* trace,
+                                 double* norm1, double* scratch, cudaStream_t s);
+
+// ---------------------------------------------------------------- observables
+// Deterministic observable row of a density matrix in one of three layouts.
+enum RhoLayout { kRhoInterleaved = 0, kRhoPlanarF64 = 1, kRhoPlanarF32 = 2 };
+size_t observables_scratch_bytes(int n);
+tc_status launch_observables(int layout, const void* re_or_c128, const void* im, const Model* m,
+                             int n, double* out, double* scratch, cudaStream_t s);
+// rho <- rho / Tr rho with the trace taken in FP64 from the planar diagonal.
+tc_status launch_renormalise(int layout, void* re, void* im, int n, double* scratch, cudaStream_t s);
+
+}  // namespace tc

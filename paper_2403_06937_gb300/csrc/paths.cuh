@@ -1,0 +1,24 @@
+// paths.cuh -- the multi-kernel paths behind the C-ABI calls.
+#pragma once
+
+#include "kernels.cuh"
+
+namespace tc {
+
+// e^{-iHdt} into U (interleaved c128) using the arena for scratch.
+tc_status expm_impl(const double* H, int n, double dt, const tc_expm_opts* opts, double* U, Arena& ar,
+                    cudaStream_t s, int* used_degree, int* used_squarings);
+
+// FP64 step loop (DMMA products).
+tc_status evolve_f64(const double* U, double* rho, int n, int steps, int renorm_every, const Model* m,
+                     double* obs, Arena& ar, cudaStream_t s);
+
+// Low-precision step loop (tcgen05 products).
+size_t evolve_lowp_bytes(int n, int precision);
+tc_status evolve_lowp(const double* U, double* rho, int n, int steps, int precision, int renorm_every,
+                      const Model* m, double* obs, Arena& ar, cudaStream_t s);
+
+// Reverse-mode gradient.
+size_t backward_bytes(int n, int steps, int ckpt_every);
+
+}  // namespace tc
