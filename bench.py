@@ -1,0 +1,357 @@
+#!/usr/bin/env python
+"""Benchmark: evolution steps/s of rho <- U rho U^dag for a Tavis-Cummings
+system (arXiv 2403.06937, Eq. 6) on one GB300, through libtc's C ABI.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--precision bf16x3|tf32x3|tf32|fp64] [--workload n14|n12|n8]
+
+One "step" is one pass of the step loop: X = U rho, rho' = X U^dag (Hermitian
+half) and the observable row (populations, photon-number probabilities,
+trace, purity, energy), plus the FP64 renormalisation when due.  H and U are
+built once before timing (U in FP64, as every precision form requires).
+
+Prints ONE JSON line on rank 0.  With N > 1 GPUs (torchrun) every rank runs
+its own independent replica of the workload (the step does not shard);
+value = all ranks' steps / max-over-ranks time.
+
+--impl reference times the CPU oracle (test infrastructure, plain C) on the
+host cores for the same workload, on a bounded sample of rows of the dense
+step, extrapolated to steps/s.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "evolution steps/s and complex-GEMM TFLOP/s at n=14 (FP64 vs split-BF16) at stated error"
+
+# dram bytes (read + write) per launch of the dominant kernel from one ncu
+# capture, scaled to the benchmark's launch; None until captured for the
+# current kernel.  Keyed by (precision, n).
+NCU_TRAFFIC = {}
+
+
+def _args():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["bf16x3", "tf32x3", "tf32", "fp64"], default="bf16x3")
+    ap.add_argument("--workload", choices=["n14", "n12", "n8"], default="n14")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    return ap.parse_args()
+
+
+def _workload(name: str):
+    return {"n14": W.config_n14, "n12": W.config_n12, "n8": W.config_n8}[name]()
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    """nvidia-smi sampled every 200 ms during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 8:
+                    continue
+                try:
+                    sm.append(float(parts[0]))
+                    mx.append(float(parts[1]))
+                    power.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[4:8]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": float(max(power)) if power else None}
+
+
+# ------------------------------------------------------------------ peaks
+def _measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "MEASURED_PEAKS.json"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def _fp64_peak_live(torch):
+    """cuBLAS DGEMM (torch.matmul float64, 4096^3) best of 3: the FP64 pipe's measured rate."""
+    a = torch.randn(4096, 4096, dtype=torch.float64, device="cuda")
+    b = torch.randn(4096, 4096, dtype=torch.float64, device="cuda")
+    torch.matmul(a, b)
+    torch.cuda.synchronize()
+    best = 1e30
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    del a, b
+    return 2.0 * 4096 ** 3 / (best * 1e-3) / 1e12
+
+
+# ------------------------------------------------------------------ CPU oracle
+def _cpu_sample(cfg, target_s: float, reps: int = 1):
+    """Time the oracle's dense step (rows of rho' = U rho U^dag) on host cores.
+
+    Returns (steps_per_s, cores, sample description).  U and rho are dense
+    seeded synthetic matrices of the workload's size (the oracle's loops do
+    the same work for any dense operands).
+    """
+    import oracle
+    oracle.build()
+    N = cfg.N
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    rng = np.random.default_rng(1234)
+    U = (rng.random((N, N)) - 0.5) + 1j * (rng.random((N, N)) - 0.5)
+    rho = (rng.random((N, N)) - 0.5) + 1j * (rng.random((N, N)) - 0.5)
+    # calibrate: one row per core
+    rows = cores
+    t0 = time.perf_counter()
+    oracle.dense_step(U, rho, rows=(0, rows))
+    t1 = time.perf_counter() - t0
+    per_row = t1 / rows
+    rows = max(cores, int(target_s / max(per_row, 1e-9)) // cores * cores)
+    rows = min(rows, N)
+    times = []
+    for r in range(reps):
+        t0 = time.perf_counter()
+        oracle.dense_step(U, rho, rows=(0, rows))
+        times.append(time.perf_counter() - t0)
+    t = float(np.median(times))
+    steps_per_s = rows / (t * N)
+    sample = ("oracle dense step (plain C loops, OpenMP over rows): rows 0..%d of rho' = U rho U^dag at N=%d, "
+              "%.2f s per sample, extrapolated to whole steps (x %d/%d)" % (rows - 1, N, t, N, rows))
+    return steps_per_s, cores, sample, t
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(a, cfg):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return 0
+    vals = []
+    per_step_target = max(1.0, min(a.cpu_seconds, 240.0 / max(1, a.steps + a.warmup)))
+    sample = cores = None
+    for i in range(a.warmup + a.steps):
+        v, cores, sample, _ = _cpu_sample(cfg, per_step_target)
+        if i >= a.warmup:
+            vals.append(v)
+    value = float(np.median(vals))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": cfg.description, "dim": cfg.N, "reference": "CPU oracle (no code ships with the paper)"},
+        "cpu_baseline": {"value": value, "unit": "steps/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(a, cfg):
+    import torch
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2403_06937_gb300 as tc
+    tc.device_check()
+
+    n, N = cfg.n, cfg.N
+    prec = a.precision
+    params = tc.Params(n, list(map(float, cfg.g)), cfg.omega_a, cfg.omega_c)
+    t_setup = time.perf_counter()
+    H = tc.build_hamiltonian(params)
+    U = tc.expm(H, n, cfg.dt)
+    del H
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t_setup
+    rho = torch.zeros((N, N), dtype=torch.complex128, device="cuda")
+    rho[N - 1, N - 1] = 1.0
+    renorm = cfg.renorm_every if prec != "fp64" else 0
+    work = torch.empty(tc.workspace_size(n, tc.PRECISIONS[prec], tc.TC_OP_EVOLVE), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    # warm-up (untimed)
+    rho, _ = tc.evolve(U, rho, n, a.warmup, prec, renorm_every=renorm, params=params, inplace=True, work=work)
+    tc.sync_status()
+
+    fp64_peak = _fp64_peak_live(torch) if prec == "fp64" else None
+    clocks = Clocks(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    tc.timing_read()
+    tc.timing_enable(True)
+    launches0 = tc.launch_count()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    rho, obs = tc.evolve(U, rho, n, a.steps, prec, renorm_every=renorm, params=params, inplace=True, work=work)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    tc.timing_enable(False)
+    launches = tc.launch_count() - launches0
+    tc.sync_status()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    klaunch, kms, kflops = tc.timing_read()
+    value = world * a.steps / (ms * 1e-3)
+    credited = 12.0 * N ** 3
+    products = {"fp64": 1, "bf16x3": 6, "tf32": 1, "tf32x3": 3}[prec]
+
+    peaks, peak_src = _measured_peaks()
+    if prec == "fp64":
+        peak = fp64_peak
+        peak_note = "FP64: cuBLAS DGEMM 4096^3 measured live in this run (torch.matmul float64)"
+    elif prec in ("tf32", "tf32x3"):
+        peak = peaks["bf16_tflops_sustained"] / 2.0
+        peak_note = "TF32: %s bf16_tflops_sustained x 1/2 (nominal tf32:bf16 ratio)" % peak_src
+    else:
+        peak = peaks["bf16_tflops_sustained"]
+        peak_note = "BF16: %s bf16_tflops_sustained (kernel timed inside a long step)" % peak_src
+    achieved = kflops / (kms * 1e-3) / 1e12 if kms > 0 else 0.0
+    o = obs.cpu().numpy()
+    roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak if peak else None, "traffic": NCU_TRAFFIC.get((prec, n)),
+            "kernel": "complex GEMM (%s), %d launches timed, %.3f ms avg" % (prec, klaunch, kms / max(klaunch, 1)),
+            "peak_source": peak_note,
+            "algorithmic_flops_per_launch_avg": kflops / max(klaunch, 1)}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp64": "f64", "bf16x3": "bf16", "tf32": "tf32", "tf32x3": "tf32"}[prec],
+        "data": "synthetic",
+        "config": {"workload": cfg.description, "precision": prec, "dim": N,
+                   "products_per_complex_product": products,
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (U and rho are %d MiB each in complex128)" % (16 * N * N >> 20),
+                   "setup_s": t_setup},
+        "credited_tflops": credited * value / world / 1e12,
+        "credited_flops_per_step": credited,
+        "roofline": roof,
+        "clocks": ck,
+        "gpu_launches": launches,
+        "trace_final": float(o[-1, 2 * n + 2]),
+        "purity_final": float(o[-1, 2 * n + 3]),
+    }
+
+    if not a.no_e2e:
+        # end to end through the public C ABI call with host buffers: every step copies
+        # rho (pinned host) in, runs one step, copies rho and the observable rows back.
+        rho_h = torch.empty((N, N), dtype=torch.complex128, pin_memory=True)
+        rho_h.copy_(rho)
+        obs_h = torch.empty((2, 2 * n + 5), dtype=torch.float64, pin_memory=True)
+        hw = torch.empty(tc.workspace_size(n, tc.PRECISIONS[prec], 16, 1), dtype=torch.uint8, device="cuda")
+        tc.evolve_host(U, rho_h, n, 1, prec, params=params, obs_host=obs_h, work=hw)   # warm
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(a.steps):
+            tc.evolve_host(U, rho_h, n, 1, prec, params=params, obs_host=obs_h, work=hw)
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([te], device="cuda", dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            te = float(t.item())
+        line["e2e"] = {"value": world * a.steps / te, "unit": "steps/s", "h2d_bytes_per_step": 16 * N * N,
+                       "d2h_bytes_per_step": 16 * N * N + 2 * (2 * n + 5) * 8,
+                       "api": "tc_evolve_host (C ABI, pinned host rho, one step per call)"}
+        del rho_h, hw
+
+    if rank == 0 and not a.no_cpu:
+        v, cores, sample, _ = _cpu_sample(cfg, a.cpu_seconds)
+        line["cpu_baseline"] = {"value": v, "unit": "steps/s", "cores": cores, "kind": "oracle", "sample": sample}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    a = _args()
+    cfg = _workload(a.workload)
+    if a.impl == "reference":
+        return run_reference(a, cfg)
+    return run_ours(a, cfg)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -120,6 +120,7 @@ typedef struct tc_expm_opts {
 #define TC_OP_EVOLVE 2
 #define TC_OP_OBSERVABLES 4
 #define TC_OP_BACKWARD 8
+#define TC_OP_EVOLVE_HOST 16
 
 /* ------------------------------------------------------------------ misc */
 
@@ -221,6 +222,36 @@ TC_API tc_status tc_evolve_backward(const tc_params* params, double dt, int step
                                     const void* rho0, const void* U, int ckpt_every,
                                     const double* O_diag, double* grad, double* loss,
                                     void* work, size_t work_bytes, void* stream);
+
+/* tc_evolve_host -- tc_evolve with the density matrix and the observables in
+ * HOST memory: copies rho_host to the device, runs `steps` steps on the GPU,
+ * copies rho and the observable rows back, and synchronises `stream` before
+ * returning (the results are in host memory on return).  Page-locked host
+ * buffers give the full copy bandwidth; pageable ones work but copy slower.
+ *  U        : device, N*N c128 (as tc_evolve), 16-byte aligned.
+ *  rho_host : host, N*N c128, in/out.
+ *  obs_host : host, (steps + 1) * TC_OBS_STRIDE(n) doubles, or NULL.
+ *  work     : device, >= tc_workspace_size(n, precision, TC_OP_EVOLVE_HOST,
+ *             steps, 0) bytes (includes the device copies of rho and obs).
+ *  Errors: as tc_evolve. */
+TC_API tc_status tc_evolve_host(const void* U, void* rho_host, int n, int steps, int precision,
+                                int renorm_every, const tc_params* params, double* obs_host,
+                                void* work, size_t work_bytes, void* stream);
+
+/* ----------------------------------------------------------- measurement */
+
+/* Number of kernels this library has launched in this process. */
+TC_API long long tc_launch_count(void);
+
+/* tc_timing_enable(1): from now on every product-kernel launch (the GEMMs of
+ * the step loop) is bracketed by a CUDA event pair recorded on the stream it
+ * is launched on, tagged with its algorithmic FLOP count (8 N^3 for X = U rho,
+ * 4 N^3 for the Hermitian half of X U^dag, times the number of low-precision
+ * products of the precision form).  tc_timing_read synchronises those events
+ * and returns the number of timed launches, their summed device time in ms
+ * and their FLOPs, then clears the record. */
+TC_API tc_status tc_timing_enable(int on);
+TC_API tc_status tc_timing_read(long long* launches, double* ms, double* flops);
 
 /* tc_sync_status -- synchronise `stream`, then report (and clear) the device
  * status word: TC_ERR_TIMEOUT or TC_ERR_NUMERIC if a kernel recorded one,

@@ -121,11 +121,46 @@ def observables(rho: torch.Tensor, n: int, params: Optional[Params] = None, stre
     return out
 
 
+def evolve_host(U: torch.Tensor, rho_host: torch.Tensor, n: int, steps: int, precision="fp64",
+                renorm_every: int = 0, params: Optional[Params] = None, obs_host: Optional[torch.Tensor] = None,
+                stream=None, work: Optional[torch.Tensor] = None) -> None:
+    """tc_evolve_host: rho_host (CPU complex128, ideally pinned) stepped in place on the GPU; blocks."""
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    N = 1 << n
+    assert rho_host.device.type == "cpu" and rho_host.dtype == torch.complex128 and rho_host.shape == (N, N)
+    need = workspace_size(n, prec, _abi.TC_OP_EVOLVE_HOST, steps)
+    if work is None or work.numel() < need:
+        work = _work(need, U.device)
+    p = params.c() if params is not None else None
+    _abi.call("tc_evolve_host", _ptr(U), _ptr(rho_host), n, int(steps), prec, int(renorm_every),
+              ctypes.byref(p) if p is not None else None, _ptr(obs_host), _ptr(work), work.numel(),
+              ctypes.c_void_p(_stream(stream)))
+
+
+def launch_count() -> int:
+    """Kernels launched by libtc in this process."""
+    return int(_abi.load().tc_launch_count())
+
+
+def timing_enable(on: bool = True) -> None:
+    _abi.call("tc_timing_enable", int(bool(on)))
+
+
+def timing_read():
+    """(launches, device ms, FLOPs) of the product kernels timed since the last read."""
+    L = ctypes.c_longlong()
+    ms = ctypes.c_double()
+    fl = ctypes.c_double()
+    _abi.call("tc_timing_read", ctypes.byref(L), ctypes.byref(ms), ctypes.byref(fl))
+    return int(L.value), float(ms.value), float(fl.value)
+
+
 def sync_status(stream=None) -> None:
     _abi.call("tc_sync_status", ctypes.c_void_p(_stream(stream)))
 
 
-__all__ = ["Params", "TCError", "build_hamiltonian", "expm", "evolve", "observables", "workspace_size",
+__all__ = ["Params", "TCError", "build_hamiltonian", "expm", "evolve", "evolve_host", "observables",
+           "workspace_size", "launch_count", "timing_enable", "timing_read",
            "device_check", "sync_status", "obs_stride", "PRECISIONS", "TC_FP64", "TC_BF16X3", "TC_TF32",
            "TC_TF32X3", "TC_COUPLING_BOSONIC", "TC_COUPLING_QUBIT_PHOTON", "TC_OP_EXPM", "TC_OP_EVOLVE",
            "TC_OP_OBSERVABLES", "TC_OP_BACKWARD"]

@@ -20,7 +20,7 @@ STATUS_NAMES = {0: "TC_OK", 1: "TC_ERR_INVALID_ARG", 2: "TC_ERR_UNSUPPORTED_DEVI
 
 TC_FP64, TC_BF16X3, TC_TF32, TC_TF32X3 = 0, 1, 2, 3
 TC_COUPLING_BOSONIC, TC_COUPLING_QUBIT_PHOTON = 0, 1
-TC_OP_EXPM, TC_OP_EVOLVE, TC_OP_OBSERVABLES, TC_OP_BACKWARD = 1, 2, 4, 8
+TC_OP_EXPM, TC_OP_EVOLVE, TC_OP_OBSERVABLES, TC_OP_BACKWARD, TC_OP_EVOLVE_HOST = 1, 2, 4, 8, 16
 
 
 class TCError(RuntimeError):
@@ -55,6 +55,10 @@ SIGNATURES = {
     "tc_evolve": (I, [VP, VP, I, I, I, I, ctypes.POINTER(tc_params), VP, VP, SZ, VP]),
     "tc_observables": (I, [VP, I, ctypes.POINTER(tc_params), VP, VP, SZ, VP]),
     "tc_evolve_backward": (I, [ctypes.POINTER(tc_params), D, I, VP, VP, I, VP, DP, DP, VP, SZ, VP]),
+    "tc_evolve_host": (I, [VP, VP, I, I, I, I, ctypes.POINTER(tc_params), VP, VP, SZ, VP]),
+    "tc_launch_count": (ctypes.c_longlong, []),
+    "tc_timing_enable": (I, [I]),
+    "tc_timing_read": (I, [ctypes.POINTER(ctypes.c_longlong), DP, DP]),
     "tc_sync_status": (I, [VP]),
 }
 

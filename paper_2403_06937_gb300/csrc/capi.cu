@@ -94,6 +94,15 @@ size_t evolve_f64_bytes(int n) {
     return 6 * mat_bytes(n, 8) + observables_scratch_bytes(n) + 256;
 }
 
+size_t evolve_bytes(int n, int precision) {
+    return precision == TC_FP64 ? evolve_f64_bytes(n) : evolve_lowp_bytes(n, precision);
+}
+
+// device staging of tc_evolve_host: rho (c128) and the observable rows
+size_t evolve_host_extra(int n, int steps) {
+    return mat_bytes(n, 16) + round256((size_t)(steps + 1) * (2 * n + 5) * sizeof(double));
+}
+
 tc_status check_work(void* work, size_t have, size_t need) {
     if (need == 0) return TC_OK;
     if (!work) return fail(TC_ERR_WORKSPACE, "work is NULL (need %zu bytes)", need);
@@ -344,6 +353,7 @@ TC_API size_t tc_workspace_size(int n, int precision, int ops, int steps, int ck
         else upd(evolve_lowp_bytes(n, precision));
     }
     if (ops & TC_OP_OBSERVABLES) upd(observables_scratch_bytes(n));
+    if (ops & TC_OP_EVOLVE_HOST) upd(evolve_bytes(n, precision) + evolve_host_extra(n, steps));
     if (ops & TC_OP_BACKWARD) upd(backward_bytes(n, steps, ckpt_every));
     return need;
 }
@@ -417,6 +427,43 @@ TC_API tc_status tc_evolve(const void* U, void* rho, int n, int steps, int preci
                            renorm_every, mp, obs, ar, s);
     return evolve_f64(static_cast<const double*>(U), static_cast<double*>(rho), n, steps, renorm_every, mp, obs,
                       ar, s);
+}
+
+TC_API tc_status tc_evolve_host(const void* U, void* rho_host, int n, int steps, int precision, int renorm_every,
+                                const tc_params* params, double* obs_host, void* work, size_t work_bytes,
+                                void* stream) {
+    if (n < 1 || n > kMaxAtoms) return fail(TC_ERR_INVALID_ARG, "n = %d outside 1..16", n);
+    if (!U || !rho_host) return fail(TC_ERR_INVALID_ARG, "U or rho_host is NULL");
+    if (reinterpret_cast<uintptr_t>(U) & 15u) return fail(TC_ERR_INVALID_ARG, "U must be 16-byte aligned");
+    if (steps < 0 || renorm_every < 0) return fail(TC_ERR_INVALID_ARG, "steps / renorm_every < 0");
+    if (precision < TC_FP64 || precision > TC_TF32X3) return fail(TC_ERR_INVALID_ARG, "unknown precision %d", precision);
+    Model m;
+    const Model* mp = nullptr;
+    if (params) {
+        TC_TRY(make_model(params, &m));
+        if (m.n != n) return fail(TC_ERR_INVALID_ARG, "params->n != n");
+        mp = &m;
+    }
+    TC_TRY(check_work(work, work_bytes, evolve_bytes(n, precision) + evolve_host_extra(n, steps)));
+    TC_TRY(check_device());
+    cudaStream_t s = as_stream(stream);
+    const size_t N = (size_t)1 << n;
+    Arena ar{static_cast<char*>(work), work_bytes, 0};
+    double* rho_dev = ar.take<double>(2 * N * N);
+    double* obs_dev = ar.take<double>((size_t)(steps + 1) * (2 * n + 5));
+    TC_CUDA(cudaMemcpyAsync(rho_dev, rho_host, 16 * N * N, cudaMemcpyHostToDevice, s));
+    tc_status st = precision == TC_FP64
+                       ? evolve_f64(static_cast<const double*>(U), rho_dev, n, steps, renorm_every, mp,
+                                    obs_host ? obs_dev : nullptr, ar, s)
+                       : evolve_lowp(static_cast<const double*>(U), rho_dev, n, steps, precision, renorm_every,
+                                     mp, obs_host ? obs_dev : nullptr, ar, s);
+    if (st != TC_OK) return st;
+    TC_CUDA(cudaMemcpyAsync(rho_host, rho_dev, 16 * N * N, cudaMemcpyDeviceToHost, s));
+    if (obs_host)
+        TC_CUDA(cudaMemcpyAsync(obs_host, obs_dev, (size_t)(steps + 1) * (2 * n + 5) * sizeof(double),
+                                cudaMemcpyDeviceToHost, s));
+    TC_CUDA(cudaStreamSynchronize(s));
+    return TC_OK;
 }
 
 TC_API tc_status tc_sync_status(void* stream) {

@@ -25,7 +25,14 @@ tc_status fail(tc_status s, const char* fmt, ...);
                               cudaGetErrorString(e_), __FILE__, __LINE__);         \
     } while (0)
 
-#define TC_LAUNCH_CHECK() TC_CUDA(cudaPeekAtLastError())
+// Every kernel launch is followed by this: it counts the launch and reports
+// a launch error as TC_ERR_CUDA.
+void count_launch(int k);
+#define TC_LAUNCH_CHECK()                                                          \
+    do {                                                                           \
+        ::tc::count_launch(1);                                                     \
+        TC_CUDA(cudaPeekAtLastError());                                            \
+    } while (0)
 
 #define TC_TRY(expr)                                                               \
     do {                                                                           \

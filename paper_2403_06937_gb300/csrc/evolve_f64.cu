@@ -4,6 +4,7 @@
 // conj(U) = U^dag), of which only the block-lower triangle is computed and
 // mirrored, keeping rho exactly Hermitian.
 #include "paths.cuh"
+#include "timing.cuh"
 
 namespace tc {
 
@@ -39,8 +40,14 @@ tc_status evolve_f64(const double* U, double* rho, int n, int steps, int renorm_
     g2.herm_lower = 1;
 
     for (int k = 1; k <= steps; k++) {
-        TC_TRY(gemm_f64(g1, s));
-        TC_TRY(gemm_f64(g2, s));
+        {
+            ProductTimer t(8.0 * (double)N * N * N, s);   // X = U rho: 8 N^3
+            TC_TRY(gemm_f64(g1, s));
+        }
+        {
+            ProductTimer t(4.0 * (double)N * N * N, s);   // rho' = X U^dag, Hermitian half: 4 N^3
+            TC_TRY(gemm_f64(g2, s));
+        }
         if (renorm_every > 0 && k % renorm_every == 0) TC_TRY(launch_renormalise(kRhoPlanarF64, Rr, Ri, n, scratch, s));
         if (obs) TC_TRY(launch_observables(kRhoPlanarF64, Rr, Ri, m, n, obs + (size_t)k * stride, scratch, s));
     }

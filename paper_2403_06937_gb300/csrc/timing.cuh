@@ -1,0 +1,23 @@
+// timing.cuh -- launch counting and optional event timing of product kernels.
+#pragma once
+
+#include "common.cuh"
+
+namespace tc {
+
+// RAII: when timing is enabled, records an event pair around the enclosed
+// product-kernel launch(es) on stream `s`, credited with `flops`.
+class ProductTimer {
+  public:
+    ProductTimer(double flops, cudaStream_t s);
+    ~ProductTimer();
+    ProductTimer(const ProductTimer&) = delete;
+    ProductTimer& operator=(const ProductTimer&) = delete;
+
+  private:
+    double flops_;
+    cudaStream_t s_;
+    cudaEvent_t a_ = nullptr, b_ = nullptr;
+};
+
+}  // namespace tc
