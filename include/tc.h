@@ -202,6 +202,35 @@ TC_API tc_status tc_evolve(const void* U, void* rho, int n, int steps, int preci
 TC_API tc_status tc_observables(const void* rho, int n, const tc_params* params,
                                 double* out, void* work, size_t work_bytes, void* stream);
 
+/* tc_observables_noalloc -- tc_observables for callers that cannot allocate
+ * device memory at all, so cannot supply a `work` buffer: for example a
+ * monitor thread inside a program whose device memory is wholly owned by
+ * another allocator (a framework's caching pool or an arena planned at
+ * start-up, where one more cudaMalloc may fail or fragment it), or a caller
+ * that must not pay the device-wide synchronisation that cudaMalloc and
+ * cudaFree can impose on work already running on other streams.  This
+ * entry point has no counterpart in the paper.
+ *
+ * It computes exactly what tc_observables computes (same kernels, same
+ * reduction order, bitwise the same row) but keeps the per-block partial sums
+ * in a fixed device array inside the library: 1024 x 37 doubles (296 KiB),
+ * enough for every n up to 16.  It calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ *  - The array exists on every GPU that loads the library, until the process
+ *    exits.
+ *  - The first call on a device looks up the array's device address with that
+ *    device current (cudaGetSymbolAddress); make that first call before any
+ *    stream capture on the device.
+ *  - Every call shares the one array.  Calls that overlap on the GPU (on
+ *    different streams, or from several host threads on one device) race on
+ *    it and may return wrong rows; serialise them.  No slot needs clearing:
+ *    each call writes every slot it later reads.
+ *  rho, n, params, out, stream: as tc_observables.
+ *  Errors: TC_ERR_INVALID_ARG (also when n needs more scratch than the array
+ *          holds), TC_ERR_UNSUPPORTED_DEVICE, TC_ERR_CUDA. */
+TC_API tc_status tc_observables_noalloc(const void* rho, int n, const tc_params* params, double* out,
+                                        void* stream);
+
 /* tc_evolve_backward -- gradient of L = Tr(O rho_K), O = diag(O_diag), with
  * rho_K = U^K rho_0 U^-K and U = e^{-iH dt}, with respect to
  * theta = (g_1..g_n, omega_a, omega_c).  Reverse mode through Eq. 6:

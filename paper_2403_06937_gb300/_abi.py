@@ -54,6 +54,7 @@ SIGNATURES = {
     "tc_expm": (I, [VP, I, D, ctypes.POINTER(tc_expm_opts), VP, VP, SZ, VP]),
     "tc_evolve": (I, [VP, VP, I, I, I, I, ctypes.POINTER(tc_params), VP, VP, SZ, VP]),
     "tc_observables": (I, [VP, I, ctypes.POINTER(tc_params), VP, VP, SZ, VP]),
+    "tc_observables_noalloc": (I, [VP, I, ctypes.POINTER(tc_params), VP, VP]),
     "tc_evolve_backward": (I, [ctypes.POINTER(tc_params), D, I, VP, VP, I, VP, DP, DP, VP, SZ, VP]),
     "tc_evolve_host": (I, [VP, VP, I, I, I, I, ctypes.POINTER(tc_params), VP, VP, SZ, VP]),
     "tc_launch_count": (ctypes.c_longlong, []),

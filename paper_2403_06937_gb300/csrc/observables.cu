@@ -11,6 +11,8 @@
 // pairs of that row), warps fold in a fixed order into per-block partials,
 // and a single block sums the partials in block order.  The grid size is a
 // function of N only, so reruns are bitwise identical.
+#include <mutex>
+
 #include "kernels.cuh"
 
 namespace tc {
@@ -192,3 +194,64 @@ tc_status launch_renormalise(int layout, void* re, void* im, int n, double* scra
 }
 
 }  // namespace tc
+
+// ---------------------------------------------------------------------------
+// tc_observables_noalloc: the same two kernels with their per-block partial
+// sums in a fixed device array instead of a caller-provided work buffer.
+//
+// The array is sized for the largest grid the observables use (1024 blocks)
+// times the widest row (n = 16: 37 doubles), 296 KiB.  It is file-scope
+// device memory: every GPU that loads this library holds it until the
+// process exits.  All calls share it, so calls that overlap on the GPU
+// (different streams, or different host threads on one device) race on it.
+// Nothing in it has to start at zero: the first kernel writes every slot the
+// second kernel reads, in the same call.
+namespace tc {
+namespace {
+constexpr size_t kNoAllocPartials = 1024 * (2 * kMaxAtoms + 5);
+static __device__ __align__(256) double g_noalloc_partials[kNoAllocPartials];
+
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[64];   // device address of the array, per device
+}  // namespace
+
+}  // namespace tc
+
+extern "C" TC_API tc_status tc_observables_noalloc(const void* rho, int n, const tc_params* params, double* out,
+                                                   void* stream) {
+    using namespace tc;
+    if (n < 1 || n > kMaxAtoms) return fail(TC_ERR_INVALID_ARG, "n = %d outside 1..16", n);
+    if (!rho || !out) return fail(TC_ERR_INVALID_ARG, "rho or out is NULL");
+    if ((reinterpret_cast<uintptr_t>(rho) | reinterpret_cast<uintptr_t>(out)) & 7u)
+        return fail(TC_ERR_INVALID_ARG, "rho and out must be 8-byte aligned");
+    const size_t need = (size_t)obs_grid(n) * (size_t)(2 * n + 5);
+    if (need > kNoAllocPartials)
+        return fail(TC_ERR_INVALID_ARG,
+                    "tc_observables_noalloc: n = %d needs %zu doubles of scratch, the fixed array holds %zu",
+                    n, need, kNoAllocPartials);
+    Model m;
+    if (params) {
+        TC_TRY(make_model(params, &m));
+        if (m.n != n) return fail(TC_ERR_INVALID_ARG, "params->n != n");
+    }
+    TC_TRY(check_device());
+    int dev = 0;
+    TC_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(TC_ERR_UNSUPPORTED_DEVICE, "device index %d out of range", dev);
+    double* partials = nullptr;
+    {
+        // first call on this device: resolve the array's device address with
+        // the device current (the array's name in host code is not that address)
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void* p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+            if (e != cudaSuccess)
+                return fail(TC_ERR_CUDA, "cudaGetSymbolAddress(observables scratch): %s", cudaGetErrorString(e));
+            g_noalloc_ptr[dev] = static_cast<double*>(p);
+        }
+        partials = g_noalloc_ptr[dev];
+    }
+    return launch_observables(kRhoInterleaved, rho, nullptr, params ? &m : nullptr, n, out, partials,
+                              as_stream(stream));
+}
