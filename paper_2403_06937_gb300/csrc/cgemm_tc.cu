@@ -1,0 +1,376 @@
+// cgemm_tc.cu -- complex GEMM Y = U P^H on the sm_103a tensor cores
+// (tcgen05.mma, operands staged by TMA, FP32 accumulators in TMEM) for the
+// low-precision forms of the step rho <- U rho U^dag (Sec. III.A, Eqs. 6, 12).
+//
+// Both products of a step have this one shape, because U is complex symmetric
+// (U^T = U, H real symmetric) and rho is Hermitian:
+//     X   = U rho   = U rho^H           (P = rho)
+//     rho' = X U^dag = (U X^H)^H = U X^H (rho' Hermitian; P = X)
+// so a kernel computing Y = U P^H for a row-major P serves both, with P
+// read K-major exactly as it is stored.
+//
+// Tile: one CTA computes the complex 128 x 128 tile Y[I, J].  A operands are
+// the row tiles U_r[I], U_i[I] (M = 128); the B operand is the 256-row stack
+// [P_r[J]; P_i[J]] (N = 256), shared by both MMAs.  Two FP32 accumulators in
+// TMEM (2 x 256 columns):
+//     D1 = U_r [P_r; P_i]^T = [U_r P_r^T | U_r P_i^T]
+//     D2 = U_i [P_r; P_i]^T = [U_i P_r^T | U_i P_i^T]
+// and the epilogue forms Y_r = U_r P_r^T + U_i P_i^T, Y_i = U_i P_r^T - U_r P_i^T.
+//
+// Precision forms: every FP32 (or FP64) operand x is held as S parts
+// (BF16x3: three BF16 parts x0 + x1 + x2; TF32: one TF32 part; TF32x3: a
+// big and a small TF32 part) and the product of two split operands is the
+// sum of the part products whose order is below the FP32 rounding level
+// (BF16x3: six products, TF32x3: three).  All S parts of every operand for a
+// 32-byte slice of K sit in one pipeline stage, and all part products of the
+// stage are issued from it, so each operand byte crosses L2 -> SMEM once.
+//
+// Roles (192 threads): warp 4 lane 0 issues TMA loads into a ring of STAGES
+// stages; warp 5 lane 0 issues tcgen05.mma and commits each stage back to the
+// producer; warps 0-3 (one TMEM lane quarter each) run the epilogue.  Every
+// wait is bounded: on timeout the CTA records kStatusTimeout, stops issuing,
+// waits (bounded) for its own copies and MMAs, frees TMEM and returns.
+#include <cuda_bf16.h>
+
+#include "cgemm_tc.cuh"
+#include "sm100.cuh"
+
+namespace tc {
+namespace {
+
+using namespace sm100;
+
+constexpr int kThreads = 192;
+constexpr int kRowBytes = 32;                 // bytes of K per operand row per stage
+constexpr int kATile = 128 * kRowBytes;       // 4 KB
+constexpr int kBTile = 256 * kRowBytes;       // 8 KB
+constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s per wait
+
+template <int S>
+struct Pairs;
+template <>
+struct Pairs<1> {
+    static constexpr int n = 1;
+    __device__ static constexpr int a(int) { return 0; }
+    __device__ static constexpr int b(int) { return 0; }
+};
+template <>
+struct Pairs<2> {   // big*big, big*small, small*big
+    static constexpr int n = 3;
+    __device__ static constexpr int a(int p) { return p == 2 ? 1 : 0; }
+    __device__ static constexpr int b(int p) { return p == 1 ? 1 : 0; }
+};
+template <>
+struct Pairs<3> {   // x0y0, x0y1, x1y0, x0y2, x1y1, x2y0
+    static constexpr int n = 6;
+    __device__ static constexpr int a(int p) { return p == 2 ? 1 : (p == 4 ? 1 : (p == 5 ? 2 : 0)); }
+    __device__ static constexpr int b(int p) { return p == 1 ? 1 : (p == 3 ? 2 : (p == 4 ? 1 : 0)); }
+};
+
+// -------------------------------------------------------------- splitting
+__device__ __forceinline__ float tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// parts of an FP32 value in the operand format of (KIND, S)
+template <int KIND, int S>
+struct Parts {
+    using T = typename std::conditional<KIND == 0, __nv_bfloat16, float>::type;
+    __device__ static void split(float x, T (&p)[S]) {
+        if constexpr (KIND == 0) {
+            float r = x;
+#pragma unroll
+            for (int s = 0; s < S; s++) {
+                p[s] = __float2bfloat16_rn(r);
+                r = r - __bfloat162float(p[s]);
+            }
+        } else {
+            float r = x;
+#pragma unroll
+            for (int s = 0; s < S; s++) {
+                p[s] = tf32_rna(r);
+                r = r - p[s];
+            }
+        }
+    }
+};
+
+template <typename T>
+__device__ __forceinline__ void store16(T* dst, const T (&v)[16]) {
+    const uint4* src = reinterpret_cast<const uint4*>(v);
+    uint4* d = reinterpret_cast<uint4*>(dst);
+#pragma unroll
+    for (int i = 0; i < (int)(16 * sizeof(T) / 16); i++) d[i] = src[i];
+}
+
+__device__ __forceinline__ void tile_of(int mode, int T, int b, int& I, int& J) {
+    if (mode == 0) {
+        // grouped raster: 8 row tiles share their U panels in L2
+        const int G = 8;
+        int per_group = G * T;
+        int g = b / per_group;
+        int first = g * G;
+        int rows = min(G, T - first);
+        int in = b % per_group;
+        I = first + in % rows;
+        J = in / rows;
+    } else {
+        int i = (int)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
+        while ((i + 1) * (i + 2) / 2 <= b) ++i;
+        while (i * (i + 1) / 2 > b) --i;
+        I = i;
+        J = b - i * (i + 1) / 2;
+    }
+}
+
+template <int KIND, int S, int STAGES, int MODE>
+__global__ void __launch_bounds__(kThreads, 1)
+    cgemm_tc_kernel(const __grid_constant__ CUtensorMap tmU, const __grid_constant__ CUtensorMap tmP, CgemmEpi ep) {
+    using P = Parts<KIND, S>;
+    using T = typename P::T;
+    constexpr int kStage = 2 * S * kATile + S * kBTile;
+    constexpr int kElem = KIND == 0 ? 2 : 4;
+    constexpr int kKPerStage = kRowBytes / kElem;   // K elements per stage (one MMA K-step)
+    constexpr uint32_t kIdesc = make_idesc(KIND == 0 ? 1u : 2u, 128u, 256u);
+
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * kStage);
+    uint64_t* empty = full + STAGES;
+    uint64_t* accum = empty + STAGES;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+    volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int I, J;
+    tile_of(MODE, ep.tiles, blockIdx.x, I, J);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; s++) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(accum, 1);
+        *abort = 0;
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        tmem_alloc(saddr(tmem_slot), 512);
+        tmem_relinquish();
+    }
+    if (warp == 4 && lane == 0) {
+        prefetch_tmap(&tmU);
+        prefetch_tmap(&tmP);
+    }
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int KB = ep.Np / kKPerStage;
+
+    if (warp == 4) {
+        // ---------------------------------------------------------- producer
+        if (lane == 0) {
+            int issued = 0;
+            for (int kb = 0; kb < KB; kb++) {
+                const int s = kb % STAGES;
+                const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+                if (!mbar_wait_bounded(&empty[s], ph ^ 1u, abort, kWaitLimitNs, 0)) break;
+                mbar_arrive_expect_tx(&full[s], kStage);
+                uint8_t* st = smem + s * kStage;
+                const uint32_t fb = saddr(&full[s]);
+                const int kx = kb * kKPerStage;
+#pragma unroll
+                for (int part = 0; part < 2; part++)
+#pragma unroll
+                    for (int a = 0; a < S; a++)
+                        tma_load_3d(saddr(st + (part * S + a) * kATile), &tmU, fb, kx, I * 128, part * S + a);
+#pragma unroll
+                for (int b = 0; b < S; b++) {
+                    uint8_t* bt = st + 2 * S * kATile + b * kBTile;
+                    tma_load_3d(saddr(bt), &tmP, fb, kx, J * 128, b);                   // P_r part b
+                    tma_load_3d(saddr(bt + 128 * kRowBytes), &tmP, fb, kx, J * 128, S + b);   // P_i part b
+                }
+                issued = kb + 1;
+            }
+            if (*abort) {
+                // let the copies already issued land before the CTA goes away
+                for (int kb = issued - STAGES > 0 ? issued - STAGES : 0; kb < issued; kb++)
+                    (void)mbar_wait_bounded(&full[kb % STAGES], (uint32_t)(kb / STAGES) & 1u, nullptr,
+                                            kWaitLimitNs, 0);
+            }
+        }
+    } else if (warp == 5) {
+        // ---------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            for (int kb = 0; kb < KB; kb++) {
+                const int s = kb % STAGES;
+                const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+                if (!mbar_wait_bounded(&full[s], ph, abort, kWaitLimitNs, 0)) break;
+                tc_fence_after();
+                uint8_t* st = smem + s * kStage;
+#pragma unroll
+                for (int p = 0; p < Pairs<S>::n; p++) {
+                    const uint64_t bd = desc_kmajor_sw32(saddr(st + 2 * S * kATile + Pairs<S>::b(p) * kBTile));
+#pragma unroll
+                    for (int part = 0; part < 2; part++) {
+                        const uint64_t ad = desc_kmajor_sw32(saddr(st + (part * S + Pairs<S>::a(p)) * kATile));
+                        umma<KIND>(tmem + part * 256, ad, bd, kIdesc, (kb > 0 || p > 0) ? 1u : 0u);
+                    }
+                }
+                umma_commit(saddr(&empty[s]));
+            }
+            // always: completes when every MMA issued above has finished
+            umma_commit(saddr(accum));
+        }
+    } else {
+        // ---------------------------------------------------------- epilogue
+        const bool ok = mbar_wait_bounded(accum, 0u, abort, kWaitLimitNs, 128);
+        tc_fence_after();
+        if (ok && !*abort) {
+            const int row = warp * 32 + lane;                  // TMEM lane = row i of the tile
+            const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+            const size_t Np = (size_t)ep.Np;
+            const size_t plane = Np * Np;
+            const size_t gi = (size_t)I * 128 + row;
+            T* parts = reinterpret_cast<T*>(ep.parts);
+            const bool diag = (MODE == 1) && (I == J);
+#pragma unroll 1
+            for (int c = 0; c < 128; c += 16) {
+                float d1r[16], d1i[16], d2r[16], d2i[16];
+                tmem_ld16(tl + c, d1r);            // U_r P_r^T
+                tmem_ld16(tl + 128 + c, d1i);      // U_r P_i^T
+                tmem_ld16(tl + 256 + c, d2r);      // U_i P_r^T
+                tmem_ld16(tl + 384 + c, d2i);      // U_i P_i^T
+                tmem_wait_ld();
+                float yr[16], yi[16];
+#pragma unroll
+                for (int q = 0; q < 16; q++) {
+                    yr[q] = d1r[q] + d2i[q];
+                    yi[q] = d2r[q] - d1i[q];
+                }
+                const size_t gj0 = (size_t)J * 128 + c;
+                if (MODE == 0 || !diag) {
+                    // direct tile, full rows of 16: parts (and FP32 planes in mode 1)
+                    T pr[S][16], pi[S][16];
+#pragma unroll
+                    for (int q = 0; q < 16; q++) {
+                        T a[S], b[S];
+                        P::split(yr[q], a);
+                        P::split(yi[q], b);
+#pragma unroll
+                        for (int s = 0; s < S; s++) { pr[s][q] = a[s]; pi[s][q] = b[s]; }
+                    }
+#pragma unroll
+                    for (int s = 0; s < S; s++) {
+                        store16(parts + (size_t)s * plane + gi * Np + gj0, pr[s]);
+                        store16(parts + (size_t)(S + s) * plane + gi * Np + gj0, pi[s]);
+                    }
+                    if (MODE == 1) {
+                        store16(ep.yr + gi * Np + gj0, yr);
+                        store16(ep.yi + gi * Np + gj0, yi);
+                    }
+                }
+                if (MODE == 1) {
+#pragma unroll
+                    for (int q = 0; q < 16; q++) {
+                        const int col = c + q;
+                        const size_t gj = gj0 + q;
+                        if (diag) {
+                            if (col > row) continue;
+                            float vr = yr[q], vi = (col == row) ? 0.0f : yi[q];
+                            T a[S], b[S];
+                            P::split(vr, a);
+                            P::split(vi, b);
+                            for (int s = 0; s < S; s++) {
+                                parts[(size_t)s * plane + gi * Np + gj] = a[s];
+                                parts[(size_t)(S + s) * plane + gi * Np + gj] = b[s];
+                            }
+                            ep.yr[gi * Np + gj] = vr;
+                            ep.yi[gi * Np + gj] = vi;
+                            if (col == row) continue;
+                        }
+                        // mirror: rho'[j][i] = conj(rho'[i][j]); lanes write consecutive i
+                        T a[S], b[S];
+                        P::split(yr[q], a);
+                        P::split(-yi[q], b);
+#pragma unroll
+                        for (int s = 0; s < S; s++) {
+                            parts[(size_t)s * plane + gj * Np + gi] = a[s];
+                            parts[(size_t)(S + s) * plane + gj * Np + gi] = b[s];
+                        }
+                        ep.yr[gj * Np + gi] = yr[q];
+                        ep.yi[gj * Np + gi] = -yi[q];
+                    }
+                }
+            }
+        }
+        if (!ok || *abort) {
+            if (threadIdx.x == 0) atomicOr(ep.status, kStatusTimeout);
+        }
+    }
+
+    __syncwarp();
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 512);
+    }
+}
+
+template <int KIND, int S, int STAGES>
+constexpr int smem_bytes() {
+    return STAGES * (2 * S * kATile + S * kBTile) + 1024 /*align*/ + 256 /*barriers*/;
+}
+
+template <int KIND, int S, int STAGES, int MODE>
+tc_status launch(const CUtensorMap& tmU, const CUtensorMap& tmP, const CgemmEpi& ep, cudaStream_t s) {
+    auto k = cgemm_tc_kernel<KIND, S, STAGES, MODE>;
+    constexpr int smem = smem_bytes<KIND, S, STAGES>();
+    static bool attr_set[64] = {};   // per device; set before the first launch there
+    int dev = 0;
+    TC_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(TC_ERR_UNSUPPORTED_DEVICE, "device index out of range");
+    if (!attr_set[dev]) {
+        TC_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        attr_set[dev] = true;
+    }
+    const int T = ep.tiles;
+    const unsigned grid = MODE == 0 ? (unsigned)(T * T) : (unsigned)(T * (T + 1) / 2);
+    k<<<grid, kThreads, smem, s>>>(tmU, tmP, ep);
+    TC_LAUNCH_CHECK();
+    return TC_OK;
+}
+
+}  // namespace
+
+tc_status cgemm_tc(int precision, int mode, const CUtensorMap& tmU, const CUtensorMap& tmP, const CgemmEpi& ep,
+                   cudaStream_t s) {
+    if (ep.Np < 128 || ep.Np % 128 != 0 || ep.tiles * 128 != ep.Np)
+        return fail(TC_ERR_INVALID_ARG, "cgemm_tc: padded dimension must be a multiple of 128");
+    if (mode != 0 && mode != 1) return fail(TC_ERR_INVALID_ARG, "cgemm_tc: mode");
+    switch (precision) {
+        case TC_BF16X3:
+            return mode == 0 ? launch<0, 3, 4, 0>(tmU, tmP, ep, s) : launch<0, 3, 4, 1>(tmU, tmP, ep, s);
+        case TC_TF32:
+            return mode == 0 ? launch<1, 1, 8, 0>(tmU, tmP, ep, s) : launch<1, 1, 8, 1>(tmU, tmP, ep, s);
+        case TC_TF32X3:
+            return mode == 0 ? launch<1, 2, 6, 0>(tmU, tmP, ep, s) : launch<1, 2, 6, 1>(tmU, tmP, ep, s);
+        default:
+            return fail(TC_ERR_INVALID_ARG, "cgemm_tc: precision %d has no tensor-core form", precision);
+    }
+}
+
+int cgemm_parts(int precision) {
+    return precision == TC_BF16X3 ? 3 : precision == TC_TF32X3 ? 2 : 1;
+}
+
+int cgemm_products(int precision) {
+    return precision == TC_BF16X3 ? 6 : precision == TC_TF32X3 ? 3 : 1;
+}
+
+size_t cgemm_elem_bytes(int precision) { return precision == TC_BF16X3 ? 2 : 4; }
+
+}  // namespace tc

@@ -1,0 +1,35 @@
+// cgemm_tc.cuh -- tensor-core complex GEMM Y = U P^H of the low-precision
+// step (see cgemm_tc.cu) and the TMA descriptors of its operand planes.
+#pragma once
+
+#include <cuda.h>
+
+#include "common.cuh"
+
+namespace tc {
+
+// Output side of one launch.
+//   mode 0: Y written as operand parts only (the X = U rho of a step).
+//   mode 1: Y Hermitian (rho' = U X^H): block-lower tiles computed, the
+//           conjugate transpose mirrored; FP32 planes and parts written.
+struct CgemmEpi {
+    int Np;          // padded dimension, a multiple of 128 (row stride of every plane)
+    int tiles;       // Np / 128
+    void* parts;     // [2 * S][Np][Np] operand parts: re parts 0..S-1, then im parts
+    float* yr;       // mode 1: FP32 real plane [Np][Np]
+    float* yi;       // mode 1: FP32 imaginary plane [Np][Np]
+    unsigned* status;
+};
+
+tc_status cgemm_tc(int precision, int mode, const CUtensorMap& tmU, const CUtensorMap& tmP, const CgemmEpi& ep,
+                   cudaStream_t s);
+
+int cgemm_parts(int precision);       // S: BF16x3 3, TF32x3 2, TF32 1
+int cgemm_products(int precision);    // part products per real product: 6, 3, 1
+size_t cgemm_elem_bytes(int precision);
+
+// 3-D tensor map over `planes` consecutive Np x Np planes of operand parts:
+// box = 32 bytes of K x 128 rows x 1 plane, 32-byte swizzle.
+tc_status make_part_map(CUtensorMap* map, const void* base, int Np, int planes, int precision);
+
+}  // namespace tc

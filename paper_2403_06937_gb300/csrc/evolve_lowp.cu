@@ -1,19 +1,280 @@
-// evolve_lowp.cu -- placeholder until the tcgen05 path lands.
+// evolve_lowp.cu -- the low-precision forms of the step loop
+// rho <- U rho U^dag (Sec. III.A, Eqs. 6, 12) on the tcgen05 tensor cores.
+//
+// U arrives in FP64 (from tc_expm) and is split once per call into operand
+// parts (BF16x3: three BF16 parts, computed in FP64; TF32x3: big/small TF32;
+// TF32: one TF32 part).  rho lives in FP32 planes between steps plus the
+// operand parts of those FP32 values; X = U rho lives only as operand parts.
+// Each step is two launches of the tensor-core GEMM Y = U P^H:
+//     X    = U rho^H  (all tiles; writes the parts of X)
+//     rho' = U X^H    (block-lower tiles + mirror; writes FP32 planes and parts)
+// then, every `renorm_every` steps, rho <- rho / Tr rho with the trace in
+// FP64, and the observable row from the FP32 planes.
+// Dimensions below 128 (n < 7) are zero-padded to one 128 x 128 tile: the
+// padded rows and columns of U and rho are zero and stay zero.
+#include <cuda_bf16.h>
+
+#include "cgemm_tc.cuh"
 #include "paths.cuh"
+#include "timing.cuh"
 
 namespace tc {
+namespace {
 
-size_t evolve_lowp_bytes(int n, int precision) { (void)n; (void)precision; return 0; }
-
-tc_status evolve_lowp(const double*, double*, int, int, int, int, const Model*, double*, Arena&, cudaStream_t) {
-    return fail(TC_ERR_INVALID_ARG, "low-precision evolution is not built yet");
+unsigned grid_for(size_t work) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    size_t want = (work + 255) / 256;
+    size_t cap = (size_t)sms * 16;
+    return (unsigned)(want < cap ? (want ? want : 1) : cap);
 }
 
-size_t backward_bytes(int n, int steps, int ckpt_every) { (void)n; (void)steps; (void)ckpt_every; return 0; }
+__device__ __forceinline__ float tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// parts of a double (U): the split is taken in FP64
+template <int KIND, int S>
+__device__ __forceinline__ void split_f64(double v, void* base, size_t plane, size_t idx, int part) {
+    if constexpr (KIND == 0) {
+        __nv_bfloat16* p = static_cast<__nv_bfloat16*>(base);
+        double r = v;
+#pragma unroll
+        for (int s = 0; s < S; s++) {
+            __nv_bfloat16 b = __double2bfloat16(r);
+            p[(size_t)(part * S + s) * plane + idx] = b;
+            r -= (double)__bfloat162float(b);
+        }
+    } else {
+        float* p = static_cast<float*>(base);
+        double r = v;
+#pragma unroll
+        for (int s = 0; s < S; s++) {
+            float t = tf32_rna((float)r);
+            p[(size_t)(part * S + s) * plane + idx] = t;
+            r -= (double)t;
+        }
+    }
+}
+
+// parts of an FP32 value (rho): the split is taken in FP32
+template <int KIND, int S>
+__device__ __forceinline__ void split_f32(float v, void* base, size_t plane, size_t idx, int part) {
+    if constexpr (KIND == 0) {
+        __nv_bfloat16* p = static_cast<__nv_bfloat16*>(base);
+        float r = v;
+#pragma unroll
+        for (int s = 0; s < S; s++) {
+            __nv_bfloat16 b = __float2bfloat16_rn(r);
+            p[(size_t)(part * S + s) * plane + idx] = b;
+            r -= __bfloat162float(b);
+        }
+    } else {
+        float* p = static_cast<float*>(base);
+        float r = v;
+#pragma unroll
+        for (int s = 0; s < S; s++) {
+            float t = tf32_rna(r);
+            p[(size_t)(part * S + s) * plane + idx] = t;
+            r -= t;
+        }
+    }
+}
+
+template <int KIND, int S>
+__global__ void prep_u_kernel(const double2* U, int N, int Np, void* parts) {
+    const size_t plane = (size_t)Np * Np;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < plane; e += (size_t)gridDim.x * blockDim.x) {
+        const size_t i = e / Np, j = e % Np;
+        double2 u = make_double2(0.0, 0.0);
+        if (i < (size_t)N && j < (size_t)N) u = U[i * N + j];
+        split_f64<KIND, S>(u.x, parts, plane, e, 0);
+        split_f64<KIND, S>(u.y, parts, plane, e, 1);
+    }
+}
+
+template <int KIND, int S>
+__global__ void prep_rho_kernel(const double2* rho, int N, int Np, float* Rr, float* Ri, void* parts) {
+    const size_t plane = (size_t)Np * Np;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < plane; e += (size_t)gridDim.x * blockDim.x) {
+        const size_t i = e / Np, j = e % Np;
+        double2 v = make_double2(0.0, 0.0);
+        if (i < (size_t)N && j < (size_t)N) v = rho[i * N + j];
+        const float fr = (float)v.x, fi = (float)v.y;
+        Rr[e] = fr;
+        Ri[e] = fi;
+        split_f32<KIND, S>(fr, parts, plane, e, 0);
+        split_f32<KIND, S>(fi, parts, plane, e, 1);
+    }
+}
+
+// rho <- rho / trace (trace read on the device; skipped and flagged if not positive finite),
+// then the operand parts are rebuilt from the rescaled FP32 values.
+template <int KIND, int S>
+__global__ void rescale_resplit_kernel(float* Rr, float* Ri, int Np, void* parts, const double* trace,
+                                       unsigned* status) {
+    const double tr = trace[0];
+    if (!(tr > 0.0) || !isfinite(tr)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, kStatusNumeric);
+        return;
+    }
+    const double inv = 1.0 / tr;
+    const size_t plane = (size_t)Np * Np;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < plane; e += (size_t)gridDim.x * blockDim.x) {
+        const float fr = (float)((double)Rr[e] * inv), fi = (float)((double)Ri[e] * inv);
+        Rr[e] = fr;
+        Ri[e] = fi;
+        split_f32<KIND, S>(fr, parts, plane, e, 0);
+        split_f32<KIND, S>(fi, parts, plane, e, 1);
+    }
+}
+
+__global__ void trace_f32_kernel(const float* Rr, int N, int Np, double* out) {
+    __shared__ double s[1024];
+    double a = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) a += (double)Rr[(size_t)i * Np + i];
+    s[threadIdx.x] = a;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = s[0];
+}
+
+__global__ void finish_kernel(const float* Rr, const float* Ri, int N, int Np, double2* rho) {
+    const size_t count = (size_t)N * N;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x) {
+        const size_t i = e / N, j = e % N;
+        rho[e] = make_double2((double)Rr[i * Np + j], (double)Ri[i * Np + j]);
+    }
+}
+
+struct LowpBufs {
+    int N, Np, S;
+    size_t E;
+    void* Uparts;
+    float* Rr;
+    float* Ri;
+    void* Rparts;
+    void* Xparts;
+    double* scratch;
+};
+
+size_t plane_bytes(int Np, size_t E) { return round256((size_t)Np * Np * E); }
+
+template <int KIND, int S>
+tc_status run_prep(const double* U, const double* rho, LowpBufs& b, cudaStream_t s) {
+    const size_t plane = (size_t)b.Np * b.Np;
+    prep_u_kernel<KIND, S><<<grid_for(plane), 256, 0, s>>>(reinterpret_cast<const double2*>(U), b.N, b.Np, b.Uparts);
+    TC_LAUNCH_CHECK();
+    prep_rho_kernel<KIND, S><<<grid_for(plane), 256, 0, s>>>(reinterpret_cast<const double2*>(rho), b.N, b.Np, b.Rr,
+                                                               b.Ri, b.Rparts);
+    TC_LAUNCH_CHECK();
+    return TC_OK;
+}
+
+template <int KIND, int S>
+tc_status run_renorm(LowpBufs& b, cudaStream_t s) {
+    trace_f32_kernel<<<1, 1024, 0, s>>>(b.Rr, b.N, b.Np, b.scratch);
+    TC_LAUNCH_CHECK();
+    rescale_resplit_kernel<KIND, S><<<grid_for((size_t)b.Np * b.Np), 256, 0, s>>>(b.Rr, b.Ri, b.Np, b.Rparts, b.scratch,
+                                                                                  device_status_word());
+    TC_LAUNCH_CHECK();
+    return TC_OK;
+}
+
+tc_status prep(int precision, const double* U, const double* rho, LowpBufs& b, cudaStream_t s) {
+    switch (precision) {
+        case TC_BF16X3: return run_prep<0, 3>(U, rho, b, s);
+        case TC_TF32: return run_prep<1, 1>(U, rho, b, s);
+        case TC_TF32X3: return run_prep<1, 2>(U, rho, b, s);
+    }
+    return fail(TC_ERR_INVALID_ARG, "precision");
+}
+
+tc_status renorm(int precision, LowpBufs& b, cudaStream_t s) {
+    switch (precision) {
+        case TC_BF16X3: return run_renorm<0, 3>(b, s);
+        case TC_TF32: return run_renorm<1, 1>(b, s);
+        case TC_TF32X3: return run_renorm<1, 2>(b, s);
+    }
+    return fail(TC_ERR_INVALID_ARG, "precision");
+}
+
+}  // namespace
+
+size_t evolve_lowp_bytes(int n, int precision) {
+    if (precision != TC_BF16X3 && precision != TC_TF32 && precision != TC_TF32X3) return 0;
+    const int N = 1 << n;
+    const int Np = N < 128 ? 128 : N;
+    const int S = cgemm_parts(precision);
+    const size_t E = cgemm_elem_bytes(precision);
+    return 3 * (size_t)(2 * S) * plane_bytes(Np, E) + 2 * plane_bytes(Np, 4) + observables_scratch_bytes(n) + 512;
+}
+
+tc_status evolve_lowp(const double* U, double* rho, int n, int steps, int precision, int renorm_every,
+                      const Model* m, double* obs, Arena& ar, cudaStream_t s) {
+    LowpBufs b{};
+    b.N = 1 << n;
+    b.Np = b.N < 128 ? 128 : b.N;
+    b.S = cgemm_parts(precision);
+    b.E = cgemm_elem_bytes(precision);
+    const size_t pl = (size_t)b.Np * b.Np;
+    auto take_planes = [&](int planes, size_t E) -> void* {
+        return ar.take<uint8_t>((size_t)planes * plane_bytes(b.Np, E));
+    };
+    b.Uparts = take_planes(2 * b.S, b.E);
+    b.Rparts = take_planes(2 * b.S, b.E);
+    b.Xparts = take_planes(2 * b.S, b.E);
+    b.Rr = static_cast<float*>(take_planes(1, 4));
+    b.Ri = static_cast<float*>(take_planes(1, 4));
+    b.scratch = ar.take<double>(observables_scratch_bytes(n) / sizeof(double));
+    if (!b.scratch) return fail(TC_ERR_WORKSPACE, "evolve: workspace too small");
+    // plane_bytes rounds each plane to 256 B; for Np >= 128 the planes are exactly Np*Np*E
+    if (plane_bytes(b.Np, b.E) != pl * b.E) return fail(TC_ERR_INVALID_ARG, "evolve: plane size");
+
+    CUtensorMap tmU, tmR, tmX;
+    TC_TRY(make_part_map(&tmU, b.Uparts, b.Np, 2 * b.S, precision));
+    TC_TRY(make_part_map(&tmR, b.Rparts, b.Np, 2 * b.S, precision));
+    TC_TRY(make_part_map(&tmX, b.Xparts, b.Np, 2 * b.S, precision));
+
+    CgemmEpi e1{};
+    e1.Np = b.Np;
+    e1.tiles = b.Np / 128;
+    e1.parts = b.Xparts;
+    e1.status = device_status_word();
+    CgemmEpi e2 = e1;
+    e2.parts = b.Rparts;
+    e2.yr = b.Rr;
+    e2.yi = b.Ri;
+
+    const int stride = TC_OBS_STRIDE(n);
+    const double N3 = (double)b.N * b.N * b.N;
+    const double prod = (double)cgemm_products(precision);
+
+    TC_TRY(prep(precision, U, rho, b, s));
+    if (obs) TC_TRY(launch_observables(kRhoPlanarF32, b.Rr, b.Ri, m, n, obs, b.scratch, s, (size_t)b.Np));
+    for (int k = 1; k <= steps; k++) {
+        {
+            ProductTimer t(8.0 * N3 * prod, s);
+            TC_TRY(cgemm_tc(precision, 0, tmU, tmR, e1, s));
+        }
+        {
+            ProductTimer t(4.0 * N3 * prod, s);
+            TC_TRY(cgemm_tc(precision, 1, tmU, tmX, e2, s));
+        }
+        if (renorm_every > 0 && k % renorm_every == 0) TC_TRY(renorm(precision, b, s));
+        if (obs)
+            TC_TRY(launch_observables(kRhoPlanarF32, b.Rr, b.Ri, m, n, obs + (size_t)k * stride, b.scratch, s,
+                                      (size_t)b.Np));
+    }
+    finish_kernel<<<grid_for((size_t)b.N * b.N), 256, 0, s>>>(b.Rr, b.Ri, b.N, b.Np, reinterpret_cast<double2*>(rho));
+    TC_LAUNCH_CHECK();
+    return TC_OK;
+}
 
 }  // namespace tc
-
-extern "C" TC_API tc_status tc_evolve_backward(const tc_params*, double, int, const void*, const void*, int,
-                                               const double*, double*, double*, void*, size_t, void*) {
-    return tc::fail(TC_ERR_INVALID_ARG, "tc_evolve_backward is not built yet");
-}

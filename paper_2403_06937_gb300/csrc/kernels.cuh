@@ -52,8 +52,9 @@ tc_status matrix_trace_and_norm1(int N, const double* H, double mu_for_norm, dou
 // Deterministic observable row of a density matrix in one of three layouts.
 enum RhoLayout { kRhoInterleaved = 0, kRhoPlanarF64 = 1, kRhoPlanarF32 = 2 };
 size_t observables_scratch_bytes(int n);
+// ld: row stride in elements (0 = N).
 tc_status launch_observables(int layout, const void* re_or_c128, const void* im, const Model* m,
-                             int n, double* out, double* scratch, cudaStream_t s);
+                             int n, double* out, double* scratch, cudaStream_t s, size_t ld = 0);
 // rho <- rho / Tr rho with the trace taken in FP64 from the planar diagonal.
 tc_status launch_renormalise(int layout, void* re, void* im, int n, double* scratch, cudaStream_t s);
 

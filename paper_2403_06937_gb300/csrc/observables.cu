@@ -31,6 +31,7 @@ template <int L>
 struct Rho {
     const void* a;
     const void* b;
+    size_t ld;   // row stride in elements
     __device__ __forceinline__ double re(size_t i) const {
         if (L == kRhoInterleaved) return static_cast<const double*>(a)[2 * i];
         if (L == kRhoPlanarF64) return static_cast<const double*>(a)[i];
@@ -53,7 +54,7 @@ __global__ void obs_partial_kernel(Rho<L> rho, Model m, int has_model, int n, do
     const unsigned N = 1u << n;
     double pur = 0.0, epair = 0.0;
     for (unsigned r = blockIdx.x * kObsWarps + warp; r < N; r += gridDim.x * kObsWarps) {
-        const size_t row = (size_t)r * N;
+        const size_t row = (size_t)r * rho.ld;
         for (unsigned c = lane; c < N; c += 32) {
             double x = rho.re(row + c), y = rho.im(row + c);
             pur += x * x + y * y;
@@ -66,7 +67,7 @@ __global__ void obs_partial_kernel(Rho<L> rho, Model m, int has_model, int n, do
                 double h = m.coupling == TC_COUPLING_QUBIT_PHOTON
                                ? m.g[lane]
                                : m.g[lane] * sqrt((double)(n - __popc(r) + 1));
-                epair += h * (rho.re(row + sg) + rho.re((size_t)sg * N + r));
+                epair += h * (rho.re(row + sg) + rho.re((size_t)sg * rho.ld + r));
             }
         }
         if (lane == 0) {
@@ -141,7 +142,8 @@ size_t observables_scratch_bytes(int n) {
 }
 
 tc_status launch_observables(int layout, const void* a, const void* b, const Model* m, int n,
-                             double* out, double* scratch, cudaStream_t s) {
+                             double* out, double* scratch, cudaStream_t s, size_t ld) {
+    if (ld == 0) ld = (size_t)1 << n;
     unsigned grid = obs_grid(n);
     Model mm{};
     int has = 0;
@@ -152,13 +154,13 @@ tc_status launch_observables(int layout, const void* a, const void* b, const Mod
     mm.n = n;
     switch (layout) {
         case kRhoInterleaved:
-            obs_partial_kernel<kRhoInterleaved><<<grid, 32 * kObsWarps, 0, s>>>(Rho<kRhoInterleaved>{a, b}, mm, has, n, scratch);
+            obs_partial_kernel<kRhoInterleaved><<<grid, 32 * kObsWarps, 0, s>>>(Rho<kRhoInterleaved>{a, b, ld}, mm, has, n, scratch);
             break;
         case kRhoPlanarF64:
-            obs_partial_kernel<kRhoPlanarF64><<<grid, 32 * kObsWarps, 0, s>>>(Rho<kRhoPlanarF64>{a, b}, mm, has, n, scratch);
+            obs_partial_kernel<kRhoPlanarF64><<<grid, 32 * kObsWarps, 0, s>>>(Rho<kRhoPlanarF64>{a, b, ld}, mm, has, n, scratch);
             break;
         case kRhoPlanarF32:
-            obs_partial_kernel<kRhoPlanarF32><<<grid, 32 * kObsWarps, 0, s>>>(Rho<kRhoPlanarF32>{a, b}, mm, has, n, scratch);
+            obs_partial_kernel<kRhoPlanarF32><<<grid, 32 * kObsWarps, 0, s>>>(Rho<kRhoPlanarF32>{a, b, ld}, mm, has, n, scratch);
             break;
         default:
             return fail(TC_ERR_INVALID_ARG, "observables: unknown layout");
