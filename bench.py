@@ -53,6 +53,7 @@ def _args():
     ap.add_argument("--workload", choices=["n14", "n12", "n8"], default="n14")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="skip the TF32 / TF32x3 / FP64 comparison forms")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     return ap.parse_args()
 
@@ -212,6 +213,42 @@ def run_reference(a, cfg):
 
 
 # ------------------------------------------------------------------ our arm
+def _time_form(tc, torch, U, n, params, prec, steps, warmup, renorm, stream, with_clocks=None):
+    """W untimed steps, then K steps of one tc_evolve call timed with CUDA events."""
+    N = 1 << n
+    rho = torch.zeros((N, N), dtype=torch.complex128, device="cuda")
+    rho[N - 1, N - 1] = 1.0
+    work = torch.empty(tc.workspace_size(n, tc.PRECISIONS[prec], tc.TC_OP_EVOLVE), dtype=torch.uint8, device="cuda")
+    if warmup:
+        rho, _ = tc.evolve(U, rho, n, warmup, prec, renorm_every=renorm, params=params, inplace=True, work=work)
+        tc.sync_status()
+    torch.cuda.synchronize()
+    tc.timing_read()
+    tc.timing_enable(True)
+    launches0 = tc.launch_count()
+    if with_clocks is not None:
+        with_clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    rho, obs = tc.evolve(U, rho, n, steps, prec, renorm_every=renorm, params=params, inplace=True, work=work)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ck = with_clocks.stop() if with_clocks is not None else None
+    tc.timing_enable(False)
+    launches = tc.launch_count() - launches0
+    tc.sync_status()
+    ms = e0.elapsed_time(e1)
+    klaunch, kms, kflops = tc.timing_read()
+    o = obs.cpu().numpy()
+    drift = {"kind": "conserved quantities after %d steps (oracle-free)" % (warmup + steps),
+             "trace": float(abs(o[-1, 2 * n + 2] - 1.0)),
+             "purity": float(abs(o[-1, 2 * n + 3] - 1.0)),
+             "energy_rel": float(abs(o[-1, 2 * n + 4] - o[0, 2 * n + 4]) / abs(o[0, 2 * n + 4]))}
+    del work, rho
+    return {"ms": ms, "launches": launches, "klaunch": klaunch, "kms": kms, "kflops": kflops, "clocks": ck,
+            "drift": drift}
+
+
 def run_ours(a, cfg):
     import torch
 
@@ -234,86 +271,79 @@ def run_ours(a, cfg):
     del H
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t_setup
-    rho = torch.zeros((N, N), dtype=torch.complex128, device="cuda")
-    rho[N - 1, N - 1] = 1.0
-    renorm = cfg.renorm_every if prec != "fp64" else 0
-    work = torch.empty(tc.workspace_size(n, tc.PRECISIONS[prec], tc.TC_OP_EVOLVE), dtype=torch.uint8, device="cuda")
+    renorm = cfg.renorm_every
     stream = torch.cuda.current_stream()
+    credited = 12.0 * N ** 3
+    peaks, peak_src = _measured_peaks()
 
-    # warm-up (untimed)
-    rho, _ = tc.evolve(U, rho, n, a.warmup, prec, renorm_every=renorm, params=params, inplace=True, work=work)
-    tc.sync_status()
+    def peak_of(p, fp64_peak=None):
+        if p == "fp64":
+            return fp64_peak, "FP64: cuBLAS DGEMM 4096^3 measured live in this run (torch.matmul float64)"
+        if p in ("tf32", "tf32x3"):
+            return peaks["bf16_tflops_sustained"] / 2.0, \
+                "TF32: %s bf16_tflops_sustained x 1/2 (nominal tf32:bf16 ratio)" % peak_src
+        return peaks["bf16_tflops_sustained"], "BF16: %s bf16_tflops_sustained (kernel timed inside a long step)" % peak_src
 
-    fp64_peak = _fp64_peak_live(torch) if prec == "fp64" else None
+    fp64_peak = _fp64_peak_live(torch) if (prec == "fp64" or not a.no_compare) else None
     clocks = Clocks(local)
     if world > 1:
         torch.distributed.barrier()
-    torch.cuda.synchronize()
-    tc.timing_read()
-    tc.timing_enable(True)
-    launches0 = tc.launch_count()
-    clocks.start()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    rho, obs = tc.evolve(U, rho, n, a.steps, prec, renorm_every=renorm, params=params, inplace=True, work=work)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ck = clocks.stop()
-    tc.timing_enable(False)
-    launches = tc.launch_count() - launches0
-    tc.sync_status()
-    ms = e0.elapsed_time(e1)
+    r = _time_form(tc, torch, U, n, params, prec, a.steps, a.warmup, renorm if prec != "fp64" else 0, stream,
+                   with_clocks=clocks)
+    ms = r["ms"]
     if world > 1:
         t = torch.tensor([ms], device="cuda", dtype=torch.float64)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
-    klaunch, kms, kflops = tc.timing_read()
     value = world * a.steps / (ms * 1e-3)
-    credited = 12.0 * N ** 3
-    products = {"fp64": 1, "bf16x3": 6, "tf32": 1, "tf32x3": 3}[prec]
-
-    peaks, peak_src = _measured_peaks()
-    if prec == "fp64":
-        peak = fp64_peak
-        peak_note = "FP64: cuBLAS DGEMM 4096^3 measured live in this run (torch.matmul float64)"
-    elif prec in ("tf32", "tf32x3"):
-        peak = peaks["bf16_tflops_sustained"] / 2.0
-        peak_note = "TF32: %s bf16_tflops_sustained x 1/2 (nominal tf32:bf16 ratio)" % peak_src
-    else:
-        peak = peaks["bf16_tflops_sustained"]
-        peak_note = "BF16: %s bf16_tflops_sustained (kernel timed inside a long step)" % peak_src
-    achieved = kflops / (kms * 1e-3) / 1e12 if kms > 0 else 0.0
-    o = obs.cpu().numpy()
+    peak, peak_note = peak_of(prec, fp64_peak)
+    achieved = r["kflops"] / (r["kms"] * 1e-3) / 1e12 if r["kms"] > 0 else 0.0
     roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak if peak else None, "traffic": NCU_TRAFFIC.get((prec, n)),
-            "kernel": "complex GEMM (%s), %d launches timed, %.3f ms avg" % (prec, klaunch, kms / max(klaunch, 1)),
+            "kernel": "complex GEMM (%s), %d launches timed, %.3f ms avg" % (prec, r["klaunch"],
+                                                                             r["kms"] / max(r["klaunch"], 1)),
             "peak_source": peak_note,
-            "algorithmic_flops_per_launch_avg": kflops / max(klaunch, 1)}
-
+            "algorithmic_flops_per_launch_avg": r["kflops"] / max(r["klaunch"], 1)}
     line = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp64": "f64", "bf16x3": "bf16", "tf32": "tf32", "tf32x3": "tf32"}[prec],
         "data": "synthetic",
         "config": {"workload": cfg.description, "precision": prec, "dim": N,
-                   "products_per_complex_product": products,
+                   "products_per_complex_product": {"fp64": 1, "bf16x3": 6, "tf32": 1, "tf32x3": 3}[prec],
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (U and rho are %d MiB each in complex128)" % (16 * N * N >> 20),
                    "setup_s": t_setup},
         "credited_tflops": credited * value / world / 1e12,
         "credited_flops_per_step": credited,
         "roofline": roof,
-        "clocks": ck,
-        "gpu_launches": launches,
-        "trace_final": float(o[-1, 2 * n + 2]),
-        "purity_final": float(o[-1, 2 * n + 3]),
+        "clocks": r["clocks"],
+        "gpu_launches": r["launches"],
+        "error": r["drift"],
     }
+
+    if not a.no_compare:
+        # the other forms on the same workload: split-TF32, TF32 and one FP64 step
+        others = {}
+        for p2, k2, w2 in (("tf32x3", a.steps, a.warmup), ("tf32", a.steps, a.warmup), ("fp64", 1, 0)):
+            if p2 == prec:
+                continue
+            r2 = _time_form(tc, torch, U, n, params, p2, k2, w2, renorm if p2 != "fp64" else 0, stream)
+            v2 = k2 / (r2["ms"] * 1e-3)
+            pk, _ = peak_of(p2, fp64_peak)
+            ach = r2["kflops"] / (r2["kms"] * 1e-3) / 1e12 if r2["kms"] > 0 else 0.0
+            others[p2] = {"value": v2, "unit": "steps/s", "steps": k2, "warmup": w2,
+                          "credited_tflops": credited * v2 / 1e12, "achieved_tflops": ach, "peak": pk,
+                          "frac": ach / pk if pk else None, "error": r2["drift"]}
+        line["other_forms"] = others
+        if "fp64" in others:
+            line["speedup_vs_fp64"] = (value / world) / others["fp64"]["value"]
 
     if not a.no_e2e:
         # end to end through the public C ABI call with host buffers: every step copies
         # rho (pinned host) in, runs one step, copies rho and the observable rows back.
-        rho_h = torch.empty((N, N), dtype=torch.complex128, pin_memory=True)
-        rho_h.copy_(rho)
+        rho_h = torch.zeros((N, N), dtype=torch.complex128, pin_memory=True)
+        rho_h[N - 1, N - 1] = 1.0
         obs_h = torch.empty((2, 2 * n + 5), dtype=torch.float64, pin_memory=True)
         hw = torch.empty(tc.workspace_size(n, tc.PRECISIONS[prec], 16, 1), dtype=torch.uint8, device="cuda")
         tc.evolve_host(U, rho_h, n, 1, prec, params=params, obs_host=obs_h, work=hw)   # warm

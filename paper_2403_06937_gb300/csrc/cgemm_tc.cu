@@ -17,6 +17,13 @@
 //     D2 = U_i [P_r; P_i]^T = [U_i P_r^T | U_i P_i^T]
 // and the epilogue forms Y_r = U_r P_r^T + U_i P_i^T, Y_i = U_i P_r^T - U_r P_i^T.
 //
+// Increment form: the operand is V = U / c - I (c = Tr U / |Tr U|, a unit
+// phase that cancels in U rho U^dag), and the epilogue adds the identity
+// term P^H exactly in FP32.  The tensor cores then only accumulate V P^H,
+// of size ||V|| |P| (a few hundredths here), so the truncation of their FP32
+// accumulation (round toward zero, a systematic shrink of every running sum)
+// is scaled down by ||V|| instead of acting on sums of size |P|.
+//
 // Precision forms: every FP32 (or FP64) operand x is held as S parts
 // (BF16x3: three BF16 parts x0 + x1 + x2; TF32: one TF32 part; TF32x3: a
 // big and a small TF32 part) and the product of two split operands is the
@@ -244,13 +251,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tmem_ld16(tl + 256 + c, d2r);      // U_i P_r^T
                 tmem_ld16(tl + 384 + c, d2i);      // U_i P_i^T
                 tmem_wait_ld();
+                const size_t gj0 = (size_t)J * 128 + c;
                 float yr[16], yi[16];
 #pragma unroll
                 for (int q = 0; q < 16; q++) {
-                    yr[q] = d1r[q] + d2i[q];
-                    yi[q] = d2r[q] - d1i[q];
+                    // identity term conj(P[j][i]): lanes read consecutive i
+                    const size_t t = (gj0 + q) * Np + gi;
+                    yr[q] = (d1r[q] + d2i[q]) + ep.pr[t];
+                    yi[q] = (d2r[q] - d1i[q]) - ep.pi[t];
                 }
-                const size_t gj0 = (size_t)J * 128 + c;
                 if (MODE == 0 || !diag) {
                     // direct tile, full rows of 16: parts (and FP32 planes in mode 1)
                     T pr[S][16], pi[S][16];
@@ -267,10 +276,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                         store16(parts + (size_t)s * plane + gi * Np + gj0, pr[s]);
                         store16(parts + (size_t)(S + s) * plane + gi * Np + gj0, pi[s]);
                     }
-                    if (MODE == 1) {
-                        store16(ep.yr + gi * Np + gj0, yr);
-                        store16(ep.yi + gi * Np + gj0, yi);
-                    }
+                    store16(ep.yr + gi * Np + gj0, yr);
+                    store16(ep.yi + gi * Np + gj0, yi);
                 }
                 if (MODE == 1) {
 #pragma unroll

@@ -8,16 +8,21 @@
 
 namespace tc {
 
-// Output side of one launch.
-//   mode 0: Y written as operand parts only (the X = U rho of a step).
+// Output side of one launch.  The operand U is given as V = U / c - I
+// (c a unit phase), and the epilogue adds the FP32 identity term:
+//     Y = P^H + V P^H      (Y = U P^H / c)
+//   mode 0: all tiles (the X = U rho of a step).
 //   mode 1: Y Hermitian (rho' = U X^H): block-lower tiles computed, the
-//           conjugate transpose mirrored; FP32 planes and parts written.
+//           conjugate transpose mirrored.
+// Both modes write Y as FP32 planes and as operand parts.
 struct CgemmEpi {
     int Np;          // padded dimension, a multiple of 128 (row stride of every plane)
     int tiles;       // Np / 128
-    void* parts;     // [2 * S][Np][Np] operand parts: re parts 0..S-1, then im parts
-    float* yr;       // mode 1: FP32 real plane [Np][Np]
-    float* yi;       // mode 1: FP32 imaginary plane [Np][Np]
+    const float* pr; // FP32 planes of P (the identity term adds conj(P[j][i]))
+    const float* pi;
+    void* parts;     // [2 * S][Np][Np] operand parts of Y: re parts 0..S-1, then im parts
+    float* yr;       // FP32 planes of Y [Np][Np]
+    float* yi;
     unsigned* status;
 };
 

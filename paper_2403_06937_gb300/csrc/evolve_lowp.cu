@@ -1,13 +1,15 @@
 // evolve_lowp.cu -- the low-precision forms of the step loop
 // rho <- U rho U^dag (Sec. III.A, Eqs. 6, 12) on the tcgen05 tensor cores.
 //
-// U arrives in FP64 (from tc_expm) and is split once per call into operand
-// parts (BF16x3: three BF16 parts, computed in FP64; TF32x3: big/small TF32;
-// TF32: one TF32 part).  rho lives in FP32 planes between steps plus the
-// operand parts of those FP32 values; X = U rho lives only as operand parts.
-// Each step is two launches of the tensor-core GEMM Y = U P^H:
-//     X    = U rho^H  (all tiles; writes the parts of X)
-//     rho' = U X^H    (block-lower tiles + mirror; writes FP32 planes and parts)
+// U arrives in FP64 (from tc_expm).  It is used in increment form: with the
+// unit phase c = Tr U / |Tr U| (which cancels in U rho U^dag), V = U / c - I
+// is formed in FP64 and split once per call into operand parts (BF16x3:
+// three BF16 parts; TF32x3: big/small TF32; TF32: one TF32 part).  rho and
+// X = U rho / c live in FP32 planes plus the operand parts of those values.
+// Each step is two launches of the tensor-core GEMM Y = P^H + V P^H:
+//     X    = rho^H + V rho^H   (all tiles)
+//     rho' = X^H + V X^H       (block-lower tiles + mirror)
+// (rho' = U rho U^dag: the two phases cancel.)
 // then, every `renorm_every` steps, rho <- rho / Tr rho with the trace in
 // FP64, and the observable row from the FP32 planes.
 // Dimensions below 128 (n < 7) are zero-padded to one 128 x 128 tile: the
@@ -84,15 +86,48 @@ __device__ __forceinline__ void split_f32(float v, void* base, size_t plane, siz
     }
 }
 
+// c = Tr U / |Tr U| into out[0..1] (1 if the trace vanishes); one block, fixed order
+__global__ void unit_phase_kernel(const double2* U, int N, double* out) {
+    __shared__ double sr[1024], si[1024];
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        double2 u = U[(size_t)i * N + i];
+        a += u.x;
+        b += u.y;
+    }
+    sr[threadIdx.x] = a;
+    si[threadIdx.x] = b;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            sr[threadIdx.x] += sr[threadIdx.x + w];
+            si[threadIdx.x] += si[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double m = hypot(sr[0], si[0]);
+        out[0] = m > 1e-300 ? sr[0] / m : 1.0;
+        out[1] = m > 1e-300 ? si[0] / m : 0.0;
+    }
+}
+
+// V = U conj(c) - I (zero in the padding), split into operand parts in FP64
 template <int KIND, int S>
-__global__ void prep_u_kernel(const double2* U, int N, int Np, void* parts) {
+__global__ void prep_u_kernel(const double2* U, int N, int Np, const double* phase, void* parts) {
     const size_t plane = (size_t)Np * Np;
+    const double cr = phase[0], ci = -phase[1];
     for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < plane; e += (size_t)gridDim.x * blockDim.x) {
         const size_t i = e / Np, j = e % Np;
-        double2 u = make_double2(0.0, 0.0);
-        if (i < (size_t)N && j < (size_t)N) u = U[i * N + j];
-        split_f64<KIND, S>(u.x, parts, plane, e, 0);
-        split_f64<KIND, S>(u.y, parts, plane, e, 1);
+        double vr = 0.0, vi = 0.0;
+        if (i < (size_t)N && j < (size_t)N) {
+            const double2 u = U[i * N + j];
+            vr = u.x * cr - u.y * ci;
+            vi = u.x * ci + u.y * cr;
+            if (i == j) vr -= 1.0;
+        }
+        split_f64<KIND, S>(vr, parts, plane, e, 0);
+        split_f64<KIND, S>(vi, parts, plane, e, 1);
     }
 }
 
@@ -156,10 +191,12 @@ __global__ void finish_kernel(const float* Rr, const float* Ri, int N, int Np, d
 struct LowpBufs {
     int N, Np, S;
     size_t E;
-    void* Uparts;
+    void* Uparts;    // parts of V = U / c - I
     float* Rr;
     float* Ri;
     void* Rparts;
+    float* Xr;
+    float* Xi;
     void* Xparts;
     double* scratch;
 };
@@ -169,7 +206,11 @@ size_t plane_bytes(int Np, size_t E) { return round256((size_t)Np * Np * E); }
 template <int KIND, int S>
 tc_status run_prep(const double* U, const double* rho, LowpBufs& b, cudaStream_t s) {
     const size_t plane = (size_t)b.Np * b.Np;
-    prep_u_kernel<KIND, S><<<grid_for(plane), 256, 0, s>>>(reinterpret_cast<const double2*>(U), b.N, b.Np, b.Uparts);
+    double* phase = b.scratch;   // consumed by prep_u before any other use of scratch
+    unit_phase_kernel<<<1, 1024, 0, s>>>(reinterpret_cast<const double2*>(U), b.N, phase);
+    TC_LAUNCH_CHECK();
+    prep_u_kernel<KIND, S><<<grid_for(plane), 256, 0, s>>>(reinterpret_cast<const double2*>(U), b.N, b.Np, phase,
+                                                            b.Uparts);
     TC_LAUNCH_CHECK();
     prep_rho_kernel<KIND, S><<<grid_for(plane), 256, 0, s>>>(reinterpret_cast<const double2*>(rho), b.N, b.Np, b.Rr,
                                                                b.Ri, b.Rparts);
@@ -213,7 +254,7 @@ size_t evolve_lowp_bytes(int n, int precision) {
     const int Np = N < 128 ? 128 : N;
     const int S = cgemm_parts(precision);
     const size_t E = cgemm_elem_bytes(precision);
-    return 3 * (size_t)(2 * S) * plane_bytes(Np, E) + 2 * plane_bytes(Np, 4) + observables_scratch_bytes(n) + 512;
+    return 3 * (size_t)(2 * S) * plane_bytes(Np, E) + 4 * plane_bytes(Np, 4) + observables_scratch_bytes(n) + 512;
 }
 
 tc_status evolve_lowp(const double* U, double* rho, int n, int steps, int precision, int renorm_every,
@@ -232,6 +273,8 @@ tc_status evolve_lowp(const double* U, double* rho, int n, int steps, int precis
     b.Xparts = take_planes(2 * b.S, b.E);
     b.Rr = static_cast<float*>(take_planes(1, 4));
     b.Ri = static_cast<float*>(take_planes(1, 4));
+    b.Xr = static_cast<float*>(take_planes(1, 4));
+    b.Xi = static_cast<float*>(take_planes(1, 4));
     b.scratch = ar.take<double>(observables_scratch_bytes(n) / sizeof(double));
     if (!b.scratch) return fail(TC_ERR_WORKSPACE, "evolve: workspace too small");
     // plane_bytes rounds each plane to 256 B; for Np >= 128 the planes are exactly Np*Np*E
@@ -242,12 +285,18 @@ tc_status evolve_lowp(const double* U, double* rho, int n, int steps, int precis
     TC_TRY(make_part_map(&tmR, b.Rparts, b.Np, 2 * b.S, precision));
     TC_TRY(make_part_map(&tmX, b.Xparts, b.Np, 2 * b.S, precision));
 
-    CgemmEpi e1{};
+    CgemmEpi e1{};                 // X = rho^H + V rho^H
     e1.Np = b.Np;
     e1.tiles = b.Np / 128;
+    e1.pr = b.Rr;
+    e1.pi = b.Ri;
     e1.parts = b.Xparts;
+    e1.yr = b.Xr;
+    e1.yi = b.Xi;
     e1.status = device_status_word();
-    CgemmEpi e2 = e1;
+    CgemmEpi e2 = e1;              // rho' = X^H + V X^H
+    e2.pr = b.Xr;
+    e2.pi = b.Xi;
     e2.parts = b.Rparts;
     e2.yr = b.Rr;
     e2.yi = b.Ri;

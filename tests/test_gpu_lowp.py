@@ -1,0 +1,185 @@
+"""Parity of the tensor-core (tcgen05) forms with the FP64 path and the oracle.
+
+Tolerances, from the arithmetic of the increment form (Y = P^H + V P^H with
+V = U / c - I, c the unit phase of Tr U):
+* rho and X are stored in FP32 (round to nearest): 2^-24 relative per store,
+  two stores per step.
+* The tensor cores accumulate V P^H in FP32 with truncation: at most one ulp
+  (2^-23 relative) of a running sum bounded by ||V||_inf max|P| per
+  accumulation, and there are `products x K / k_step` accumulations per
+  element (BF16x3: 6 x K/16, TF32x3: 3 x K/8, TF32: K/8).
+* The operand parts represent V and P to 2^-24 (split forms) or 2^-11 (TF32)
+  relative, per operand of each of the two products.
+So one step is within
+    2^-24 (4 + 2 n_acc 2 ||V||) max|rho|      (split forms)
+    (4 x 2^-11 ||V|| + 2^-24 (4 + 2 n_acc 2 ||V||)) max|rho|   (TF32)
+and the stated target for the split-BF16 form is 1e-5 on populations.
+TF32 does not meet that target (it is reported, not pinned); TF32x3 is its
+remedy.
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+ACC = {"bf16x3": (6, 16), "tf32x3": (3, 8), "tf32": (1, 8)}   # part products, K per MMA
+
+
+def step_bound(precision, K, vnorm, scale):
+    prod, kstep = ACC[precision]
+    n_acc = prod * K / kstep
+    b = 2.0 ** -24 * (4.0 + 2.0 * n_acc * 2.0 * vnorm) * scale
+    if precision == "tf32":
+        b += 4.0 * 2.0 ** -11 * vnorm * scale
+    return b
+
+
+def v_norm(U):
+    """||U / c - I||_inf with c the unit phase of Tr U (a tolerance input only)."""
+    tr = np.trace(U)
+    c = tr / abs(tr)
+    return float(np.abs(U / c - np.eye(U.shape[0])).sum(1).max())
+
+
+@pytest.fixture(scope="module")
+def tc():
+    from paper_2403_06937_gb300 import build
+    build.build()
+    import paper_2403_06937_gb300 as tc
+    tc.device_check()
+    return tc
+
+
+def _setup(tc, n, seed=3, scale=4.0, dt=0.1, wa=1.01, wc=1.0):
+    g = W.draw_couplings(n, seed) * scale
+    p = tc.Params(n, list(map(float, g)), wa, wc)
+    U = tc.expm(tc.build_hamiltonian(p), n, dt)
+    return g, p, U
+
+
+@pytest.mark.parametrize("precision", ["bf16x3", "tf32x3", "tf32"])
+@pytest.mark.parametrize("n", [3, 5, 7, 8, 10])
+def test_one_step_matches_fp64(tc, oracle, n, precision):
+    """n < 7 runs zero-padded in one 128 x 128 tile; n = 8, 10 span 2 x 2 and 8 x 8 tiles."""
+    g, p, U = _setup(tc, n)
+    rho0, _, _ = W.random_mixed_state(n, min(4, 1 << n), 11 + n)
+    r0 = torch.from_numpy(rho0).cuda()
+    ref, robs = tc.evolve(U, r0, n, 1, "fp64", params=p)
+    out, obs = tc.evolve(U, r0, n, 1, precision, params=p)
+    tc.sync_status()
+    N = 1 << n
+    vn = v_norm(oracle.expm(n, g, 1.01, 1.0, 0.1))
+    scale = float(np.abs(rho0).max())
+    bound = step_bound(precision, max(N, 128), vn, scale)
+    err = (out - ref).abs().max().item()
+    assert err < bound, (err, bound)
+    # populations, <p>, P(m), trace are sums of at most N diagonal entries with
+    # weights <= n; purity is bounded through |rho| <= scale.
+    d = np.abs(obs.cpu().numpy() - robs.cpu().numpy())[1]
+    assert np.all(d[:2 * n + 3] <= n * N * bound)
+    assert d[2 * n + 3] <= 2 * N * N * scale * bound
+
+
+@pytest.mark.parametrize("precision", ["bf16x3", "tf32x3", "tf32"])
+def test_result_is_exactly_hermitian(tc, precision):
+    n = 9
+    g, p, U = _setup(tc, n)
+    rho0, _, _ = W.random_mixed_state(n, 3, 2)
+    out, _ = tc.evolve(U, torch.from_numpy(rho0).cuda(), n, 2, precision, params=p)
+    o = out.cpu().numpy()
+    assert np.array_equal(o, o.conj().T)
+
+
+@pytest.mark.parametrize("precision", ["bf16x3", "tf32x3", "tf32"])
+def test_n8_workload(tc, oracle, precision):
+    """n = 8, 100 steps, from all-excited: populations against the oracle.
+
+    Split forms: the stated target, 1e-5 on populations and on rho entries.
+    TF32: within 100 times its one-step bound (reported, not the target).
+    """
+    cfg = W.config_n8()
+    p = tc.Params(cfg.n, list(cfg.g), cfg.omega_a, cfg.omega_c)
+    U = tc.expm(tc.build_hamiltonian(p), cfg.n, cfg.dt)
+    rho0 = torch.from_numpy(W.all_excited_rho(cfg.n)).cuda()
+    rho, obs = tc.evolve(U, rho0, cfg.n, cfg.steps, precision, params=p)
+    tc.sync_status()
+    psi, oobs = oracle.propagate(cfg.n, cfg.g, cfg.omega_a, cfg.omega_c, cfg.dt, cfg.steps,
+                                 W.all_excited_state(cfg.n))
+    n = cfg.n
+    o = obs.cpu().numpy()
+    pop_err = np.max(np.abs(o[:, :2 * n + 2] - oobs[:, :2 * n + 2]))
+    rho_err = np.max(np.abs(rho.cpu().numpy() - np.outer(psi, psi.conj())))
+    if precision == "tf32":
+        vn = v_norm(oracle.expm(n, cfg.g, cfg.omega_a, cfg.omega_c, cfg.dt))
+        b = cfg.steps * step_bound(precision, cfg.N, vn, 1.0)
+        assert rho_err < b and pop_err < n * b
+    else:
+        assert pop_err < 1e-5, pop_err
+        assert rho_err < 1e-5, rho_err
+
+
+def test_renormalisation_in_fp32_form(tc):
+    n = 8
+    g, p, U = _setup(tc, n)
+    rho0, _, _ = W.random_mixed_state(n, 2, 5)
+    rho, obs = tc.evolve(U, torch.from_numpy(1.5 * rho0).cuda(), n, 4, "bf16x3", renorm_every=2, params=p)
+    o = obs.cpu().numpy()
+    N = 1 << n
+    assert abs(o[1, 2 * n + 2] - 1.5) < 1e-6      # one step: trace kept to FP32 level
+    assert abs(o[2, 2 * n + 2] - 1.0) < N * 2.0 ** -24   # renormalised (FP32 storage of N entries)
+    assert abs(o[4, 2 * n + 2] - 1.0) < N * 2.0 ** -24
+
+
+def test_runs_are_bitwise_reproducible(tc):
+    n = 9
+    g, p, U = _setup(tc, n)
+    rho0, _, _ = W.random_mixed_state(n, 3, 4)
+    r0 = torch.from_numpy(rho0).cuda()
+    a, oa = tc.evolve(U, r0, n, 3, "bf16x3", params=p)
+    b, ob = tc.evolve(U, r0, n, 3, "bf16x3", params=p)
+    assert torch.equal(a, b) and torch.equal(oa, ob)
+
+
+@pytest.mark.parametrize("precision", ["bf16x3", "tf32x3", "tf32"])
+def test_n12_against_fp64_path(tc, precision):
+    cfg = W.config_n12()
+    p = tc.Params(cfg.n, list(cfg.g), cfg.omega_a, cfg.omega_c)
+    U = tc.expm(tc.build_hamiltonian(p), cfg.n, cfg.dt)
+    rho0 = torch.from_numpy(W.all_excited_rho(cfg.n)).cuda()
+    steps = 3
+    ref, robs = tc.evolve(U, rho0, cfg.n, steps, "fp64", params=p)
+    out, obs = tc.evolve(U, rho0, cfg.n, steps, precision, params=p)
+    tc.sync_status()
+    vn = 0.05       # ||V||_inf <= e^{||(H - mu) dt||} - 1 < 0.05 for this workload (dt = 0.05)
+    tol = steps * step_bound(precision, cfg.N, vn, 1.0)       # max|rho0| = 1
+    assert (out - ref).abs().max().item() < tol
+    assert np.max(np.abs(obs.cpu().numpy() - robs.cpu().numpy())[:, :2 * cfg.n + 3]) < tol
+
+
+def test_n14_workload_sampled_bf16x3(tc, oracle):
+    """n = 14, dim 16384: the benchmark's launch configuration, a few steps, sampled entries."""
+    cfg = W.config_n14()
+    steps = 3
+    p = tc.Params(cfg.n, list(cfg.g), cfg.omega_a, cfg.omega_c)
+    U = tc.expm(tc.build_hamiltonian(p), cfg.n, cfg.dt)
+    rho0 = torch.zeros((cfg.N, cfg.N), dtype=torch.complex128, device="cuda")
+    rho0[-1, -1] = 1.0
+    rho, obs = tc.evolve(U, rho0, cfg.n, steps, "bf16x3", renorm_every=cfg.renorm_every, params=p)
+    tc.sync_status()
+    psi, oobs = oracle.propagate(cfg.n, cfg.g, cfg.omega_a, cfg.omega_c, cfg.dt, steps,
+                                 W.all_excited_state(cfg.n))
+    n = cfg.n
+    o = obs.cpu().numpy()
+    assert np.max(np.abs(o[:, :2 * n + 3] - oobs[:, :2 * n + 3])) < 1e-5
+    rng = np.random.default_rng(5)
+    idx = rng.integers(0, cfg.N, size=(20000, 2))
+    top = np.argsort(-np.abs(psi))[:48]
+    ii = torch.from_numpy(np.concatenate([idx[:, 0], np.repeat(top, len(top))])).cuda()
+    jj = torch.from_numpy(np.concatenate([idx[:, 1], np.tile(top, len(top))])).cuda()
+    got = rho[ii, jj].cpu().numpy()
+    ii, jj = ii.cpu().numpy(), jj.cpu().numpy()
+    want = psi[ii] * psi[jj].conj()
+    assert np.max(np.abs(got - want)) < 1e-5
