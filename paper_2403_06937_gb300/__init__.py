@@ -137,6 +137,56 @@ def evolve_host(U: torch.Tensor, rho_host: torch.Tensor, n: int, steps: int, pre
               ctypes.c_void_p(_stream(stream)))
 
 
+def evolve_backward(params: Params, dt: float, steps: int, rho0: torch.Tensor, U: torch.Tensor,
+                    O_diag: torch.Tensor, ckpt_every: int = 20, stream=None, work: Optional[torch.Tensor] = None):
+    """tc_evolve_backward: (grad, loss) of L = Tr(diag(O) rho_K) w.r.t. (g_1..g_n, omega_a, omega_c).
+
+    grad is a float64 numpy-convertible CPU tensor of n + 2 values; the call blocks.
+    """
+    n = params.n
+    N = 1 << n
+    assert rho0.dtype == torch.complex128 and rho0.is_contiguous() and rho0.shape == (N, N)
+    assert U.dtype == torch.complex128 and U.is_contiguous() and U.shape == (N, N)
+    assert O_diag.dtype == torch.float64 and O_diag.is_cuda and O_diag.numel() == N
+    need = workspace_size(n, TC_FP64, TC_OP_BACKWARD, steps, ckpt_every)
+    if work is None or work.numel() < need:
+        work = _work(need, rho0.device)
+    grad = (ctypes.c_double * (n + 2))()
+    loss = ctypes.c_double()
+    p = params.c()
+    _abi.call("tc_evolve_backward", ctypes.byref(p), float(dt), int(steps), _ptr(rho0), _ptr(U), int(ckpt_every),
+              _ptr(O_diag.contiguous()), grad, ctypes.byref(loss), _ptr(work), work.numel(),
+              ctypes.c_void_p(_stream(stream)))
+    return torch.tensor(list(grad), dtype=torch.float64), float(loss.value)
+
+
+class EvolveFn(torch.autograd.Function):
+    """L = Tr(diag(O) rho_K) as a differentiable function of (g, omega_a, omega_c).
+
+    forward: builds H (Eq. 4), U = e^{-iH dt} and steps rho0 K times (FP64);
+    backward: tc_evolve_backward (reverse mode with checkpoints).
+    Inputs g (n,), omega_a (), omega_c () are float64 tensors; rho0 and O_diag
+    are CUDA tensors.  Returns a 0-d float64 tensor.
+    """
+
+    @staticmethod
+    def forward(ctx, g, omega_a, omega_c, rho0, O_diag, dt, steps, ckpt_every=20, coupling=TC_COUPLING_BOSONIC):
+        n = int(g.numel())
+        params = Params(n, [float(x) for x in g.detach().cpu()], float(omega_a), float(omega_c), coupling)
+        U = expm(build_hamiltonian(params, device=rho0.device), n, dt)
+        grad, loss = evolve_backward(params, dt, steps, rho0, U, O_diag, ckpt_every)
+        ctx.save_for_backward(grad)
+        ctx.n = n
+        return torch.tensor(loss, dtype=torch.float64, device=g.device)
+
+    @staticmethod
+    def backward(ctx, gout):
+        (grad,) = ctx.saved_tensors
+        grad = grad.to(gout.device) * gout
+        n = ctx.n
+        return grad[:n], grad[n], grad[n + 1], None, None, None, None, None, None
+
+
 def launch_count() -> int:
     """Kernels launched by libtc in this process."""
     return int(_abi.load().tc_launch_count())
@@ -160,6 +210,7 @@ def sync_status(stream=None) -> None:
 
 
 __all__ = ["Params", "TCError", "build_hamiltonian", "expm", "evolve", "evolve_host", "observables",
+           "evolve_backward", "EvolveFn",
            "workspace_size", "launch_count", "timing_enable", "timing_read",
            "device_check", "sync_status", "obs_stride", "PRECISIONS", "TC_FP64", "TC_BF16X3", "TC_TF32",
            "TC_TF32X3", "TC_COUPLING_BOSONIC", "TC_COUPLING_QUBIT_PHOTON", "TC_OP_EXPM", "TC_OP_EVOLVE",
