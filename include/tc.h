@@ -267,6 +267,32 @@ TC_API tc_status tc_evolve_host(const void* U, void* rho_host, int n, int steps,
                                 int renorm_every, const tc_params* params, double* obs_host,
                                 void* work, size_t work_bytes, void* stream);
 
+/* ------------------------------------------------------------- batching */
+
+/* Bytes of `work` for tc_batch_evolve of `count` systems with n[b] atoms. */
+TC_API size_t tc_batch_workspace_size(int count, const int* n, int precision);
+
+/* tc_batch_evolve -- `count` independent systems of uneven size (n[b] atoms
+ * each, own U and rho), each stepped `steps` times by rho <- U rho U^dag
+ * (Eq. 6) as in tc_evolve.  The tensor-core forms run each product of a step
+ * as ONE persistent launch over the tiles of all systems (systems in
+ * decreasing size, static round-robin over the SMs); TC_FP64 runs the
+ * systems' DMMA products one after another.  Steps 2..K are captured into one
+ * CUDA graph on a library-owned stream and launched once; the call returns
+ * after the batch has finished.  Every system's result (rho, observables) is
+ * bitwise the result of tc_evolve on that system alone with the same
+ * precision.
+ *  n, U, rho, params, obs : host arrays of `count` entries.  U[b] and rho[b]
+ *             are device pointers (N_b x N_b c128, 16-byte aligned; rho in/out);
+ *             params may be NULL (energy column 0) or give each system's
+ *             parameters; obs may be NULL or hold device pointers (entries
+ *             may be NULL) of (steps + 1) * TC_OBS_STRIDE(n[b]) doubles.
+ *  work     : device, >= tc_batch_workspace_size(count, n, precision).
+ *  Errors: as tc_evolve, for any system. */
+TC_API tc_status tc_batch_evolve(int count, const int* n, const void* const* U, void* const* rho, int steps,
+                                 int precision, int renorm_every, const tc_params* params,
+                                 double* const* obs, void* work, size_t work_bytes, void* stream);
+
 /* ----------------------------------------------------------- measurement */
 
 /* Number of kernels this library has launched in this process. */

@@ -187,6 +187,43 @@ class EvolveFn(torch.autograd.Function):
         return grad[:n], grad[n], grad[n + 1], None, None, None, None, None, None
 
 
+def batch_evolve(Us, rhos, steps: int, precision="bf16x3", renorm_every: int = 0, params=None,
+                 observe: bool = True, inplace: bool = False, stream=None, work: Optional[torch.Tensor] = None):
+    """tc_batch_evolve: step many systems of uneven size together.
+
+    Us, rhos: lists of (N_b x N_b) complex128 CUDA tensors; params: list of
+    Params or None.  Returns (list of rho_T, list of obs or None).
+    """
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    count = len(Us)
+    ns = []
+    for U, r in zip(Us, rhos):
+        N = U.shape[0]
+        n = N.bit_length() - 1
+        assert 1 << n == N and U.dtype == torch.complex128 and r.shape == U.shape and r.dtype == torch.complex128
+        ns.append(n)
+    outs = rhos if inplace else [r.clone() for r in rhos]
+    obs = [torch.empty((steps + 1, obs_stride(n)), dtype=torch.float64, device=r.device) for n, r in zip(ns, rhos)] \
+        if observe else None
+    n_arr = (ctypes.c_int * count)(*ns)
+    need = int(_abi.load().tc_batch_workspace_size(count, n_arr, prec))
+    if work is None or work.numel() < need:
+        work = _work(need, rhos[0].device)
+    U_arr = (ctypes.c_void_p * count)(*[U.data_ptr() for U in Us])
+    R_arr = (ctypes.c_void_p * count)(*[r.data_ptr() for r in outs])
+    O_arr = (ctypes.c_void_p * count)(*[o.data_ptr() for o in obs]) if observe else None
+    P_arr = None
+    keep = []
+    if params is not None:
+        cps = [p.c() for p in params]
+        keep = cps
+        P_arr = (_abi.tc_params * count)(*cps)
+    _abi.call("tc_batch_evolve", count, n_arr, U_arr, R_arr, int(steps), prec, int(renorm_every), P_arr, O_arr,
+              _ptr(work), work.numel(), ctypes.c_void_p(_stream(stream)))
+    del keep
+    return outs, obs
+
+
 def launch_count() -> int:
     """Kernels launched by libtc in this process."""
     return int(_abi.load().tc_launch_count())
@@ -210,7 +247,7 @@ def sync_status(stream=None) -> None:
 
 
 __all__ = ["Params", "TCError", "build_hamiltonian", "expm", "evolve", "evolve_host", "observables",
-           "evolve_backward", "EvolveFn",
+           "evolve_backward", "EvolveFn", "batch_evolve",
            "workspace_size", "launch_count", "timing_enable", "timing_read",
            "device_check", "sync_status", "obs_stride", "PRECISIONS", "TC_FP64", "TC_BF16X3", "TC_TF32",
            "TC_TF32X3", "TC_COUPLING_BOSONIC", "TC_COUPLING_QUBIT_PHOTON", "TC_OP_EXPM", "TC_OP_EVOLVE",

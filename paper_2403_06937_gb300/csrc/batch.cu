@@ -1,0 +1,242 @@
+// batch.cu -- many independent systems of uneven size stepped together
+// (tc_batch_evolve).  The tensor-core forms run each product of a step as one
+// persistent launch over the tiles of every system (cgemm_batch.cu); the FP64
+// form runs the systems' DMMA products one after another.  The whole step
+// loop is captured into one CUDA graph on a library stream and launched once.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <numeric>
+#include <vector>
+
+#include "cgemm_batch.cuh"
+#include "cgemm_tc.cuh"
+#include "lowp.cuh"
+#include "paths.cuh"
+
+namespace tc {
+namespace {
+
+struct GraphStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t before = nullptr, after = nullptr;
+};
+std::mutex g_gs_mu;
+GraphStream g_gs[64];
+
+tc_status graph_stream(GraphStream** out) {
+    int dev = 0;
+    TC_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(TC_ERR_UNSUPPORTED_DEVICE, "device index out of range");
+    std::lock_guard<std::mutex> lk(g_gs_mu);
+    GraphStream& g = g_gs[dev];
+    if (!g.s) {
+        TC_CUDA(cudaStreamCreateWithFlags(&g.s, cudaStreamNonBlocking));
+        TC_CUDA(cudaEventCreateWithFlags(&g.before, cudaEventDisableTiming));
+        TC_CUDA(cudaEventCreateWithFlags(&g.after, cudaEventDisableTiming));
+    }
+    *out = &g;
+    return TC_OK;
+}
+
+size_t f64_system_bytes(int n) {
+    const size_t cm = 2 * round256(sizeof(double) << (2 * n));
+    return 3 * cm + observables_scratch_bytes(n) + 256;   // U, rho, X planar
+}
+
+struct F64Sys {
+    int n, N;
+    double *Ur, *Ui, *Rr, *Ri, *Xr, *Xi, *scratch;
+};
+
+}  // namespace
+
+size_t batch_bytes(int count, const int* n, int precision) {
+    size_t total = 256 + round256(sizeof(BatchSys) * (size_t)count) + 64;
+    for (int b = 0; b < count; b++) {
+        if (n[b] < 1 || n[b] > kMaxAtoms) return 0;
+        total += precision == TC_FP64 ? f64_system_bytes(n[b]) : lowp_system_bytes(n[b], precision) + 512;
+    }
+    return total;
+}
+
+}  // namespace tc
+
+using namespace tc;
+
+extern "C" {
+
+TC_API size_t tc_batch_workspace_size(int count, const int* n, int precision) {
+    if (count < 1 || !n) return 0;
+    if (precision < TC_FP64 || precision > TC_TF32X3) return 0;
+    return batch_bytes(count, n, precision);
+}
+
+TC_API tc_status tc_batch_evolve(int count, const int* n, const void* const* U, void* const* rho, int steps,
+                                 int precision, int renorm_every, const tc_params* params, double* const* obs,
+                                 void* work, size_t work_bytes, void* stream) {
+    if (count < 1 || !n || !U || !rho) return fail(TC_ERR_INVALID_ARG, "count, n, U or rho missing");
+    if (steps < 0 || renorm_every < 0) return fail(TC_ERR_INVALID_ARG, "steps / renorm_every < 0");
+    if (precision < TC_FP64 || precision > TC_TF32X3) return fail(TC_ERR_INVALID_ARG, "unknown precision %d", precision);
+    std::vector<Model> models(count);
+    for (int b = 0; b < count; b++) {
+        if (n[b] < 1 || n[b] > kMaxAtoms) return fail(TC_ERR_INVALID_ARG, "system %d: n = %d outside 1..16", b, n[b]);
+        if (!U[b] || !rho[b]) return fail(TC_ERR_INVALID_ARG, "system %d: U or rho is NULL", b);
+        if ((reinterpret_cast<uintptr_t>(U[b]) | reinterpret_cast<uintptr_t>(rho[b])) & 15u)
+            return fail(TC_ERR_INVALID_ARG, "system %d: U and rho must be 16-byte aligned", b);
+        if (params) {
+            TC_TRY(make_model(&params[b], &models[b]));
+            if (models[b].n != n[b]) return fail(TC_ERR_INVALID_ARG, "system %d: params.n != n", b);
+        }
+    }
+    const size_t need = batch_bytes(count, n, precision);
+    if (!work) return fail(TC_ERR_WORKSPACE, "work is NULL (need %zu bytes)", need);
+    if (reinterpret_cast<uintptr_t>(work) & 255u) return fail(TC_ERR_WORKSPACE, "work is not 256-byte aligned");
+    if (work_bytes < need) return fail(TC_ERR_WORKSPACE, "work has %zu bytes, need %zu", work_bytes, need);
+    TC_TRY(check_device());
+    cudaStream_t us = as_stream(stream);
+
+    // systems in decreasing size: the longest tiles first in the persistent schedule
+    std::vector<int> order(count);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return n[a] > n[b]; });
+
+    Arena ar{static_cast<char*>(work), work_bytes, 0};
+    BatchSys* sys_dev = ar.take<BatchSys>((size_t)count);
+    GraphStream* gs = nullptr;
+    TC_TRY(graph_stream(&gs));
+    cudaStream_t s = gs->s;
+    TC_CUDA(cudaEventRecord(gs->before, us));
+    TC_CUDA(cudaStreamWaitEvent(s, gs->before, 0));
+
+    std::vector<LowpBufs> lb(count);
+    std::vector<F64Sys> fb(count);
+    std::vector<BatchSys> host(count);
+    int tiles[2] = {0, 0};
+    if (precision == TC_FP64) {
+        for (int k = 0; k < count; k++) {
+            const int b = order[k];
+            F64Sys& f = fb[k];
+            f.n = n[b];
+            f.N = 1 << n[b];
+            const size_t NN = (size_t)f.N * f.N;
+            f.Ur = ar.take<double>(NN); f.Ui = ar.take<double>(NN);
+            f.Rr = ar.take<double>(NN); f.Ri = ar.take<double>(NN);
+            f.Xr = ar.take<double>(NN); f.Xi = ar.take<double>(NN);
+            f.scratch = ar.take<double>(observables_scratch_bytes(n[b]) / sizeof(double));
+            if (!f.scratch) return fail(TC_ERR_WORKSPACE, "batch: workspace too small");
+            TC_TRY(launch_split_c128(static_cast<const double*>(U[b]), f.Ur, f.Ui, NN, s));
+            TC_TRY(launch_split_c128(static_cast<const double*>(rho[b]), f.Rr, f.Ri, NN, s));
+        }
+    } else {
+        for (int k = 0; k < count; k++) {
+            const int b = order[k];
+            TC_TRY(lowp_carve(n[b], precision, ar, lb[k]));
+            TC_TRY(lowp_prep(precision, static_cast<const double*>(U[b]), static_cast<const double*>(rho[b]), lb[k], s));
+            BatchSys& h = host[k];
+            std::memset(&h, 0, sizeof(h));
+            TC_TRY(make_part_map(&h.tmU, lb[k].Uparts, lb[k].Np, 2 * lb[k].S, precision));
+            TC_TRY(make_part_map(&h.tmR, lb[k].Rparts, lb[k].Np, 2 * lb[k].S, precision));
+            TC_TRY(make_part_map(&h.tmX, lb[k].Xparts, lb[k].Np, 2 * lb[k].S, precision));
+            h.Rr = lb[k].Rr; h.Ri = lb[k].Ri; h.Rparts = lb[k].Rparts;
+            h.Xr = lb[k].Xr; h.Xi = lb[k].Xi; h.Xparts = lb[k].Xparts;
+            h.Np = lb[k].Np;
+            h.tiles = lb[k].Np / 128;
+            h.tile_begin[0] = tiles[0];
+            h.tile_begin[1] = tiles[1];
+            tiles[0] += h.tiles * h.tiles;
+            tiles[1] += h.tiles * (h.tiles + 1) / 2;
+        }
+        TC_CUDA(cudaMemcpyAsync(sys_dev, host.data(), sizeof(BatchSys) * count, cudaMemcpyHostToDevice, s));
+        TC_CUDA(cudaStreamSynchronize(s));   // host copy of the descriptors may go
+    }
+
+    auto observe = [&](int k, int row) -> tc_status {
+        const int b = order[k];
+        if (!obs || !obs[b]) return TC_OK;
+        const int stride = TC_OBS_STRIDE(n[b]);
+        const Model* mp = params ? &models[b] : nullptr;
+        if (precision == TC_FP64)
+            return launch_observables(kRhoPlanarF64, fb[k].Rr, fb[k].Ri, mp, n[b], obs[b] + (size_t)row * stride,
+                                      fb[k].scratch, s);
+        return launch_observables(kRhoPlanarF32, lb[k].Rr, lb[k].Ri, mp, n[b], obs[b] + (size_t)row * stride,
+                                  lb[k].scratch, s, (size_t)lb[k].Np);
+    };
+    for (int k = 0; k < count; k++) TC_TRY(observe(k, 0));
+
+    // one step of every system, enqueued on s
+    unsigned* status = device_status_word();
+    auto one_step = [&](int step) -> tc_status {
+        if (precision == TC_FP64) {
+            for (int k = 0; k < count; k++) {
+                F64Sys& f = fb[k];
+                GemmF64 g1{};
+                g1.M = g1.N = g1.K = f.N;
+                g1.Ar = f.Ur; g1.Ai = f.Ui; g1.lda = f.N;
+                g1.Br = f.Rr; g1.Bi = f.Ri; g1.ldb = f.N;
+                g1.Cr = f.Xr; g1.Ci = f.Xi; g1.ldc = f.N;
+                g1.alpha = 1.0; g1.cplx = 1;
+                GemmF64 g2 = g1;
+                g2.Ar = f.Xr; g2.Ai = f.Xi;
+                g2.Br = f.Ur; g2.Bi = f.Ui; g2.conjB = 1;
+                g2.Cr = f.Rr; g2.Ci = f.Ri;
+                g2.herm_lower = 1;
+                TC_TRY(gemm_f64(g1, s));
+                TC_TRY(gemm_f64(g2, s));
+                if (renorm_every > 0 && step % renorm_every == 0)
+                    TC_TRY(launch_renormalise(kRhoPlanarF64, f.Rr, f.Ri, f.n, f.scratch, s));
+            }
+        } else {
+            TC_TRY(cgemm_batch(precision, 0, sys_dev, count, tiles[0], status, s));
+            TC_TRY(cgemm_batch(precision, 1, sys_dev, count, tiles[1], status, s));
+            if (renorm_every > 0 && step % renorm_every == 0)
+                for (int k = 0; k < count; k++) TC_TRY(lowp_renorm(precision, lb[k], s));
+        }
+        for (int k = 0; k < count; k++) TC_TRY(observe(k, step));
+        return TC_OK;
+    };
+
+    if (steps > 0) {
+        // set kernel attributes outside the capture with one real step, then capture the rest
+        TC_TRY(one_step(1));
+        if (steps > 1) {
+            cudaGraph_t graph = nullptr;
+            cudaGraphExec_t exec = nullptr;
+            TC_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            tc_status st = TC_OK;
+            for (int k = 2; k <= steps && st == TC_OK; k++) st = one_step(k);
+            cudaError_t ce = cudaStreamEndCapture(s, &graph);
+            if (st != TC_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return st;
+            }
+            if (ce != cudaSuccess) return fail(TC_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ce));
+            ce = cudaGraphInstantiate(&exec, graph, 0);
+            if (ce != cudaSuccess) {
+                cudaGraphDestroy(graph);
+                return fail(TC_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+            }
+            ce = cudaGraphLaunch(exec, s);
+            cudaError_t ce2 = cudaStreamSynchronize(s);
+            cudaGraphExecDestroy(exec);
+            cudaGraphDestroy(graph);
+            if (ce != cudaSuccess || ce2 != cudaSuccess)
+                return fail(TC_ERR_CUDA, "graph launch: %s", cudaGetErrorString(ce != cudaSuccess ? ce : ce2));
+        }
+    }
+    // results back to the callers' rho
+    for (int k = 0; k < count; k++) {
+        const int b = order[k];
+        if (precision == TC_FP64) {
+            const size_t NN = (size_t)fb[k].N * fb[k].N;
+            TC_TRY(launch_join_c128(fb[k].Rr, fb[k].Ri, static_cast<double*>(rho[b]), NN, s));
+        } else {
+            TC_TRY(lowp_finish(lb[k], static_cast<double*>(rho[b]), s));
+        }
+    }
+    TC_CUDA(cudaEventRecord(gs->after, s));
+    TC_CUDA(cudaStreamWaitEvent(us, gs->after, 0));
+    return TC_OK;
+}
+
+}  // extern "C"

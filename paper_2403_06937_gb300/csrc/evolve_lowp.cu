@@ -17,6 +17,7 @@
 #include <cuda_bf16.h>
 
 #include "cgemm_tc.cuh"
+#include "lowp.cuh"
 #include "paths.cuh"
 #include "timing.cuh"
 
@@ -188,20 +189,11 @@ __global__ void finish_kernel(const float* Rr, const float* Ri, int N, int Np, d
     }
 }
 
-struct LowpBufs {
-    int N, Np, S;
-    size_t E;
-    void* Uparts;    // parts of V = U / c - I
-    float* Rr;
-    float* Ri;
-    void* Rparts;
-    float* Xr;
-    float* Xi;
-    void* Xparts;
-    double* scratch;
-};
+}  // namespace
 
 size_t plane_bytes(int Np, size_t E) { return round256((size_t)Np * Np * E); }
+
+namespace {
 
 template <int KIND, int S>
 tc_status run_prep(const double* U, const double* rho, LowpBufs& b, cudaStream_t s) {
@@ -228,7 +220,9 @@ tc_status run_renorm(LowpBufs& b, cudaStream_t s) {
     return TC_OK;
 }
 
-tc_status prep(int precision, const double* U, const double* rho, LowpBufs& b, cudaStream_t s) {
+}  // namespace
+
+tc_status lowp_prep(int precision, const double* U, const double* rho, LowpBufs& b, cudaStream_t s) {
     switch (precision) {
         case TC_BF16X3: return run_prep<0, 3>(U, rho, b, s);
         case TC_TF32: return run_prep<1, 1>(U, rho, b, s);
@@ -237,7 +231,7 @@ tc_status prep(int precision, const double* U, const double* rho, LowpBufs& b, c
     return fail(TC_ERR_INVALID_ARG, "precision");
 }
 
-tc_status renorm(int precision, LowpBufs& b, cudaStream_t s) {
+tc_status lowp_renorm(int precision, LowpBufs& b, cudaStream_t s) {
     switch (precision) {
         case TC_BF16X3: return run_renorm<0, 3>(b, s);
         case TC_TF32: return run_renorm<1, 1>(b, s);
@@ -246,10 +240,13 @@ tc_status renorm(int precision, LowpBufs& b, cudaStream_t s) {
     return fail(TC_ERR_INVALID_ARG, "precision");
 }
 
-}  // namespace
+tc_status lowp_finish(const LowpBufs& b, double* rho, cudaStream_t s) {
+    finish_kernel<<<grid_for((size_t)b.N * b.N), 256, 0, s>>>(b.Rr, b.Ri, b.N, b.Np, reinterpret_cast<double2*>(rho));
+    TC_LAUNCH_CHECK();
+    return TC_OK;
+}
 
-size_t evolve_lowp_bytes(int n, int precision) {
-    if (precision != TC_BF16X3 && precision != TC_TF32 && precision != TC_TF32X3) return 0;
+size_t lowp_system_bytes(int n, int precision) {
     const int N = 1 << n;
     const int Np = N < 128 ? 128 : N;
     const int S = cgemm_parts(precision);
@@ -257,14 +254,11 @@ size_t evolve_lowp_bytes(int n, int precision) {
     return 3 * (size_t)(2 * S) * plane_bytes(Np, E) + 4 * plane_bytes(Np, 4) + observables_scratch_bytes(n) + 512;
 }
 
-tc_status evolve_lowp(const double* U, double* rho, int n, int steps, int precision, int renorm_every,
-                      const Model* m, double* obs, Arena& ar, cudaStream_t s) {
-    LowpBufs b{};
+tc_status lowp_carve(int n, int precision, Arena& ar, LowpBufs& b) {
     b.N = 1 << n;
     b.Np = b.N < 128 ? 128 : b.N;
     b.S = cgemm_parts(precision);
     b.E = cgemm_elem_bytes(precision);
-    const size_t pl = (size_t)b.Np * b.Np;
     auto take_planes = [&](int planes, size_t E) -> void* {
         return ar.take<uint8_t>((size_t)planes * plane_bytes(b.Np, E));
     };
@@ -276,8 +270,20 @@ tc_status evolve_lowp(const double* U, double* rho, int n, int steps, int precis
     b.Xr = static_cast<float*>(take_planes(1, 4));
     b.Xi = static_cast<float*>(take_planes(1, 4));
     b.scratch = ar.take<double>(observables_scratch_bytes(n) / sizeof(double));
-    if (!b.scratch) return fail(TC_ERR_WORKSPACE, "evolve: workspace too small");
-    // plane_bytes rounds each plane to 256 B; for Np >= 128 the planes are exactly Np*Np*E
+    if (!b.scratch) return fail(TC_ERR_WORKSPACE, "low-precision workspace too small");
+    return TC_OK;
+}
+
+size_t evolve_lowp_bytes(int n, int precision) {
+    if (precision != TC_BF16X3 && precision != TC_TF32 && precision != TC_TF32X3) return 0;
+    return lowp_system_bytes(n, precision);
+}
+
+tc_status evolve_lowp(const double* U, double* rho, int n, int steps, int precision, int renorm_every,
+                      const Model* m, double* obs, Arena& ar, cudaStream_t s) {
+    LowpBufs b{};
+    TC_TRY(lowp_carve(n, precision, ar, b));
+    const size_t pl = (size_t)b.Np * b.Np;
     if (plane_bytes(b.Np, b.E) != pl * b.E) return fail(TC_ERR_INVALID_ARG, "evolve: plane size");
 
     CUtensorMap tmU, tmR, tmX;
@@ -305,7 +311,7 @@ tc_status evolve_lowp(const double* U, double* rho, int n, int steps, int precis
     const double N3 = (double)b.N * b.N * b.N;
     const double prod = (double)cgemm_products(precision);
 
-    TC_TRY(prep(precision, U, rho, b, s));
+    TC_TRY(lowp_prep(precision, U, rho, b, s));
     if (obs) TC_TRY(launch_observables(kRhoPlanarF32, b.Rr, b.Ri, m, n, obs, b.scratch, s, (size_t)b.Np));
     for (int k = 1; k <= steps; k++) {
         {
@@ -316,14 +322,12 @@ tc_status evolve_lowp(const double* U, double* rho, int n, int steps, int precis
             ProductTimer t(4.0 * N3 * prod, s);
             TC_TRY(cgemm_tc(precision, 1, tmU, tmX, e2, s));
         }
-        if (renorm_every > 0 && k % renorm_every == 0) TC_TRY(renorm(precision, b, s));
+        if (renorm_every > 0 && k % renorm_every == 0) TC_TRY(lowp_renorm(precision, b, s));
         if (obs)
             TC_TRY(launch_observables(kRhoPlanarF32, b.Rr, b.Ri, m, n, obs + (size_t)k * stride, b.scratch, s,
                                       (size_t)b.Np));
     }
-    finish_kernel<<<grid_for((size_t)b.N * b.N), 256, 0, s>>>(b.Rr, b.Ri, b.N, b.Np, reinterpret_cast<double2*>(rho));
-    TC_LAUNCH_CHECK();
-    return TC_OK;
+    return lowp_finish(b, rho, s);
 }
 
 }  // namespace tc
