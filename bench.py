@@ -50,7 +50,9 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["bf16x3", "tf32x3", "tf32", "fp64"], default="bf16x3")
-    ap.add_argument("--workload", choices=["n14", "n12", "n8"], default="n14")
+    ap.add_argument("--workload", choices=["n14", "n12", "n8", "batch", "grad"], default="n14",
+                    help="n14 (default, the metric's workload), n12, n8; batch: 64 systems n=6..12 "
+                         "(aggregate system-steps/s vs per-system sequential calls); grad: n=11 gradient")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the TF32 / TF32x3 / FP64 comparison forms")
@@ -375,8 +377,89 @@ def run_ours(a, cfg):
     return 0
 
 
+def run_batch(a):
+    """64 systems, n ~ U{6..12} (seed 2), 200 steps: one tc_batch_evolve vs per-system tc_evolve."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2403_06937_gb300 as tc
+    tc.device_check()
+    prec = a.precision
+    cfgs = W.config_batch(steps=200 if prec != "fp64" else 2)
+    steps = cfgs[0].steps
+    Us, rhos, ps = [], [], []
+    for c in cfgs:
+        p = tc.Params(c.n, list(map(float, c.g)), c.omega_a, c.omega_c)
+        Us.append(tc.expm(tc.build_hamiltonian(p), c.n, c.dt))
+        r = torch.zeros((c.N, c.N), dtype=torch.complex128, device="cuda")
+        r[-1, -1] = 1.0
+        rhos.append(r)
+        ps.append(p)
+    tc.batch_evolve(Us, rhos, 1, prec, params=ps)          # warm (attributes, modules)
+    torch.cuda.synchronize()
+    l0 = tc.launch_count()
+    t0 = time.perf_counter()
+    out, obs = tc.batch_evolve(Us, rhos, steps, prec, params=ps)
+    torch.cuda.synchronize()
+    tb = time.perf_counter() - t0
+    launches = tc.launch_count() - l0
+    t0 = time.perf_counter()
+    for U, r, p in zip(Us, rhos, ps):
+        tc.evolve(U, r, p.n, steps, prec, params=p)
+    torch.cuda.synchronize()
+    ts = time.perf_counter() - t0
+    credited = sum(12.0 * c.N ** 3 for c in cfgs) * steps
+    value = len(cfgs) * steps / tb
+    line = {"metric": "batched evolution: aggregate system-steps/s (64 systems, n=6..12)", "value": value,
+            "unit": "system-steps/s", "n_gpus": 1, "steps": steps, "warmup": 1, "ms_per_step": 1e3 * tb / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "bf16x3": "bf16", "tf32": "tf32", "tf32x3": "tf32"}[prec], "data": "synthetic",
+            "config": {"workload": "64 systems, n ~ U{6..12} seed 2, own g_i ~ U[0.005,0.015], dt=0.05, %d steps"
+                       % steps, "precision": prec, "ns": [c.n for c in cfgs]},
+            "credited_tflops": credited / tb / 1e12,
+            "sequential": {"value": len(cfgs) * steps / ts, "unit": "system-steps/s",
+                           "api": "tc_evolve per system, one after another"},
+            "speedup_vs_sequential": ts / tb, "gpu_launches": launches}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_grad(a):
+    """n = 11, 400 steps, checkpoints every 20: wall time of tc_evolve_backward (FP64)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2403_06937_gb300 as tc
+    tc.device_check()
+    cfg = W.config_n11_grad()
+    n, N = cfg.n, cfg.N
+    p = tc.Params(n, list(map(float, cfg.g)), cfg.omega_a, cfg.omega_c)
+    U = tc.expm(tc.build_hamiltonian(p), n, cfg.dt)
+    rho0 = torch.zeros((N, N), dtype=torch.complex128, device="cuda")
+    rho0[-1, -1] = 1.0
+    s = torch.arange(N, device="cuda")
+    O = ((s >> (n - cfg.loss_atom)) & 1).to(torch.float64)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    grad, loss = tc.evolve_backward(p, cfg.dt, cfg.steps, rho0, U, O, ckpt_every=cfg.ckpt_every)
+    t = time.perf_counter() - t0
+    # FP64 products: forward 12N^3 + recompute 12N^3 + Lambda 12N^3 + W 8N^3 per step
+    flops = cfg.steps * 44.0 * N ** 3
+    line = {"metric": "gradient wall time, n=11, 400 steps (FP64 adjoint + Frechet)", "value": t, "unit": "s",
+            "n_gpus": 1, "steps": cfg.steps, "warmup": 0, "ms_per_step": 1e3 * t / cfg.steps,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": cfg.description}, "loss": loss, "grad": grad.tolist(),
+            "fp64_tflops": flops / t / 1e12}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     a = _args()
+    if a.workload == "batch":
+        return run_batch(a)
+    if a.workload == "grad":
+        return run_grad(a)
     cfg = _workload(a.workload)
     if a.impl == "reference":
         return run_reference(a, cfg)

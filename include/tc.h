@@ -267,6 +267,27 @@ TC_API tc_status tc_evolve_host(const void* U, void* rho_host, int n, int steps,
                                 int renorm_every, const tc_params* params, double* obs_host,
                                 void* work, size_t work_bytes, void* stream);
 
+/* ------------------------------------------------------------- tuning */
+
+/* tc_autotune -- time every built configuration of the step products for n
+ * atoms at `precision` on synthetic operands in `work` and keep the fastest
+ * for later calls in this process (tc_evolve, tc_expm, tc_evolve_backward,
+ * tc_batch_evolve):
+ *   FP64: the DMMA GEMM tile, 32 x 32 or 64 x 64 (timed on a K slice);
+ *   tensor cores: the raster group of the X = U rho launch (4, 8, 16 row
+ *   tiles sharing U panels in L2) and the TMA ring depth (two per precision).
+ * The choice is also appended, one JSON object per line, to the file named by
+ * the environment variable TC_AUTOTUNE_CACHE (when set), which is read on the
+ * first lookup of a process.  Every configuration computes each output in the
+ * same order, so tuning changes speed, not results.  Synchronises `stream`.
+ *  work   : device, >= tc_workspace_size(n, precision, TC_OP_EVOLVE, 0, 0).
+ *  choice : host, 3 ints (f64 tile, raster group, ring depth), or NULL. */
+TC_API tc_status tc_autotune(int n, int precision, void* work, size_t work_bytes, void* stream, int* choice);
+
+/* The configuration tc_evolve will use for (n, precision): tuned if tuned in
+ * this process or found in TC_AUTOTUNE_CACHE, else the default.  Host only. */
+TC_API tc_status tc_autotune_lookup(int n, int precision, int* choice);
+
 /* ------------------------------------------------------------- batching */
 
 /* Bytes of `work` for tc_batch_evolve of `count` systems with n[b] atoms. */

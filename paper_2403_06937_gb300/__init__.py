@@ -224,6 +224,25 @@ def batch_evolve(Us, rhos, steps: int, precision="bf16x3", renorm_every: int = 0
     return outs, obs
 
 
+def autotune(n: int, precision="bf16x3", stream=None, work: Optional[torch.Tensor] = None):
+    """tc_autotune: time the built kernel configurations for (n, precision); returns the choice."""
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    need = workspace_size(n, prec, TC_OP_EVOLVE)
+    if work is None or work.numel() < need:
+        work = _work(need, "cuda")
+    out = (ctypes.c_int * 3)()
+    _abi.call("tc_autotune", n, prec, _ptr(work), work.numel(), ctypes.c_void_p(_stream(stream)), out)
+    return {"f64_tile": out[0], "tc_group": out[1], "tc_stages": out[2]}
+
+
+def autotune_lookup(n: int, precision="bf16x3"):
+    """tc_autotune_lookup: the configuration in use for (n, precision) (host only)."""
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    out = (ctypes.c_int * 3)()
+    _abi.call("tc_autotune_lookup", n, prec, out)
+    return {"f64_tile": out[0], "tc_group": out[1], "tc_stages": out[2]}
+
+
 def launch_count() -> int:
     """Kernels launched by libtc in this process."""
     return int(_abi.load().tc_launch_count())
@@ -247,7 +266,7 @@ def sync_status(stream=None) -> None:
 
 
 __all__ = ["Params", "TCError", "build_hamiltonian", "expm", "evolve", "evolve_host", "observables",
-           "evolve_backward", "EvolveFn", "batch_evolve",
+           "evolve_backward", "EvolveFn", "batch_evolve", "autotune", "autotune_lookup",
            "workspace_size", "launch_count", "timing_enable", "timing_read",
            "device_check", "sync_status", "obs_stride", "PRECISIONS", "TC_FP64", "TC_BF16X3", "TC_TF32",
            "TC_TF32X3", "TC_COUPLING_BOSONIC", "TC_COUPLING_QUBIT_PHOTON", "TC_OP_EXPM", "TC_OP_EVOLVE",

@@ -10,34 +10,13 @@
 #include <vector>
 
 #include "cgemm_batch.cuh"
+#include "graph.cuh"
 #include "cgemm_tc.cuh"
 #include "lowp.cuh"
 #include "paths.cuh"
 
 namespace tc {
 namespace {
-
-struct GraphStream {
-    cudaStream_t s = nullptr;
-    cudaEvent_t before = nullptr, after = nullptr;
-};
-std::mutex g_gs_mu;
-GraphStream g_gs[64];
-
-tc_status graph_stream(GraphStream** out) {
-    int dev = 0;
-    TC_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return fail(TC_ERR_UNSUPPORTED_DEVICE, "device index out of range");
-    std::lock_guard<std::mutex> lk(g_gs_mu);
-    GraphStream& g = g_gs[dev];
-    if (!g.s) {
-        TC_CUDA(cudaStreamCreateWithFlags(&g.s, cudaStreamNonBlocking));
-        TC_CUDA(cudaEventCreateWithFlags(&g.before, cudaEventDisableTiming));
-        TC_CUDA(cudaEventCreateWithFlags(&g.after, cudaEventDisableTiming));
-    }
-    *out = &g;
-    return TC_OK;
-}
 
 size_t f64_system_bytes(int n) {
     const size_t cm = 2 * round256(sizeof(double) << (2 * n));
@@ -103,54 +82,12 @@ TC_API tc_status tc_batch_evolve(int count, const int* n, const void* const* U, 
 
     Arena ar{static_cast<char*>(work), work_bytes, 0};
     BatchSys* sys_dev = ar.take<BatchSys>((size_t)count);
-    GraphStream* gs = nullptr;
-    TC_TRY(graph_stream(&gs));
-    cudaStream_t s = gs->s;
-    TC_CUDA(cudaEventRecord(gs->before, us));
-    TC_CUDA(cudaStreamWaitEvent(s, gs->before, 0));
+    cudaStream_t s = us;   // rebound to the capture stream inside run_captured
 
     std::vector<LowpBufs> lb(count);
     std::vector<F64Sys> fb(count);
     std::vector<BatchSys> host(count);
     int tiles[2] = {0, 0};
-    if (precision == TC_FP64) {
-        for (int k = 0; k < count; k++) {
-            const int b = order[k];
-            F64Sys& f = fb[k];
-            f.n = n[b];
-            f.N = 1 << n[b];
-            const size_t NN = (size_t)f.N * f.N;
-            f.Ur = ar.take<double>(NN); f.Ui = ar.take<double>(NN);
-            f.Rr = ar.take<double>(NN); f.Ri = ar.take<double>(NN);
-            f.Xr = ar.take<double>(NN); f.Xi = ar.take<double>(NN);
-            f.scratch = ar.take<double>(observables_scratch_bytes(n[b]) / sizeof(double));
-            if (!f.scratch) return fail(TC_ERR_WORKSPACE, "batch: workspace too small");
-            TC_TRY(launch_split_c128(static_cast<const double*>(U[b]), f.Ur, f.Ui, NN, s));
-            TC_TRY(launch_split_c128(static_cast<const double*>(rho[b]), f.Rr, f.Ri, NN, s));
-        }
-    } else {
-        for (int k = 0; k < count; k++) {
-            const int b = order[k];
-            TC_TRY(lowp_carve(n[b], precision, ar, lb[k]));
-            TC_TRY(lowp_prep(precision, static_cast<const double*>(U[b]), static_cast<const double*>(rho[b]), lb[k], s));
-            BatchSys& h = host[k];
-            std::memset(&h, 0, sizeof(h));
-            TC_TRY(make_part_map(&h.tmU, lb[k].Uparts, lb[k].Np, 2 * lb[k].S, precision));
-            TC_TRY(make_part_map(&h.tmR, lb[k].Rparts, lb[k].Np, 2 * lb[k].S, precision));
-            TC_TRY(make_part_map(&h.tmX, lb[k].Xparts, lb[k].Np, 2 * lb[k].S, precision));
-            h.Rr = lb[k].Rr; h.Ri = lb[k].Ri; h.Rparts = lb[k].Rparts;
-            h.Xr = lb[k].Xr; h.Xi = lb[k].Xi; h.Xparts = lb[k].Xparts;
-            h.Np = lb[k].Np;
-            h.tiles = lb[k].Np / 128;
-            h.tile_begin[0] = tiles[0];
-            h.tile_begin[1] = tiles[1];
-            tiles[0] += h.tiles * h.tiles;
-            tiles[1] += h.tiles * (h.tiles + 1) / 2;
-        }
-        TC_CUDA(cudaMemcpyAsync(sys_dev, host.data(), sizeof(BatchSys) * count, cudaMemcpyHostToDevice, s));
-        TC_CUDA(cudaStreamSynchronize(s));   // host copy of the descriptors may go
-    }
-
     auto observe = [&](int k, int row) -> tc_status {
         const int b = order[k];
         if (!obs || !obs[b]) return TC_OK;
@@ -162,8 +99,6 @@ TC_API tc_status tc_batch_evolve(int count, const int* n, const void* const* U, 
         return launch_observables(kRhoPlanarF32, lb[k].Rr, lb[k].Ri, mp, n[b], obs[b] + (size_t)row * stride,
                                   lb[k].scratch, s, (size_t)lb[k].Np);
     };
-    for (int k = 0; k < count; k++) TC_TRY(observe(k, 0));
-
     // one step of every system, enqueued on s
     unsigned* status = device_status_word();
     auto one_step = [&](int step) -> tc_status {
@@ -196,47 +131,73 @@ TC_API tc_status tc_batch_evolve(int count, const int* n, const void* const* U, 
         return TC_OK;
     };
 
-    if (steps > 0) {
-        // set kernel attributes outside the capture with one real step, then capture the rest
-        TC_TRY(one_step(1));
-        if (steps > 1) {
-            cudaGraph_t graph = nullptr;
-            cudaGraphExec_t exec = nullptr;
-            TC_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-            tc_status st = TC_OK;
-            for (int k = 2; k <= steps && st == TC_OK; k++) st = one_step(k);
-            cudaError_t ce = cudaStreamEndCapture(s, &graph);
-            if (st != TC_OK) {
-                if (graph) cudaGraphDestroy(graph);
-                return st;
-            }
-            if (ce != cudaSuccess) return fail(TC_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ce));
-            ce = cudaGraphInstantiate(&exec, graph, 0);
-            if (ce != cudaSuccess) {
-                cudaGraphDestroy(graph);
-                return fail(TC_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ce));
-            }
-            ce = cudaGraphLaunch(exec, s);
-            cudaError_t ce2 = cudaStreamSynchronize(s);
-            cudaGraphExecDestroy(exec);
-            cudaGraphDestroy(graph);
-            if (ce != cudaSuccess || ce2 != cudaSuccess)
-                return fail(TC_ERR_CUDA, "graph launch: %s", cudaGetErrorString(ce != cudaSuccess ? ce : ce2));
-        }
-    }
-    // results back to the callers' rho
-    for (int k = 0; k < count; k++) {
-        const int b = order[k];
+
+    auto first = [&](cudaStream_t cs) -> tc_status {
+        s = cs;
         if (precision == TC_FP64) {
-            const size_t NN = (size_t)fb[k].N * fb[k].N;
-            TC_TRY(launch_join_c128(fb[k].Rr, fb[k].Ri, static_cast<double*>(rho[b]), NN, s));
+            for (int k = 0; k < count; k++) {
+                const int b = order[k];
+                F64Sys& f = fb[k];
+                f.n = n[b];
+                f.N = 1 << n[b];
+                const size_t NN = (size_t)f.N * f.N;
+                f.Ur = ar.take<double>(NN); f.Ui = ar.take<double>(NN);
+                f.Rr = ar.take<double>(NN); f.Ri = ar.take<double>(NN);
+                f.Xr = ar.take<double>(NN); f.Xi = ar.take<double>(NN);
+                f.scratch = ar.take<double>(observables_scratch_bytes(n[b]) / sizeof(double));
+                if (!f.scratch) return fail(TC_ERR_WORKSPACE, "batch: workspace too small");
+                TC_TRY(launch_split_c128(static_cast<const double*>(U[b]), f.Ur, f.Ui, NN, s));
+                TC_TRY(launch_split_c128(static_cast<const double*>(rho[b]), f.Rr, f.Ri, NN, s));
+            }
         } else {
-            TC_TRY(lowp_finish(lb[k], static_cast<double*>(rho[b]), s));
+            for (int k = 0; k < count; k++) {
+                const int b = order[k];
+                TC_TRY(lowp_carve(n[b], precision, ar, lb[k]));
+                TC_TRY(lowp_prep(precision, static_cast<const double*>(U[b]), static_cast<const double*>(rho[b]), lb[k], s));
+                BatchSys& h = host[k];
+                std::memset(&h, 0, sizeof(h));
+                TC_TRY(make_part_map(&h.tmU, lb[k].Uparts, lb[k].Np, 2 * lb[k].S, precision));
+                TC_TRY(make_part_map(&h.tmR, lb[k].Rparts, lb[k].Np, 2 * lb[k].S, precision));
+                TC_TRY(make_part_map(&h.tmX, lb[k].Xparts, lb[k].Np, 2 * lb[k].S, precision));
+                h.Rr = lb[k].Rr; h.Ri = lb[k].Ri; h.Rparts = lb[k].Rparts;
+                h.Xr = lb[k].Xr; h.Xi = lb[k].Xi; h.Xparts = lb[k].Xparts;
+                h.Np = lb[k].Np;
+                h.tiles = lb[k].Np / 128;
+                h.tile_begin[0] = tiles[0];
+                h.tile_begin[1] = tiles[1];
+                tiles[0] += h.tiles * h.tiles;
+                tiles[1] += h.tiles * (h.tiles + 1) / 2;
+            }
+            TC_CUDA(cudaMemcpyAsync(sys_dev, host.data(), sizeof(BatchSys) * count, cudaMemcpyHostToDevice, s));
+            TC_CUDA(cudaStreamSynchronize(s));   // host copy of the descriptors may go
         }
-    }
-    TC_CUDA(cudaEventRecord(gs->after, s));
-    TC_CUDA(cudaStreamWaitEvent(us, gs->after, 0));
-    return TC_OK;
+
+
+        for (int k = 0; k < count; k++) TC_TRY(observe(k, 0));
+        if (steps > 0) TC_TRY(one_step(1));
+        return TC_OK;
+    };
+    auto rest = [&](cudaStream_t cs) -> tc_status {
+        s = cs;
+        for (int k = 2; k <= steps; k++) TC_TRY(one_step(k));
+        return TC_OK;
+    };
+    auto tail = [&](cudaStream_t cs) -> tc_status {
+        s = cs;
+        // results back to the callers' rho
+        for (int k = 0; k < count; k++) {
+            const int b = order[k];
+            if (precision == TC_FP64) {
+                const size_t NN = (size_t)fb[k].N * fb[k].N;
+                TC_TRY(launch_join_c128(fb[k].Rr, fb[k].Ri, static_cast<double*>(rho[b]), NN, s));
+            } else {
+                TC_TRY(lowp_finish(lb[k], static_cast<double*>(rho[b]), s));
+            }
+        }
+
+        return TC_OK;
+    };
+    return run_captured(us, first, rest, tail, steps > 1);
 }
 
 }  // extern "C"

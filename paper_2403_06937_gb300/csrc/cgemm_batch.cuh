@@ -9,7 +9,7 @@ namespace tc {
 
 // One system of a batch, kept in device memory (the caller's workspace).
 // The TMA descriptors must be 64-byte aligned.
-struct alignas(64) BatchSys {
+struct BatchSys {   // aligned as CUtensorMap (at least 64 bytes)
     CUtensorMap tmU;     // parts of V = U / c - I
     CUtensorMap tmR;     // parts of rho
     CUtensorMap tmX;     // parts of X

@@ -50,10 +50,10 @@ using namespace cg;
 
 constexpr int kThreads = 192;
 
-__device__ __forceinline__ void tile_of(int mode, int T, int b, int& I, int& J) {
+__device__ __forceinline__ void tile_of(int mode, int T, int G, int b, int& I, int& J) {
     if (mode == 0) {
-        // grouped raster: 8 row tiles share their U panels in L2
-        const int G = 8;
+        // grouped raster: G row tiles share their U panels in L2
+        if (G < 1) G = 1;
         int per_group = G * T;
         int g = b / per_group;
         int first = g * G;
@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int I, J;
-    tile_of(MODE, ep.tiles, blockIdx.x, I, J);
+    tile_of(MODE, ep.tiles, ep.group, blockIdx.x, I, J);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; s++) {
@@ -213,17 +213,27 @@ tc_status launch(const CUtensorMap& tmU, const CUtensorMap& tmP, const CgemmEpi&
 
 }  // namespace
 
+int cgemm_default_stages(int precision) { return precision == TC_BF16X3 ? 4 : precision == TC_TF32X3 ? 6 : 8; }
+int cgemm_alt_stages(int precision) { return precision == TC_BF16X3 ? 3 : precision == TC_TF32X3 ? 3 : 4; }
+
 tc_status cgemm_tc(int precision, int mode, const CUtensorMap& tmU, const CUtensorMap& tmP, const CgemmEpi& ep,
-                   cudaStream_t s) {
+                   cudaStream_t s, int stages) {
     if (ep.Np < 128 || ep.Np % 128 != 0 || ep.tiles * 128 != ep.Np)
         return fail(TC_ERR_INVALID_ARG, "cgemm_tc: padded dimension must be a multiple of 128");
     if (mode != 0 && mode != 1) return fail(TC_ERR_INVALID_ARG, "cgemm_tc: mode");
+    if (stages == 0) stages = cgemm_default_stages(precision);
+    const bool alt = stages == cgemm_alt_stages(precision);
+    if (!alt && stages != cgemm_default_stages(precision))
+        return fail(TC_ERR_INVALID_ARG, "cgemm_tc: %d stages not built for precision %d", stages, precision);
     switch (precision) {
         case TC_BF16X3:
+            if (alt) return mode == 0 ? launch<0, 3, 3, 0>(tmU, tmP, ep, s) : launch<0, 3, 3, 1>(tmU, tmP, ep, s);
             return mode == 0 ? launch<0, 3, 4, 0>(tmU, tmP, ep, s) : launch<0, 3, 4, 1>(tmU, tmP, ep, s);
         case TC_TF32:
+            if (alt) return mode == 0 ? launch<1, 1, 4, 0>(tmU, tmP, ep, s) : launch<1, 1, 4, 1>(tmU, tmP, ep, s);
             return mode == 0 ? launch<1, 1, 8, 0>(tmU, tmP, ep, s) : launch<1, 1, 8, 1>(tmU, tmP, ep, s);
         case TC_TF32X3:
+            if (alt) return mode == 0 ? launch<1, 2, 3, 0>(tmU, tmP, ep, s) : launch<1, 2, 3, 1>(tmU, tmP, ep, s);
             return mode == 0 ? launch<1, 2, 6, 0>(tmU, tmP, ep, s) : launch<1, 2, 6, 1>(tmU, tmP, ep, s);
         default:
             return fail(TC_ERR_INVALID_ARG, "cgemm_tc: precision %d has no tensor-core form", precision);

@@ -18,6 +18,7 @@ namespace tc {
 struct CgemmEpi {
     int Np;          // padded dimension, a multiple of 128 (row stride of every plane)
     int tiles;       // Np / 128
+    int group;       // mode 0: row tiles per raster group (tiles sharing U panels in L2)
     const float* pr; // FP32 planes of P (the identity term adds conj(P[j][i]))
     const float* pi;
     void* parts;     // [2 * S][Np][Np] operand parts of Y: re parts 0..S-1, then im parts
@@ -26,8 +27,12 @@ struct CgemmEpi {
     unsigned* status;
 };
 
+// stages: TMA ring depth (0 = the largest that fits); the built depths are
+// BF16x3 {4, 3}, TF32 {8, 4}, TF32x3 {6, 3}.
 tc_status cgemm_tc(int precision, int mode, const CUtensorMap& tmU, const CUtensorMap& tmP, const CgemmEpi& ep,
-                   cudaStream_t s);
+                   cudaStream_t s, int stages = 0);
+int cgemm_default_stages(int precision);
+int cgemm_alt_stages(int precision);
 
 int cgemm_parts(int precision);       // S: BF16x3 3, TF32x3 2, TF32 1
 int cgemm_products(int precision);    // part products per real product: 6, 3, 1

@@ -17,6 +17,7 @@
 #include <cuda_bf16.h>
 
 #include "cgemm_tc.cuh"
+#include "graph.cuh"
 #include "lowp.cuh"
 #include "paths.cuh"
 #include "timing.cuh"
@@ -291,9 +292,11 @@ tc_status evolve_lowp(const double* U, double* rho, int n, int steps, int precis
     TC_TRY(make_part_map(&tmR, b.Rparts, b.Np, 2 * b.S, precision));
     TC_TRY(make_part_map(&tmX, b.Xparts, b.Np, 2 * b.S, precision));
 
+    const TuneChoice tune = tune_lookup(n, precision);
     CgemmEpi e1{};                 // X = rho^H + V rho^H
     e1.Np = b.Np;
     e1.tiles = b.Np / 128;
+    e1.group = tune.tc_group;
     e1.pr = b.Rr;
     e1.pi = b.Ri;
     e1.parts = b.Xparts;
@@ -311,23 +314,33 @@ tc_status evolve_lowp(const double* U, double* rho, int n, int steps, int precis
     const double N3 = (double)b.N * b.N * b.N;
     const double prod = (double)cgemm_products(precision);
 
-    TC_TRY(lowp_prep(precision, U, rho, b, s));
-    if (obs) TC_TRY(launch_observables(kRhoPlanarF32, b.Rr, b.Ri, m, n, obs, b.scratch, s, (size_t)b.Np));
-    for (int k = 1; k <= steps; k++) {
+    auto one_step = [&](int k, cudaStream_t cs) -> tc_status {
         {
-            ProductTimer t(8.0 * N3 * prod, s);
-            TC_TRY(cgemm_tc(precision, 0, tmU, tmR, e1, s));
+            ProductTimer t(8.0 * N3 * prod, cs);
+            TC_TRY(cgemm_tc(precision, 0, tmU, tmR, e1, cs, tune.tc_stages));
         }
         {
-            ProductTimer t(4.0 * N3 * prod, s);
-            TC_TRY(cgemm_tc(precision, 1, tmU, tmX, e2, s));
+            ProductTimer t(4.0 * N3 * prod, cs);
+            TC_TRY(cgemm_tc(precision, 1, tmU, tmX, e2, cs, tune.tc_stages));
         }
-        if (renorm_every > 0 && k % renorm_every == 0) TC_TRY(lowp_renorm(precision, b, s));
+        if (renorm_every > 0 && k % renorm_every == 0) TC_TRY(lowp_renorm(precision, b, cs));
         if (obs)
-            TC_TRY(launch_observables(kRhoPlanarF32, b.Rr, b.Ri, m, n, obs + (size_t)k * stride, b.scratch, s,
+            TC_TRY(launch_observables(kRhoPlanarF32, b.Rr, b.Ri, m, n, obs + (size_t)k * stride, b.scratch, cs,
                                       (size_t)b.Np));
-    }
-    return lowp_finish(b, rho, s);
+        return TC_OK;
+    };
+    auto first = [&](cudaStream_t cs) -> tc_status {
+        TC_TRY(lowp_prep(precision, U, rho, b, cs));
+        if (obs) TC_TRY(launch_observables(kRhoPlanarF32, b.Rr, b.Ri, m, n, obs, b.scratch, cs, (size_t)b.Np));
+        if (steps >= 1) TC_TRY(one_step(1, cs));
+        return TC_OK;
+    };
+    auto rest = [&](cudaStream_t cs) -> tc_status {
+        for (int k = 2; k <= steps; k++) TC_TRY(one_step(k, cs));
+        return TC_OK;
+    };
+    auto tail = [&](cudaStream_t cs) -> tc_status { return lowp_finish(b, rho, cs); };
+    return run_captured(s, first, rest, tail, steps > 2 && !timing_enabled());
 }
 
 }  // namespace tc

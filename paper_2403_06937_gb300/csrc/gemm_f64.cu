@@ -15,10 +15,9 @@
 namespace tc {
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16;
+constexpr int BK = 16;
 constexpr int LDA_S = BK + 4;   // padded smem strides (doubles): conflict-free fragment reads
-constexpr int LDB_S = BN + 4;
-constexpr int kThreads = 128;
+constexpr int kThreads = 128;   // 2 x 2 warps, each a (BT/2) x (BT/2) sub-tile
 
 __device__ __forceinline__ void dmma(double (&d)[4], const double (&a)[4], const double (&b)[2]) {
     asm volatile(
@@ -37,8 +36,11 @@ __device__ __forceinline__ void lower_tile(int b, int& bi, int& bj) {
     bj = b - i * (i + 1) / 2;
 }
 
-template <bool CPLX>
+template <bool CPLX, int BT>
 __global__ void __launch_bounds__(kThreads, 1) gemm_f64_kernel(GemmF64 p) {
+    constexpr int BM = BT, BN = BT;
+    constexpr int LDB_S = BN + 4;
+    constexpr int MI = BT / 32, NI = BT / 16;   // m16 / n8 fragments per warp
     __shared__ double sAr[BM * LDA_S];
     __shared__ double sBr[BK * LDB_S];
     __shared__ double sAi[CPLX ? BM * LDA_S : 1];
@@ -53,14 +55,14 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_f64_kernel(GemmF64 p) {
     }
     const int m0 = tile_m * BM, n0 = tile_n * BN;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    const int wm = (warp >> 1) * (BT / 2), wn = (warp & 1) * (BT / 2);
     const int gq = lane >> 2, tq = lane & 3;
 
-    double accr[2][4][4], acci[2][4][4];
+    double accr[MI][NI][4], acci[MI][NI][4];
 #pragma unroll
-    for (int a = 0; a < 2; a++)
+    for (int a = 0; a < MI; a++)
 #pragma unroll
-        for (int b = 0; b < 4; b++)
+        for (int b = 0; b < NI; b++)
 #pragma unroll
             for (int c = 0; c < 4; c++) { accr[a][b][c] = 0.0; acci[a][b][c] = 0.0; }
 
@@ -93,9 +95,9 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_f64_kernel(GemmF64 p) {
 
 #pragma unroll
         for (int kk = 0; kk < BK; kk += 8) {
-            double ar[2][4], ai[2][4], nai[2][4], br[4][2], bi[4][2];
+            double ar[MI][4], ai[MI][4], nai[MI][4], br[NI][2], bi[NI][2];
 #pragma unroll
-            for (int mi = 0; mi < 2; mi++) {
+            for (int mi = 0; mi < MI; mi++) {
                 int r0 = wm + mi * 16 + gq;
                 ar[mi][0] = sAr[r0 * LDA_S + kk + tq];
                 ar[mi][1] = sAr[(r0 + 8) * LDA_S + kk + tq];
@@ -111,7 +113,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_f64_kernel(GemmF64 p) {
                 }
             }
 #pragma unroll
-            for (int ni = 0; ni < 4; ni++) {
+            for (int ni = 0; ni < NI; ni++) {
                 int c0 = wn + ni * 8 + gq;
                 br[ni][0] = sBr[(kk + tq) * LDB_S + c0];
                 br[ni][1] = sBr[(kk + tq + 4) * LDB_S + c0];
@@ -121,9 +123,9 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_f64_kernel(GemmF64 p) {
                 }
             }
 #pragma unroll
-            for (int mi = 0; mi < 2; mi++)
+            for (int mi = 0; mi < MI; mi++)
 #pragma unroll
-                for (int ni = 0; ni < 4; ni++) {
+                for (int ni = 0; ni < NI; ni++) {
                     dmma(accr[mi][ni], ar[mi], br[ni]);
                     if (CPLX) {
                         dmma(accr[mi][ni], nai[mi], bi[ni]);   // - Ai Bi
@@ -138,9 +140,9 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_f64_kernel(GemmF64 p) {
     // epilogue: C = alpha * acc + beta * C  (fragment c0..c3 -> rows g, g+8; cols 2t, 2t+1)
     const bool diag_tile = p.herm_lower && tile_m == tile_n;
 #pragma unroll
-    for (int mi = 0; mi < 2; mi++)
+    for (int mi = 0; mi < MI; mi++)
 #pragma unroll
-        for (int ni = 0; ni < 4; ni++)
+        for (int ni = 0; ni < NI; ni++)
 #pragma unroll
             for (int q = 0; q < 4; q++) {
                 int row = m0 + wm + mi * 16 + gq + ((q >> 1) << 3);
@@ -172,26 +174,36 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_f64_kernel(GemmF64 p) {
             }
 }
 
+template <int BT>
+tc_status launch_bt(const GemmF64& g, cudaStream_t s) {
+    dim3 block(kThreads);
+    dim3 grid;
+    if (g.herm_lower) {
+        long t = (g.N + BT - 1) / BT;
+        grid = dim3((unsigned)(t * (t + 1) / 2));
+    } else {
+        grid = dim3((g.N + BT - 1) / BT, (g.M + BT - 1) / BT);
+    }
+    if (g.cplx)
+        gemm_f64_kernel<true, BT><<<grid, block, 0, s>>>(g);
+    else
+        gemm_f64_kernel<false, BT><<<grid, block, 0, s>>>(g);
+    TC_LAUNCH_CHECK();
+    return TC_OK;
+}
+
 }  // namespace
+
+int gemm_f64_default_tile(int N) { return N >= 4096 ? 64 : 32; }
 
 tc_status gemm_f64(const GemmF64& g, cudaStream_t s) {
     if (g.M <= 0 || g.N <= 0 || g.K <= 0) return TC_OK;
     if (g.herm_lower && (g.M != g.N || g.beta != 0.0))
         return fail(TC_ERR_INVALID_ARG, "gemm_f64: Hermitian mode needs M == N and beta == 0");
-    dim3 block(kThreads);
-    dim3 grid;
-    if (g.herm_lower) {
-        long t = (g.N + BN - 1) / BN;
-        grid = dim3((unsigned)(t * (t + 1) / 2));
-    } else {
-        grid = dim3((g.N + BN - 1) / BN, (g.M + BM - 1) / BM);
-    }
-    if (g.cplx)
-        gemm_f64_kernel<true><<<grid, block, 0, s>>>(g);
-    else
-        gemm_f64_kernel<false><<<grid, block, 0, s>>>(g);
-    TC_LAUNCH_CHECK();
-    return TC_OK;
+    const int tile = g.tile ? g.tile : tuned_f64_tile(g.N > g.M ? g.N : g.M);
+    if (tile == 32) return launch_bt<32>(g, s);
+    if (tile == 64) return launch_bt<64>(g, s);
+    return fail(TC_ERR_INVALID_ARG, "gemm_f64: tile %d not built (32 or 64)", tile);
 }
 
 }  // namespace tc

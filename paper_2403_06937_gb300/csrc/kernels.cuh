@@ -31,8 +31,20 @@ struct GemmF64 {
     int conjA, conjB;
     int cplx;
     int herm_lower;
+    int tile;        // 32 or 64 (square CTA tile); 0 = the tuned or default choice for this size
 };
 tc_status gemm_f64(const GemmF64& g, cudaStream_t s);
+int gemm_f64_default_tile(int N);
+
+// ---------------------------------------------------------------- tuning
+// Kernel configuration chosen by tc_autotune (or the default) per (N, precision).
+struct TuneChoice {
+    int f64_tile;    // FP64 DMMA GEMM tile: 32 or 64
+    int tc_group;    // tensor-core GEMM: row tiles per raster group (L2 reuse of U panels)
+    int tc_stages;   // tensor-core GEMM: TMA ring depth
+};
+TuneChoice tune_lookup(int n, int precision);
+int tuned_f64_tile(int N);
 
 // ---------------------------------------------------------------- elementwise
 // out = c0*I + sum_j c[j] * M_j (real N x N, up to 4 terms; M_j may alias out)

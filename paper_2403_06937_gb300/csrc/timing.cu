@@ -33,6 +33,8 @@ cudaEvent_t take_event() {
 
 void count_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
+bool timing_enabled() { return g_timing_on.load() != 0; }
+
 ProductTimer::ProductTimer(double flops, cudaStream_t s) : flops_(flops), s_(s) {
     if (!g_timing_on.load()) return;
     std::lock_guard<std::mutex> lk(g_mu);

@@ -5,6 +5,10 @@
 
 namespace tc {
 
+// True while tc_timing_enable(1) is in effect (the step loops then launch
+// directly instead of through a CUDA graph, so each launch is bracketed).
+bool timing_enabled();
+
 // RAII: when timing is enabled, records an event pair around the enclosed
 // product-kernel launch(es) on stream `s`, credited with `flops`.
 class ProductTimer {

@@ -1,0 +1,270 @@
+// tune.cu -- the autotuner of the step products.
+//
+// For one (n, precision) it times every built configuration of the kernels a
+// step launches, on synthetic operands laid out exactly as tc_evolve lays
+// them out in the caller's workspace, and keeps the fastest:
+//   FP64:         the DMMA GEMM tile (32 x 32 or 64 x 64 complex elements);
+//   tensor cores: the raster group of the X = U rho launch (row tiles whose
+//                 U panels are shared through L2: 4, 8 or 16) and the depth
+//                 of the TMA ring (two built depths per precision).
+// The choice lives in a process-wide table that tc_evolve, tc_expm and
+// tc_evolve_backward consult, and is appended as one JSON object per line to
+// the file named by TC_AUTOTUNE_CACHE (read back on the first lookup), keyed
+// by the device architecture, n and the precision.  Every configuration
+// computes every output element in the same order, so the choice changes
+// speed, not results.
+#include <cstdio>
+#include <cstdlib>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include <cuda_bf16.h>
+
+#include "cgemm_tc.cuh"
+#include "lowp.cuh"
+#include "paths.cuh"
+
+namespace tc {
+namespace {
+
+struct Key {
+    int arch, n, precision;
+    bool operator<(const Key& o) const {
+        if (arch != o.arch) return arch < o.arch;
+        if (n != o.n) return n < o.n;
+        return precision < o.precision;
+    }
+};
+std::mutex g_mu;
+std::map<Key, TuneChoice> g_table;
+bool g_loaded = false;
+
+int current_arch() {
+    int dev = 0, major = 0, minor = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    return major * 10 + minor;
+}
+
+TuneChoice default_choice(int n, int precision) {
+    TuneChoice c;
+    c.f64_tile = gemm_f64_default_tile(1 << n);
+    c.tc_group = 8;
+    c.tc_stages = precision == TC_FP64 ? 0 : cgemm_default_stages(precision);
+    return c;
+}
+
+void load_cache_locked() {
+    if (g_loaded) return;
+    g_loaded = true;
+    const char* path = std::getenv("TC_AUTOTUNE_CACHE");
+    if (!path || !*path) return;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return;
+    char line[512];
+    while (std::fgets(line, sizeof(line), f)) {
+        int arch = 0, n = 0, prec = 0, tile = 0, group = 0, stages = 0;
+        if (std::sscanf(line,
+                        " {\"arch\": %d, \"n\": %d, \"precision\": %d, \"f64_tile\": %d, \"tc_group\": %d, "
+                        "\"tc_stages\": %d",
+                        &arch, &n, &prec, &tile, &group, &stages) == 6) {
+            TuneChoice c{tile, group, stages};
+            g_table[Key{arch, n, prec}] = c;
+        }
+    }
+    std::fclose(f);
+}
+
+void save_entry(int arch, int n, int prec, const TuneChoice& c, double ms) {
+    const char* path = std::getenv("TC_AUTOTUNE_CACHE");
+    if (!path || !*path) return;
+    FILE* f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f,
+                 "{\"arch\": %d, \"n\": %d, \"precision\": %d, \"f64_tile\": %d, \"tc_group\": %d, "
+                 "\"tc_stages\": %d, \"ms\": %.6f}\n",
+                 arch, n, prec, c.f64_tile, c.tc_group, c.tc_stages, ms);
+    std::fclose(f);
+}
+
+// counter-based pattern in [-0.005, 0.005): realistic magnitudes, no NaN/Inf
+__device__ __forceinline__ float pattern(size_t i, uint32_t seed) {
+    uint32_t h = (uint32_t)(i * 2654435761u) ^ seed;
+    h ^= h >> 15;
+    h *= 2246822519u;
+    h ^= h >> 13;
+    return ((float)(h & 0xFFFFu) / 65536.0f - 0.5f) * 0.01f;
+}
+__global__ void fill_f64(double* p, size_t n, uint32_t seed) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        p[i] = (double)pattern(i, seed);
+}
+__global__ void fill_f32(float* p, size_t n, uint32_t seed) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        p[i] = pattern(i, seed);
+}
+__global__ void fill_bf16(__nv_bfloat16* p, size_t n, uint32_t seed) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        p[i] = __float2bfloat16_rn(pattern(i, seed));
+}
+
+template <typename F>
+tc_status time_ms(cudaStream_t s, int reps, F launch, double* best) {
+    cudaEvent_t a, b;
+    TC_CUDA(cudaEventCreate(&a));
+    TC_CUDA(cudaEventCreate(&b));
+    tc_status st = launch();   // warm-up
+    *best = 1e30;
+    for (int r = 0; r < reps && st == TC_OK; r++) {
+        cudaEventRecord(a, s);
+        st = launch();
+        cudaEventRecord(b, s);
+        if (st != TC_OK) break;
+        if (cudaEventSynchronize(b) != cudaSuccess) {
+            st = fail(TC_ERR_CUDA, "autotune: event wait failed");
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        if (ms < *best) *best = ms;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return st;
+}
+
+}  // namespace
+
+TuneChoice tune_lookup(int n, int precision) {
+    const int arch = current_arch();
+    std::lock_guard<std::mutex> lk(g_mu);
+    load_cache_locked();
+    auto it = g_table.find(Key{arch, n, precision});
+    if (it != g_table.end()) return it->second;
+    return default_choice(n, precision);
+}
+
+int tuned_f64_tile(int N) {
+    int n = 0;
+    while ((1 << n) < N && n < 30) n++;
+    return tune_lookup(n, TC_FP64).f64_tile;
+}
+
+}  // namespace tc
+
+using namespace tc;
+
+extern "C" {
+
+TC_API tc_status tc_autotune_lookup(int n, int precision, int* choice) {
+    if (n < 1 || n > kMaxAtoms || !choice) return fail(TC_ERR_INVALID_ARG, "tc_autotune_lookup: bad argument");
+    if (precision < TC_FP64 || precision > TC_TF32X3) return fail(TC_ERR_INVALID_ARG, "unknown precision");
+    const TuneChoice c = tune_lookup(n, precision);
+    choice[0] = c.f64_tile;
+    choice[1] = c.tc_group;
+    choice[2] = c.tc_stages;
+    return TC_OK;
+}
+
+TC_API tc_status tc_autotune(int n, int precision, void* work, size_t work_bytes, void* stream, int* choice) {
+    if (n < 1 || n > kMaxAtoms) return fail(TC_ERR_INVALID_ARG, "n = %d outside 1..16", n);
+    if (precision < TC_FP64 || precision > TC_TF32X3) return fail(TC_ERR_INVALID_ARG, "unknown precision");
+    const size_t need = tc_workspace_size(n, precision, TC_OP_EVOLVE, 0, 0);
+    if (!work) return fail(TC_ERR_WORKSPACE, "work is NULL (need %zu bytes)", need);
+    if (reinterpret_cast<uintptr_t>(work) & 255u) return fail(TC_ERR_WORKSPACE, "work is not 256-byte aligned");
+    if (work_bytes < need) return fail(TC_ERR_WORKSPACE, "work has %zu bytes, need %zu", work_bytes, need);
+    TC_TRY(check_device());
+    cudaStream_t s = as_stream(stream);
+    const int N = 1 << n;
+    const size_t NN = (size_t)N * N;
+    const unsigned blocks = 152 * 8;
+    Arena ar{static_cast<char*>(work), work_bytes, 0};
+    TuneChoice best_c = default_choice(n, precision);
+    double best_ms = 1e30;
+
+    if (precision == TC_FP64) {
+        double* pl[6];
+        for (int k = 0; k < 6; k++) {
+            pl[k] = ar.take<double>(NN);
+            fill_f64<<<blocks, 256, 0, s>>>(pl[k], NN, 17u + k);
+            TC_LAUNCH_CHECK();
+        }
+        // X = U rho over a K slice (FP64 at full K takes tens of seconds at n = 14)
+        const int K = N < 1024 ? N : 1024;
+        for (int tile : {32, 64}) {
+            GemmF64 g{};
+            g.M = g.N = N;
+            g.K = K;
+            g.Ar = pl[0]; g.Ai = pl[1]; g.lda = N;
+            g.Br = pl[2]; g.Bi = pl[3]; g.ldb = N;
+            g.Cr = pl[4]; g.Ci = pl[5]; g.ldc = N;
+            g.alpha = 1.0;
+            g.cplx = 1;
+            g.tile = tile;
+            double ms = 0.0;
+            TC_TRY(time_ms(s, 2, [&]() { return gemm_f64(g, s); }, &ms));
+            if (ms < best_ms) {
+                best_ms = ms;
+                best_c.f64_tile = tile;
+            }
+        }
+    } else {
+        LowpBufs b{};
+        TC_TRY(lowp_carve(n, precision, ar, b));
+        const size_t planes = (size_t)2 * b.S * b.Np * b.Np;
+        if (b.E == 2) {
+            fill_bf16<<<blocks, 256, 0, s>>>(static_cast<__nv_bfloat16*>(b.Uparts), planes, 3u);
+            fill_bf16<<<blocks, 256, 0, s>>>(static_cast<__nv_bfloat16*>(b.Rparts), planes, 5u);
+        } else {
+            fill_f32<<<blocks, 256, 0, s>>>(static_cast<float*>(b.Uparts), planes, 3u);
+            fill_f32<<<blocks, 256, 0, s>>>(static_cast<float*>(b.Rparts), planes, 5u);
+        }
+        TC_LAUNCH_CHECK();
+        fill_f32<<<blocks, 256, 0, s>>>(b.Rr, (size_t)b.Np * b.Np, 7u);
+        fill_f32<<<blocks, 256, 0, s>>>(b.Ri, (size_t)b.Np * b.Np, 9u);
+        TC_LAUNCH_CHECK();
+        CUtensorMap tmU, tmR;
+        TC_TRY(make_part_map(&tmU, b.Uparts, b.Np, 2 * b.S, precision));
+        TC_TRY(make_part_map(&tmR, b.Rparts, b.Np, 2 * b.S, precision));
+        CgemmEpi e{};
+        e.Np = b.Np;
+        e.tiles = b.Np / 128;
+        e.pr = b.Rr;
+        e.pi = b.Ri;
+        e.parts = b.Xparts;
+        e.yr = b.Xr;
+        e.yi = b.Xi;
+        e.status = device_status_word();
+        for (int stages : {cgemm_default_stages(precision), cgemm_alt_stages(precision)}) {
+            for (int group : {4, 8, 16}) {
+                e.group = group;
+                double ms = 0.0;
+                TC_TRY(time_ms(s, 3, [&]() { return cgemm_tc(precision, 0, tmU, tmR, e, s, stages); }, &ms));
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best_c.tc_group = group;
+                    best_c.tc_stages = stages;
+                }
+            }
+        }
+    }
+    TC_CUDA(cudaStreamSynchronize(s));
+    const int arch = current_arch();
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        load_cache_locked();
+        g_table[Key{arch, n, precision}] = best_c;
+    }
+    save_entry(arch, n, precision, best_c, best_ms);
+    if (choice) {
+        choice[0] = best_c.f64_tile;
+        choice[1] = best_c.tc_group;
+        choice[2] = best_c.tc_stages;
+    }
+    return TC_OK;
+}
+
+}  // extern "C"

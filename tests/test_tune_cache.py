@@ -1,0 +1,30 @@
+"""The autotuner's cache file is read back by a new process (host only)."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+SCRIPT = r"""
+import json, sys
+sys.path.insert(0, %r)
+from paper_2403_06937_gb300 import build
+build.build()
+import paper_2403_06937_gb300 as tc
+print(json.dumps([tc.autotune_lookup(11, 'bf16x3'), tc.autotune_lookup(11, 'fp64'), tc.autotune_lookup(12, 'bf16x3')]))
+"""
+
+
+def test_cache_file_is_read_on_first_lookup(tmp_path):
+    cache = tmp_path / "tune.jsonl"
+    # arch 0: the key a process without a CUDA device looks up
+    cache.write_text('{"arch": 0, "n": 11, "precision": 1, "f64_tile": 64, "tc_group": 16, "tc_stages": 3, "ms": 1.0}\n'
+                     '{"arch": 0, "n": 11, "precision": 0, "f64_tile": 64, "tc_group": 8, "tc_stages": 0, "ms": 2.0}\n'
+                     'not json\n')
+    env = dict(os.environ, TC_AUTOTUNE_CACHE=str(cache))
+    out = subprocess.run([sys.executable, "-c", SCRIPT % ROOT], env=env, capture_output=True, text=True, check=True)
+    a, b, c = json.loads(out.stdout.strip().splitlines()[-1])
+    assert a == {"f64_tile": 64, "tc_group": 16, "tc_stages": 3}
+    assert b["f64_tile"] == 64
+    assert c["tc_group"] == 8 and c["tc_stages"] == 4      # untuned: the defaults
