@@ -37,10 +37,13 @@ import workloads as W  # noqa: E402
 
 METRIC = "evolution steps/s and complex-GEMM TFLOP/s at n=14 (FP64 vs split-BF16) at stated error"
 
-# dram bytes (read + write) per launch of the dominant kernel from one ncu
-# capture, scaled to the benchmark's launch; None until captured for the
-# current kernel.  Keyed by (precision, n).
-NCU_TRAFFIC = {}
+# DRAM bytes (read + write) per launch of the dominant kernel, averaged over
+# the launches of one ncu capture of the benchmark's own command (one pass:
+# dram__bytes_read.sum + dram__bytes_write.sum); None until captured for the
+# current kernel build.  Keyed by (precision, n).  Source: profiles/
+# cgemm_tc_bf16x3.md (n = 14: X = U rho 227.5 / 243.7 GB, rho' half 111.1 /
+# 108.2 GB per launch).
+NCU_TRAFFIC = {("bf16x3", 14): 172.6e9}
 
 
 def _args():
@@ -302,6 +305,8 @@ def run_ours(a, cfg):
     achieved = r["kflops"] / (r["kms"] * 1e-3) / 1e12 if r["kms"] > 0 else 0.0
     roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak if peak else None, "traffic": NCU_TRAFFIC.get((prec, n)),
+            "traffic_unit": "DRAM bytes per launch (ncu), algorithmic operand bytes ~%.1e" % (
+                (3 * 2 * {"fp64": 8, "bf16x3": 6, "tf32": 4, "tf32x3": 8}[prec] + 8) * N * N),
             "kernel": "complex GEMM (%s), %d launches timed, %.3f ms avg" % (prec, r["klaunch"],
                                                                              r["kms"] / max(r["klaunch"], 1)),
             "peak_source": peak_note,

@@ -186,6 +186,11 @@ TC_API tc_status tc_expm(const double* H, int n, double dt, const tc_expm_opts* 
  *  obs      : device, (steps + 1) * TC_OBS_STRIDE(n) doubles, or NULL.  Row 0
  *             is rho_0, row k is rho after step k.
  *  work     : device, >= tc_workspace_size(n, precision, TC_OP_EVOLVE, 0, 0).
+ *  With steps > 2 (and kernel timing off) steps 2..K are captured into one
+ *  CUDA graph and launched on a library-owned stream ordered after `stream`;
+ *  `stream` is ordered after it, and the call returns without waiting.  If
+ *  `stream` is itself being captured, the launches go into the caller's
+ *  graph instead.
  *  Errors: TC_ERR_INVALID_ARG, TC_ERR_WORKSPACE, TC_ERR_CUDA. */
 TC_API tc_status tc_evolve(const void* U, void* rho, int n, int steps, int precision,
                            int renorm_every, const tc_params* params, double* obs,
@@ -274,8 +279,10 @@ TC_API tc_status tc_evolve_host(const void* U, void* rho_host, int n, int steps,
  * for later calls in this process (tc_evolve, tc_expm, tc_evolve_backward,
  * tc_batch_evolve):
  *   FP64: the DMMA GEMM tile, 32 x 32 or 64 x 64 (timed on a K slice);
- *   tensor cores: the raster group of the X = U rho launch (4, 8, 16 row
- *   tiles sharing U panels in L2) and the TMA ring depth (two per precision).
+ *   tensor cores: the raster group G (G row tiles at a time for X = U rho,
+ *   G x G super-blocks of the lower triangle for the Hermitian product, so
+ *   concurrent CTAs share operand panels in L2; 4, 8, 12, 16) and the TMA
+ *   ring depth (two per precision), timed over one whole step.
  * The choice is also appended, one JSON object per line, to the file named by
  * the environment variable TC_AUTOTUNE_CACHE (when set), which is read on the
  * first lookup of a process.  Every configuration computes each output in the
@@ -287,6 +294,10 @@ TC_API tc_status tc_autotune(int n, int precision, void* work, size_t work_bytes
 /* The configuration tc_evolve will use for (n, precision): tuned if tuned in
  * this process or found in TC_AUTOTUNE_CACHE, else the default.  Host only. */
 TC_API tc_status tc_autotune_lookup(int n, int precision, int* choice);
+
+/* Pin the configuration for (n, precision) in this process (host only):
+ * choice = {f64 tile 32 | 64, raster group 1..128, a built ring depth}. */
+TC_API tc_status tc_autotune_set(int n, int precision, const int* choice);
 
 /* ------------------------------------------------------------- batching */
 

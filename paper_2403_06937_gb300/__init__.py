@@ -243,6 +243,15 @@ def autotune_lookup(n: int, precision="bf16x3"):
     return {"f64_tile": out[0], "tc_group": out[1], "tc_stages": out[2]}
 
 
+def autotune_set(n: int, precision="bf16x3", f64_tile: int = 32, tc_group: int = 8, tc_stages: int = 0) -> None:
+    """tc_autotune_set: pin the configuration for (n, precision) in this process."""
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    if prec != TC_FP64 and tc_stages == 0:
+        tc_stages = {TC_BF16X3: 4, TC_TF32X3: 6, TC_TF32: 8}[prec]
+    arr = (ctypes.c_int * 3)(int(f64_tile), int(tc_group), int(tc_stages))
+    _abi.call("tc_autotune_set", n, prec, arr)
+
+
 def launch_count() -> int:
     """Kernels launched by libtc in this process."""
     return int(_abi.load().tc_launch_count())
@@ -266,7 +275,7 @@ def sync_status(stream=None) -> None:
 
 
 __all__ = ["Params", "TCError", "build_hamiltonian", "expm", "evolve", "evolve_host", "observables",
-           "evolve_backward", "EvolveFn", "batch_evolve", "autotune", "autotune_lookup",
+           "evolve_backward", "EvolveFn", "batch_evolve", "autotune", "autotune_lookup", "autotune_set",
            "workspace_size", "launch_count", "timing_enable", "timing_read",
            "device_check", "sync_status", "obs_stride", "PRECISIONS", "TC_FP64", "TC_BF16X3", "TC_TF32",
            "TC_TF32X3", "TC_COUPLING_BOSONIC", "TC_COUPLING_QUBIT_PHOTON", "TC_OP_EXPM", "TC_OP_EVOLVE",

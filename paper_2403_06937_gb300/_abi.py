@@ -59,6 +59,7 @@ SIGNATURES = {
     "tc_evolve_host": (I, [VP, VP, I, I, I, I, ctypes.POINTER(tc_params), VP, VP, SZ, VP]),
     "tc_autotune": (I, [I, I, VP, SZ, VP, ctypes.POINTER(I)]),
     "tc_autotune_lookup": (I, [I, I, ctypes.POINTER(I)]),
+    "tc_autotune_set": (I, [I, I, ctypes.POINTER(I)]),
     "tc_batch_workspace_size": (SZ, [I, ctypes.POINTER(I), I]),
     "tc_batch_evolve": (I, [I, ctypes.POINTER(I), ctypes.POINTER(VP), ctypes.POINTER(VP), I, I, I,
                             ctypes.POINTER(tc_params), ctypes.POINTER(VP), VP, SZ, VP]),

@@ -31,6 +31,12 @@ tc_status graph_stream(GraphStream** out) {
 tc_status run_captured(cudaStream_t user, const std::function<tc_status(cudaStream_t)>& first,
                        const std::function<tc_status(cudaStream_t)>& rest,
                        const std::function<tc_status(cudaStream_t)>& tail, bool capture) {
+    if (capture) {
+        // a caller already capturing `user` gets the launches in its own graph
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        TC_CUDA(cudaStreamIsCapturing(user, &cs));
+        if (cs != cudaStreamCaptureStatusNone) capture = false;
+    }
     if (!capture) {
         TC_TRY(first(user));
         TC_TRY(rest(user));

@@ -4,9 +4,10 @@
 // step launches, on synthetic operands laid out exactly as tc_evolve lays
 // them out in the caller's workspace, and keeps the fastest:
 //   FP64:         the DMMA GEMM tile (32 x 32 or 64 x 64 complex elements);
-//   tensor cores: the raster group of the X = U rho launch (row tiles whose
-//                 U panels are shared through L2: 4, 8 or 16) and the depth
-//                 of the TMA ring (two built depths per precision).
+//   tensor cores: the raster group G (the X = U rho launch takes G row
+//                 tiles at a time, the Hermitian launch G x G super-blocks,
+//                 so concurrent CTAs share operand panels in L2: 4, 8, 12,
+//                 16) and the depth of the TMA ring (two per precision).
 // The choice lives in a process-wide table that tc_evolve, tc_expm and
 // tc_evolve_backward consult, and is appended as one JSON object per line to
 // the file named by TC_AUTOTUNE_CACHE (read back on the first lookup), keyed
@@ -169,6 +170,20 @@ TC_API tc_status tc_autotune_lookup(int n, int precision, int* choice) {
     return TC_OK;
 }
 
+TC_API tc_status tc_autotune_set(int n, int precision, const int* choice) {
+    if (n < 1 || n > kMaxAtoms || !choice) return fail(TC_ERR_INVALID_ARG, "tc_autotune_set: bad argument");
+    if (precision < TC_FP64 || precision > TC_TF32X3) return fail(TC_ERR_INVALID_ARG, "unknown precision");
+    if (choice[0] != 32 && choice[0] != 64) return fail(TC_ERR_INVALID_ARG, "f64 tile must be 32 or 64");
+    if (choice[1] < 1 || choice[1] > 128) return fail(TC_ERR_INVALID_ARG, "raster group must be 1..128");
+    if (precision != TC_FP64 && choice[2] != cgemm_default_stages(precision) && choice[2] != cgemm_alt_stages(precision))
+        return fail(TC_ERR_INVALID_ARG, "ring depth %d not built for precision %d", choice[2], precision);
+    const int arch = current_arch();
+    std::lock_guard<std::mutex> lk(g_mu);
+    load_cache_locked();
+    g_table[Key{arch, n, precision}] = TuneChoice{choice[0], choice[1], precision == TC_FP64 ? 0 : choice[2]};
+    return TC_OK;
+}
+
 TC_API tc_status tc_autotune(int n, int precision, void* work, size_t work_bytes, void* stream, int* choice) {
     if (n < 1 || n > kMaxAtoms) return fail(TC_ERR_INVALID_ARG, "n = %d outside 1..16", n);
     if (precision < TC_FP64 || precision > TC_TF32X3) return fail(TC_ERR_INVALID_ARG, "unknown precision");
@@ -226,10 +241,11 @@ TC_API tc_status tc_autotune(int n, int precision, void* work, size_t work_bytes
         fill_f32<<<blocks, 256, 0, s>>>(b.Rr, (size_t)b.Np * b.Np, 7u);
         fill_f32<<<blocks, 256, 0, s>>>(b.Ri, (size_t)b.Np * b.Np, 9u);
         TC_LAUNCH_CHECK();
-        CUtensorMap tmU, tmR;
+        CUtensorMap tmU, tmR, tmX;
         TC_TRY(make_part_map(&tmU, b.Uparts, b.Np, 2 * b.S, precision));
         TC_TRY(make_part_map(&tmR, b.Rparts, b.Np, 2 * b.S, precision));
-        CgemmEpi e{};
+        TC_TRY(make_part_map(&tmX, b.Xparts, b.Np, 2 * b.S, precision));
+        CgemmEpi e{};   // X = rho^H + V rho^H
         e.Np = b.Np;
         e.tiles = b.Np / 128;
         e.pr = b.Rr;
@@ -238,11 +254,22 @@ TC_API tc_status tc_autotune(int n, int precision, void* work, size_t work_bytes
         e.yr = b.Xr;
         e.yi = b.Xi;
         e.status = device_status_word();
+        CgemmEpi e2 = e;  // rho' = X^H + V X^H
+        e2.pr = b.Xr;
+        e2.pi = b.Xi;
+        e2.parts = b.Rparts;
+        e2.yr = b.Rr;
+        e2.yi = b.Ri;
+        // one whole step (both launches) per configuration
         for (int stages : {cgemm_default_stages(precision), cgemm_alt_stages(precision)}) {
-            for (int group : {4, 8, 16}) {
+            for (int group : {4, 8, 12, 16}) {
                 e.group = group;
+                e2.group = group;
                 double ms = 0.0;
-                TC_TRY(time_ms(s, 3, [&]() { return cgemm_tc(precision, 0, tmU, tmR, e, s, stages); }, &ms));
+                TC_TRY(time_ms(s, 3, [&]() {
+                    tc_status st = cgemm_tc(precision, 0, tmU, tmR, e, s, stages);
+                    return st == TC_OK ? cgemm_tc(precision, 1, tmU, tmX, e2, s, stages) : st;
+                }, &ms));
                 if (ms < best_ms) {
                     best_ms = ms;
                     best_c.tc_group = group;
