@@ -217,6 +217,25 @@ def run_reference(a, cfg):
     return 0
 
 
+# ------------------------------------------------------------------ replicas
+def max_over_ranks(x: float, world: int) -> float:
+    """Max of a per-rank float over all ranks (the one collective of the
+    benchmark: the step itself is not sharded, every rank runs a replica)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(steps: int, world: int, max_ms: float) -> float:
+    """Whole-job steps/s: every rank ran `steps` steps of its own replica."""
+    return world * steps / (max_ms * 1e-3)
+
+
 # ------------------------------------------------------------------ our arm
 def _time_form(tc, torch, U, n, params, prec, steps, warmup, renorm, stream, with_clocks=None):
     """W untimed steps, then K steps of one tc_evolve call timed with CUDA events."""
@@ -295,12 +314,8 @@ def run_ours(a, cfg):
         torch.distributed.barrier()
     r = _time_form(tc, torch, U, n, params, prec, a.steps, a.warmup, renorm if prec != "fp64" else 0, stream,
                    with_clocks=clocks)
-    ms = r["ms"]
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * a.steps / (ms * 1e-3)
+    ms = max_over_ranks(r["ms"], world)
+    value = replica_value(a.steps, world, ms)
     peak, peak_note = peak_of(prec, fp64_peak)
     achieved = r["kflops"] / (r["kms"] * 1e-3) / 1e12 if r["kms"] > 0 else 0.0
     roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -361,11 +376,7 @@ def run_ours(a, cfg):
         for _ in range(a.steps):
             tc.evolve_host(U, rho_h, n, 1, prec, params=params, obs_host=obs_h, work=hw)
         torch.cuda.synchronize()
-        te = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([te], device="cuda", dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            te = float(t.item())
+        te = max_over_ranks(time.perf_counter() - t0, world)
         line["e2e"] = {"value": world * a.steps / te, "unit": "steps/s", "h2d_bytes_per_step": 16 * N * N,
                        "d2h_bytes_per_step": 16 * N * N + 2 * (2 * n + 5) * 8,
                        "api": "tc_evolve_host (C ABI, pinned host rho, one step per call)"}

@@ -340,6 +340,23 @@ TC_API long long tc_launch_count(void);
 TC_API tc_status tc_timing_enable(int on);
 TC_API tc_status tc_timing_read(long long* launches, double* ms, double* flops);
 
+/* ------------------------------------------------------ failure testing */
+
+/* Fault kinds of tc_fault_inject. */
+#define TC_FAULT_TC_STAGE_WITHHELD 1
+
+/* tc_fault_inject -- test facility for the timeout path of the tensor-core
+ * kernels, injected from the host: the next `count` tensor-core GEMM
+ * launches of this process skip filling their first operand stage, so the
+ * MMA issuer's wait for it can never complete, and every barrier wait of
+ * those launches is limited to `wait_limit_s` seconds (0 < limit <= 10).
+ * The kernel then gives up: it records TC_ERR_TIMEOUT in the device status
+ * word, stops issuing, waits (bounded) for the copies it did issue, frees its
+ * tensor memory and returns, so the context stays usable.  The affected
+ * launch's output is garbage; tc_sync_status reports TC_ERR_TIMEOUT.  Use it
+ * with launches outside a CUDA graph (steps <= 2 per tc_evolve call). */
+TC_API tc_status tc_fault_inject(int kind, int count, double wait_limit_s);
+
 /* tc_sync_status -- synchronise `stream`, then report (and clear) the device
  * status word: TC_ERR_TIMEOUT or TC_ERR_NUMERIC if a kernel recorded one,
  * TC_ERR_CUDA on an asynchronous CUDA error, else TC_OK. */

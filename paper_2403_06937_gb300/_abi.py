@@ -66,6 +66,7 @@ SIGNATURES = {
     "tc_launch_count": (ctypes.c_longlong, []),
     "tc_timing_enable": (I, [I]),
     "tc_timing_read": (I, [ctypes.POINTER(ctypes.c_longlong), DP, DP]),
+    "tc_fault_inject": (I, [I, I, D]),
     "tc_sync_status": (I, [VP]),
 }
 

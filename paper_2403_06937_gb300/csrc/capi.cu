@@ -7,6 +7,7 @@
 #include <string>
 
 #include "kernels.cuh"
+#include "cgemm_tc.cuh"
 #include "paths.cuh"
 
 namespace tc {
@@ -463,6 +464,14 @@ TC_API tc_status tc_evolve_host(const void* U, void* rho_host, int n, int steps,
         TC_CUDA(cudaMemcpyAsync(obs_host, obs_dev, (size_t)(steps + 1) * (2 * n + 5) * sizeof(double),
                                 cudaMemcpyDeviceToHost, s));
     TC_CUDA(cudaStreamSynchronize(s));
+    return TC_OK;
+}
+
+TC_API tc_status tc_fault_inject(int kind, int count, double wait_limit_s) {
+    if (kind != TC_FAULT_TC_STAGE_WITHHELD) return fail(TC_ERR_INVALID_ARG, "unknown fault kind %d", kind);
+    if (count < 0 || !(wait_limit_s > 0.0) || wait_limit_s > 10.0)
+        return fail(TC_ERR_INVALID_ARG, "count >= 0 and 0 < wait_limit_s <= 10 required");
+    cgemm_inject_timeout(count, (unsigned long long)(wait_limit_s * 1e9));
     return TC_OK;
 }
 

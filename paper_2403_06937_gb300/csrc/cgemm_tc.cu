@@ -39,6 +39,8 @@
 // waits (bounded) for its own copies and MMAs, frees TMEM and returns.
 #include <cuda_bf16.h>
 
+#include <atomic>
+
 #include "cgemm_dev.cuh"
 #include "cgemm_tc.cuh"
 
@@ -117,6 +119,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint64_t lim = ep.wait_ns ? ep.wait_ns : kWaitLimitNs;
     int I, J;
     tile_of(MODE, ep.tiles, ep.group, blockIdx.x, I, J);
 
@@ -149,7 +152,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int kb = 0; kb < KB; kb++) {
                 const int s = kb % STAGES;
                 const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-                if (!mbar_wait_bounded(&empty[s], ph ^ 1u, abort, kWaitLimitNs, 0)) break;
+                if (!mbar_wait_bounded(&empty[s], ph ^ 1u, abort, lim, 0)) break;
+                if (ep.withhold && kb == 0) continue;   // injected fault: stage 0 is never filled
                 mbar_arrive_expect_tx(&full[s], kStage);
                 uint8_t* st = smem + s * kStage;
                 const uint32_t fb = saddr(&full[s]);
@@ -170,8 +174,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (*abort) {
                 // let the copies already issued land before the CTA goes away
                 for (int kb = issued - STAGES > 0 ? issued - STAGES : 0; kb < issued; kb++)
-                    (void)mbar_wait_bounded(&full[kb % STAGES], (uint32_t)(kb / STAGES) & 1u, nullptr,
-                                            kWaitLimitNs, 0);
+                    if (!(ep.withhold && kb == 0))
+                        (void)mbar_wait_bounded(&full[kb % STAGES], (uint32_t)(kb / STAGES) & 1u, nullptr,
+                                                lim, 0);
             }
         }
     } else if (warp == 5) {
@@ -180,7 +185,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int kb = 0; kb < KB; kb++) {
                 const int s = kb % STAGES;
                 const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-                if (!mbar_wait_bounded(&full[s], ph, abort, kWaitLimitNs, 0)) break;
+                if (!mbar_wait_bounded(&full[s], ph, abort, lim, 0)) break;
                 tc_fence_after();
                 uint8_t* st = smem + s * kStage;
 #pragma unroll
@@ -199,7 +204,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else {
         // ---------------------------------------------------------- epilogue
-        const bool ok = mbar_wait_bounded(accum, 0u, abort, kWaitLimitNs, 128);
+        const bool ok = mbar_wait_bounded(accum, 0u, abort, lim, 128);
         tc_fence_after();
         if (ok && !*abort)
             cg::epilogue_tile<KIND, S, MODE>(tmem, warp, lane, I, J, ep.Np, ep.pr, ep.pi, ep.parts, ep.yr, ep.yi);
@@ -243,11 +248,26 @@ tc_status launch(const CUtensorMap& tmU, const CUtensorMap& tmP, const CgemmEpi&
 
 }  // namespace
 
+namespace {
+std::atomic<int> g_inject_count{0};
+std::atomic<unsigned long long> g_inject_wait{0};
+}  // namespace
+
+void cgemm_inject_timeout(int count, unsigned long long wait_ns) {
+    g_inject_wait.store(wait_ns);
+    g_inject_count.store(count);
+}
+
 int cgemm_default_stages(int precision) { return precision == TC_BF16X3 ? 4 : precision == TC_TF32X3 ? 6 : 8; }
 int cgemm_alt_stages(int precision) { return precision == TC_BF16X3 ? 3 : precision == TC_TF32X3 ? 3 : 4; }
 
-tc_status cgemm_tc(int precision, int mode, const CUtensorMap& tmU, const CUtensorMap& tmP, const CgemmEpi& ep,
+tc_status cgemm_tc(int precision, int mode, const CUtensorMap& tmU, const CUtensorMap& tmP, const CgemmEpi& ep_in,
                    cudaStream_t s, int stages) {
+    CgemmEpi ep = ep_in;
+    if (g_inject_count.load() > 0 && g_inject_count.fetch_sub(1) > 0) {
+        ep.withhold = 1;
+        ep.wait_ns = g_inject_wait.load();
+    }
     if (ep.Np < 128 || ep.Np % 128 != 0 || ep.tiles * 128 != ep.Np)
         return fail(TC_ERR_INVALID_ARG, "cgemm_tc: padded dimension must be a multiple of 128");
     if (mode != 0 && mode != 1) return fail(TC_ERR_INVALID_ARG, "cgemm_tc: mode");

@@ -25,6 +25,8 @@ struct CgemmEpi {
     float* yr;       // FP32 planes of Y [Np][Np]
     float* yi;
     unsigned* status;
+    unsigned long long wait_ns;   // limit of every barrier wait (0 = 2 s)
+    int withhold;                 // fault injection: the producer never fills the first stage
 };
 
 // stages: TMA ring depth (0 = the largest that fits); the built depths are
@@ -33,6 +35,10 @@ tc_status cgemm_tc(int precision, int mode, const CUtensorMap& tmU, const CUtens
                    cudaStream_t s, int stages = 0);
 int cgemm_default_stages(int precision);
 int cgemm_alt_stages(int precision);
+
+// Test facility: the next `count` launches withhold their first stage (so the
+// consumer's wait runs out) and limit every wait to `wait_ns`.
+void cgemm_inject_timeout(int count, unsigned long long wait_ns);
 
 int cgemm_parts(int precision);       // S: BF16x3 3, TF32x3 2, TF32 1
 int cgemm_products(int precision);    // part products per real product: 6, 3, 1
