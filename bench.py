@@ -290,9 +290,7 @@ def run_ours(a, cfg):
     prec = a.precision
     params = tc.Params(n, list(map(float, cfg.g)), cfg.omega_a, cfg.omega_c)
     t_setup = time.perf_counter()
-    H = tc.build_hamiltonian(params)
-    U = tc.expm(H, n, cfg.dt)
-    del H
+    U = tc.expm_model(params, cfg.dt)
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t_setup
     renorm = cfg.renorm_every

@@ -121,6 +121,7 @@ typedef struct tc_expm_opts {
 #define TC_OP_OBSERVABLES 4
 #define TC_OP_BACKWARD 8
 #define TC_OP_EVOLVE_HOST 16
+#define TC_OP_EXPM_MODEL 32
 
 /* ------------------------------------------------------------------ misc */
 
@@ -169,6 +170,26 @@ TC_API tc_status tc_build_hamiltonian(const tc_params* params, double* H, void* 
  *          TC_ERR_WORKSPACE (short/misaligned work). */
 TC_API tc_status tc_expm(const double* H, int n, double dt, const tc_expm_opts* opts,
                          void* U, void* work, size_t work_bytes, void* stream);
+
+/* tc_expm_model -- U = e^{-i H dt} for the Hamiltonian of `params` (Eq. 4)
+ * without forming H: with B = (H - mu I) dt (mu = Tr H / N when
+ * opts->shift), the Taylor polynomial of e^{-iB} (Eq. 7) is evaluated by
+ * Horner's rule, T <- I + (-iB) T / k, each step applying B as the structured
+ * operator it is (row r of B X combines row r and the n rows r xor 2^b of X):
+ * O(n N^2) memory-bound work per Taylor term instead of dense FP64 products.
+ * The degree is the smallest whose remainder bound is below 2^-53; an
+ * argument with ||B||_inf > 1 is first scaled by 2^-s and squared back
+ * (dense FP64 complex products).  U is then multiplied by e^{-i mu dt} and
+ * symmetrised.
+ * Same result as tc_expm on the dense H to rounding (about 1e-15).
+ *  params : model (host).
+ *  opts   : NULL = automatic; taylor_degree 1..64 and squarings honoured.
+ *  U      : device, N*N c128, written, 16-byte aligned.
+ *  work   : device, >= 6 N^2 doubles (tc_workspace_size(n, TC_FP64,
+ *           TC_OP_EXPM_MODEL, 0, 0)).
+ *  Errors: TC_ERR_INVALID_ARG, TC_ERR_WORKSPACE. */
+TC_API tc_status tc_expm_model(const tc_params* params, double dt, const tc_expm_opts* opts, void* U, void* work,
+                               size_t work_bytes, void* stream);
 
 /* tc_evolve -- `steps` steps of rho <- U rho U^dag (Eq. 6, evaluated as the
  * two products of Eq. 12: X = U rho, then rho' = X U^dag).  U must be

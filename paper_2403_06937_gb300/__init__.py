@@ -89,6 +89,22 @@ def expm(H: torch.Tensor, n: int, dt: float, taylor_degree: int = 0, squarings: 
     return U
 
 
+def expm_model(params: Params, dt: float, taylor_degree: int = 0, squarings: int = -1, shift: bool = True,
+               device="cuda", stream=None, work: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """tc_expm_model: U = e^{-iH dt} from the model, H applied as a stencil (no dense H)."""
+    n = params.n
+    N = 1 << n
+    U = torch.empty((N, N), dtype=torch.complex128, device=device)
+    need = workspace_size(n, TC_FP64, _abi.TC_OP_EXPM_MODEL)
+    if work is None or work.numel() < need:
+        work = _work(need, device)
+    opts = _abi.tc_expm_opts(int(taylor_degree), int(squarings), int(bool(shift)))
+    p = params.c()
+    _abi.call("tc_expm_model", ctypes.byref(p), float(dt), ctypes.byref(opts), _ptr(U), _ptr(work), work.numel(),
+              ctypes.c_void_p(_stream(stream)))
+    return U
+
+
 def evolve(U: torch.Tensor, rho: torch.Tensor, n: int, steps: int, precision="fp64", renorm_every: int = 0,
            params: Optional[Params] = None, observe: bool = True, inplace: bool = False, stream=None,
            work: Optional[torch.Tensor] = None):
@@ -274,7 +290,7 @@ def sync_status(stream=None) -> None:
     _abi.call("tc_sync_status", ctypes.c_void_p(_stream(stream)))
 
 
-__all__ = ["Params", "TCError", "build_hamiltonian", "expm", "evolve", "evolve_host", "observables",
+__all__ = ["Params", "TCError", "build_hamiltonian", "expm", "expm_model", "evolve", "evolve_host", "observables",
            "evolve_backward", "EvolveFn", "batch_evolve", "autotune", "autotune_lookup", "autotune_set",
            "workspace_size", "launch_count", "timing_enable", "timing_read",
            "device_check", "sync_status", "obs_stride", "PRECISIONS", "TC_FP64", "TC_BF16X3", "TC_TF32",

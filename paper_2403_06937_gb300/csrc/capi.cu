@@ -354,6 +354,7 @@ TC_API size_t tc_workspace_size(int n, int precision, int ops, int steps, int ck
         else upd(evolve_lowp_bytes(n, precision));
     }
     if (ops & TC_OP_OBSERVABLES) upd(observables_scratch_bytes(n));
+    if (ops & TC_OP_EXPM_MODEL) upd(expm_model_bytes(n));
     if (ops & TC_OP_EVOLVE_HOST) upd(evolve_bytes(n, precision) + evolve_host_extra(n, steps));
     if (ops & TC_OP_BACKWARD) upd(backward_bytes(n, steps, ckpt_every));
     return need;

@@ -9,6 +9,11 @@ namespace tc {
 tc_status expm_impl(const double* H, int n, double dt, const tc_expm_opts* opts, double* U, Arena& ar,
                     cudaStream_t s, int* used_degree, int* used_squarings);
 
+// e^{-iHdt} from the model by Horner's rule with H applied as a stencil.
+size_t expm_model_bytes(int n);
+tc_status expm_model_impl(const Model& m, double dt, const tc_expm_opts* opts, double* U, Arena& ar,
+                          cudaStream_t s, int* used_degree, int* used_squarings);
+
 // FP64 step loop (DMMA products).
 tc_status evolve_f64(const double* U, double* rho, int n, int steps, int renorm_every, const Model* m,
                      double* obs, Arena& ar, cudaStream_t s);
