@@ -64,6 +64,13 @@ def config_n14() -> TCConfig:
                     description="n=14, dim 16384, g~U[0.005,0.015] seed 0, detuning 0.002, dt=0.05, 500 steps, renorm every 50")
 
 
+def config_n15() -> TCConfig:
+    """n = 15, dim 32768 (the paper's largest dimension): g seed 0, precision form only."""
+    return TCConfig("n15_precision", 15, draw_couplings(15, 0), 1.002, 1.0, 0.05, 500,
+                    renorm_every=50,
+                    description="n=15, dim 32768, g~U[0.005,0.015] seed 0, detuning 0.002, dt=0.05, renorm every 50")
+
+
 def config_n11_grad() -> TCConfig:
     """n = 11, dim 2048: g seed 1, 400 steps, loss = excited population of atom 1."""
     return TCConfig("n11_grad", 11, draw_couplings(11, 1), 1.002, 1.0, 0.05, 400,
