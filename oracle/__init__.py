@@ -33,6 +33,13 @@ Functions and what pins them (tests under ``tests/test_oracle_*.py``):
 * ``jacobi_eig``        Textbook cyclic Jacobi.  Pinned against LAPACK.
 * ``dicke_matrix``      Equal-coupling tridiagonal.  Pinned by n = 1, 2 by hand
                          and against the full 2^n propagation.
+* ``lindblad`` (module)  The open-system form: Eq. 5 with photon leakage,
+                         dense on the truncated space, the exact damping
+                         channel and the symmetric split step.  Pinned by the
+                         damped Jaynes-Cummings closed form, the damping
+                         superoperator's exponential, second-order convergence
+                         and the closed-system oracle at kappa = 0
+                         (tests/test_oracle_lindblad.py).
 * ``tangent_step`` / ``grad_forward``
                          Forward-mode derivative (Van Loan block).  Pinned by
                          central differences of ``propagate`` and exact
