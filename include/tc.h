@@ -122,6 +122,7 @@ typedef struct tc_expm_opts {
 #define TC_OP_BACKWARD 8
 #define TC_OP_EVOLVE_HOST 16
 #define TC_OP_EXPM_MODEL 32
+#define TC_OP_LINDBLAD 64
 
 /* ------------------------------------------------------------------ misc */
 
@@ -256,6 +257,52 @@ TC_API tc_status tc_observables(const void* rho, int n, const tc_params* params,
  *          holds), TC_ERR_UNSUPPORTED_DEVICE, TC_ERR_CUDA. */
 TC_API tc_status tc_observables_noalloc(const void* rho, int n, const tc_params* params, double* out,
                                         void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Open-system form: the master equation of Sec. III.A (Eq. 5) with its
+ * Lindblad term on.  The paper names the term and sets it to zero; the term
+ * here is photon leakage at rate kappa, L(rho) = kappa (a rho a^dag -
+ * {a^dag a, rho} / 2).  H conserves the excitation number k = popcount(s) + p
+ * and a leaked photon lowers it by one, so the state is block diagonal:
+ * block k holds the d_k atom strings with popcount(s) <= k, photon count
+ * k - popcount(s).  Packed layout: blocks k = 0..n one after another, block
+ * k d_k x d_k row-major interleaved complex128, its basis the first d_k
+ * entries of `basis` (all 2^n strings ordered by popcount, then by value).
+ * Block n is the closed model's space (Eq. 2) in that order.
+ * ------------------------------------------------------------------------- */
+
+/* tc_lindblad_layout -- the packed layout for n atoms (host only, no GPU).
+ *  dims    : host int[n+1] or NULL: d_k.
+ *  offsets : host size_t[n+2] or NULL: element offset of block k; offsets[n+1]
+ *            = total elements (complex) of a packed state.
+ *  basis   : host int[2^n] or NULL: atom string at each block position.
+ *  Errors: TC_ERR_INVALID_ARG (n outside 1..16). */
+TC_API tc_status tc_lindblad_layout(int n, int* dims, size_t* offsets, int* basis);
+
+/* tc_lindblad_propagators -- U_k = e^{-i H_k dt} for every block (Eq. 6 per
+ * block), by the structured Horner evaluation of tc_expm_model.
+ *  U     : device, packed complex128 (offsets[n+1] elements), written,
+ *          16-byte aligned.
+ *  work  : device, >= tc_workspace_size(n, TC_FP64, TC_OP_LINDBLAD, 0, 0).
+ *  Errors: TC_ERR_INVALID_ARG, TC_ERR_WORKSPACE, TC_ERR_CUDA. */
+TC_API tc_status tc_lindblad_propagators(const tc_params* params, double dt, void* U, void* work,
+                                         size_t work_bytes, void* stream);
+
+/* tc_lindblad_evolve -- `steps` symmetric split steps of Eq. 5:
+ *     rho <- D_{dt/2}(U D_{dt/2}(rho) U^dag)
+ * with D_tau the exact damping over tau (the bosonic pure-loss channel,
+ * mixing block k+m into block k) and U from tc_lindblad_propagators with the
+ * same dt.  Second order in dt; kappa = 0 is the closed evolution of Eq. 6.
+ *  U, rho   : device packed complex128; rho in/out (Hermitian blocks).
+ *  precision: TC_FP64.
+ *  obs      : device f64[(steps+1) * TC_OBS_STRIDE(n)] or NULL; the row of
+ *             tc_observables summed over blocks, P(m) = probability of m
+ *             photons, E = Tr(H rho).
+ *  work     : device, >= tc_workspace_size(n, precision, TC_OP_LINDBLAD, 0, 0).
+ *  Errors: TC_ERR_INVALID_ARG, TC_ERR_WORKSPACE, TC_ERR_CUDA. */
+TC_API tc_status tc_lindblad_evolve(const tc_params* params, double kappa, double dt, const void* U, void* rho,
+                                    int steps, int precision, double* obs, void* work, size_t work_bytes,
+                                    void* stream);
 
 /* tc_evolve_backward -- gradient of L = Tr(O rho_K), O = diag(O_diag), with
  * rho_K = U^K rho_0 U^-K and U = e^{-iH dt}, with respect to

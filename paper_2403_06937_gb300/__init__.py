@@ -125,6 +125,67 @@ def evolve(U: torch.Tensor, rho: torch.Tensor, n: int, steps: int, precision="fp
     return out, obs
 
 
+@dataclass
+class LindbladLayout:
+    """Packed excitation-block layout of the open-system form (tc_lindblad_layout)."""
+    n: int
+    dims: list        # d_k, k = 0..n
+    offsets: list     # element offset of block k; offsets[n + 1] = total
+    basis: list       # atom string at each block position
+
+    @property
+    def total(self) -> int:
+        return self.offsets[-1]
+
+    def blocks(self, packed: torch.Tensor):
+        """Views [d_k x d_k] of a packed state, k = 0..n."""
+        return [packed[self.offsets[k]:self.offsets[k + 1]].view(self.dims[k], self.dims[k])
+                for k in range(self.n + 1)]
+
+
+def lindblad_layout(n: int) -> LindbladLayout:
+    dims = (ctypes.c_int * (n + 1))()
+    offs = (ctypes.c_size_t * (n + 2))()
+    basis = (ctypes.c_int * (1 << n))()
+    _abi.call("tc_lindblad_layout", int(n), ctypes.cast(dims, ctypes.c_void_p), ctypes.cast(offs, ctypes.c_void_p),
+              ctypes.cast(basis, ctypes.c_void_p))
+    return LindbladLayout(n, list(dims), [int(o) for o in offs], list(basis))
+
+
+def lindblad_propagators(params: Params, dt: float, device="cuda", stream=None,
+                         work: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """tc_lindblad_propagators: packed U_k = e^{-i H_k dt} for every excitation block."""
+    lay = lindblad_layout(params.n)
+    U = torch.empty(lay.total, dtype=torch.complex128, device=device)
+    need = workspace_size(params.n, TC_FP64, _abi.TC_OP_LINDBLAD)
+    if work is None or work.numel() < need:
+        work = _work(need, device)
+    p = params.c()
+    _abi.call("tc_lindblad_propagators", ctypes.byref(p), float(dt), _ptr(U), _ptr(work), work.numel(),
+              ctypes.c_void_p(_stream(stream)))
+    return U
+
+
+def lindblad_evolve(params: Params, kappa: float, dt: float, U: torch.Tensor, rho: torch.Tensor, steps: int,
+                    precision="fp64", observe: bool = True, inplace: bool = False, stream=None,
+                    work: Optional[torch.Tensor] = None):
+    """tc_lindblad_evolve: `steps` split steps of Eq. 5 with photon leakage.  Returns (rho_T, obs or None)."""
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    n = params.n
+    lay = lindblad_layout(n)
+    for t in (U, rho):
+        assert t.dtype == torch.complex128 and t.is_contiguous() and t.numel() == lay.total
+    out = rho if inplace else rho.clone()
+    obs = torch.empty((steps + 1, obs_stride(n)), dtype=torch.float64, device=rho.device) if observe else None
+    need = workspace_size(n, prec, _abi.TC_OP_LINDBLAD)
+    if work is None or work.numel() < need:
+        work = _work(need, rho.device)
+    p = params.c()
+    _abi.call("tc_lindblad_evolve", ctypes.byref(p), float(kappa), float(dt), _ptr(U), _ptr(out), int(steps), prec,
+              _ptr(obs), _ptr(work), work.numel(), ctypes.c_void_p(_stream(stream)))
+    return out, obs
+
+
 def observables(rho: torch.Tensor, n: int, params: Optional[Params] = None, stream=None) -> torch.Tensor:
     """tc_observables: [P_1..P_n, <p>, P(0..n), Tr rho, Tr rho^2, E] of a density matrix."""
     N = 1 << n
@@ -290,7 +351,8 @@ def sync_status(stream=None) -> None:
     _abi.call("tc_sync_status", ctypes.c_void_p(_stream(stream)))
 
 
-__all__ = ["Params", "TCError", "build_hamiltonian", "expm", "expm_model", "evolve", "evolve_host", "observables",
+__all__ = ["Params", "TCError", "build_hamiltonian", "expm", "expm_model", "evolve", "LindbladLayout",
+           "lindblad_layout", "lindblad_propagators", "lindblad_evolve", "evolve_host", "observables",
            "evolve_backward", "EvolveFn", "batch_evolve", "autotune", "autotune_lookup", "autotune_set",
            "workspace_size", "launch_count", "timing_enable", "timing_read",
            "device_check", "sync_status", "obs_stride", "PRECISIONS", "TC_FP64", "TC_BF16X3", "TC_TF32",

@@ -21,6 +21,7 @@ STATUS_NAMES = {0: "TC_OK", 1: "TC_ERR_INVALID_ARG", 2: "TC_ERR_UNSUPPORTED_DEVI
 TC_FP64, TC_BF16X3, TC_TF32, TC_TF32X3 = 0, 1, 2, 3
 TC_COUPLING_BOSONIC, TC_COUPLING_QUBIT_PHOTON = 0, 1
 TC_OP_EXPM, TC_OP_EVOLVE, TC_OP_OBSERVABLES, TC_OP_BACKWARD, TC_OP_EVOLVE_HOST, TC_OP_EXPM_MODEL = 1, 2, 4, 8, 16, 32
+TC_OP_LINDBLAD = 64
 
 
 class TCError(RuntimeError):
@@ -53,6 +54,9 @@ SIGNATURES = {
     "tc_build_hamiltonian": (I, [ctypes.POINTER(tc_params), VP, VP]),
     "tc_expm": (I, [VP, I, D, ctypes.POINTER(tc_expm_opts), VP, VP, SZ, VP]),
     "tc_expm_model": (I, [ctypes.POINTER(tc_params), D, ctypes.POINTER(tc_expm_opts), VP, VP, SZ, VP]),
+    "tc_lindblad_layout": (I, [I, VP, VP, VP]),
+    "tc_lindblad_propagators": (I, [ctypes.POINTER(tc_params), D, VP, VP, SZ, VP]),
+    "tc_lindblad_evolve": (I, [ctypes.POINTER(tc_params), D, D, VP, VP, I, I, VP, VP, SZ, VP]),
     "tc_evolve": (I, [VP, VP, I, I, I, I, ctypes.POINTER(tc_params), VP, VP, SZ, VP]),
     "tc_observables": (I, [VP, I, ctypes.POINTER(tc_params), VP, VP, SZ, VP]),
     "tc_observables_noalloc": (I, [VP, I, ctypes.POINTER(tc_params), VP, VP]),

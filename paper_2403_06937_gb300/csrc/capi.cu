@@ -104,14 +104,6 @@ size_t evolve_host_extra(int n, int steps) {
     return mat_bytes(n, 16) + round256((size_t)(steps + 1) * (2 * n + 5) * sizeof(double));
 }
 
-tc_status check_work(void* work, size_t have, size_t need) {
-    if (need == 0) return TC_OK;
-    if (!work) return fail(TC_ERR_WORKSPACE, "work is NULL (need %zu bytes)", need);
-    if (reinterpret_cast<uintptr_t>(work) & 255u) return fail(TC_ERR_WORKSPACE, "work is not 256-byte aligned");
-    if (have < need) return fail(TC_ERR_WORKSPACE, "work has %zu bytes, need %zu", have, need);
-    return TC_OK;
-}
-
 // ------------------------------------------------------------------ expm plan
 // Real GEMMs to evaluate a degree-d polynomial in Y by Horner in Y^q blocks
 // (Paterson-Stockmeyer), given Y^1..Y^q.
@@ -234,6 +226,14 @@ tc_status eval_poly(int N, const double* a, int d, int q, double* const* Y, doub
 
 }  // namespace
 
+tc_status check_work(void* work, size_t have, size_t need) {
+    if (need == 0) return TC_OK;
+    if (!work) return fail(TC_ERR_WORKSPACE, "work is NULL (need %zu bytes)", need);
+    if (reinterpret_cast<uintptr_t>(work) & 255u) return fail(TC_ERR_WORKSPACE, "work is not 256-byte aligned");
+    if (have < need) return fail(TC_ERR_WORKSPACE, "work has %zu bytes, need %zu", have, need);
+    return TC_OK;
+}
+
 tc_status expm_impl(const double* H, int n, double dt, const tc_expm_opts* opts, double* U, Arena& ar,
                     cudaStream_t s, int* used_degree, int* used_squarings) {
     const int N = 1 << n;
@@ -355,6 +355,7 @@ TC_API size_t tc_workspace_size(int n, int precision, int ops, int steps, int ck
     }
     if (ops & TC_OP_OBSERVABLES) upd(observables_scratch_bytes(n));
     if (ops & TC_OP_EXPM_MODEL) upd(expm_model_bytes(n));
+    if (ops & TC_OP_LINDBLAD) upd(lindblad_bytes(n, precision));
     if (ops & TC_OP_EVOLVE_HOST) upd(evolve_bytes(n, precision) + evolve_host_extra(n, steps));
     if (ops & TC_OP_BACKWARD) upd(backward_bytes(n, steps, ckpt_every));
     return need;

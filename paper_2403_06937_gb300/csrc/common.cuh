@@ -43,6 +43,9 @@ void count_launch(int k);
 // TC_OK if the current device is sm_103 (the only target compiled).
 tc_status check_device();
 
+// TC_OK if `work` is non-null, 256-byte aligned and holds `need` bytes.
+tc_status check_work(void* work, size_t have, size_t need);
+
 // Device status word: kernels OR in these bits; tc_sync_status reads them.
 enum : unsigned { kStatusTimeout = 1u, kStatusNumeric = 2u };
 unsigned* device_status_word();   // device address of the word (per device)

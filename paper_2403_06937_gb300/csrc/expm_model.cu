@@ -16,59 +16,59 @@
 #include <algorithm>
 #include <cmath>
 
+#include "model_dev.cuh"
 #include "paths.cuh"
 
 namespace tc {
 namespace {
 
-// H elements with the same correctly rounded operations as the dense build
-__device__ __forceinline__ double h_diag(const Model& m, unsigned s) {
-    const int pc = __popc(s);
-    return __dadd_rn(__dmul_rn(m.omega_c, (double)(m.n - pc)), __dmul_rn(m.omega_a, (double)pc));
-}
-__device__ __forceinline__ double h_pair(const Model& m, unsigned r, int bit) {
-    const unsigned x = 1u << bit;
-    const unsigned se = (r & x) ? r : (r ^ x);   // excited side
-    const int atom0 = m.n - 1 - bit;
-    if (m.coupling == TC_COUPLING_QUBIT_PHOTON) return m.g[atom0];
-    return __dmul_rn(m.g[atom0], __dsqrt_rn((double)(m.n - __popc(se) + 1)));
-}
-
 constexpr int kCols = 4;        // columns per thread
 constexpr int kThreads = 256;   // a block covers kCols * kThreads columns of one row
 
-// One Horner step: T' = I + (-i B) T / k with B = (H - mu I) dt, planar T.
-// (-i B)(T_r + i T_i) = B T_i - i B T_r.  Block (x, y) handles row r = x and
-// a chunk of columns; the row's n + 1 entries of B are computed once into
-// shared memory, and every thread reads rows r and r xor 2^b of T at its
-// columns (coalesced along the row).  first: T = I, so B T = B.  Rows run
-// along grid x (N reaches 2^16, above the grid-y limit).
-__global__ void __launch_bounds__(kThreads) horner_step_kernel(Model m, double mu, double dt, double inv_k,
-                                                                const double* __restrict__ Tr,
+// One Horner step: T' = I + (-i B) T / k with B = (H_blk - mu I) dt, planar
+// d x d T.  (-i B)(T_r + i T_i) = B T_i - i B T_r.  Block (x, y) handles
+// row r = x and a chunk of columns; the row's n + 1 entries of B are
+// computed once into shared memory (col[b] < 0: the neighbour is outside the
+// block), and every thread reads rows r and col[b] of T at its columns
+// (coalesced along the row).  first: T = I, so B T = B.  Rows run along grid
+// x (d reaches 2^16, above the grid-y limit).
+__global__ void __launch_bounds__(kThreads) horner_step_kernel(Model m, ExcitationBlock blk, double mu, double dt,
+                                                                double inv_k, const double* __restrict__ Tr,
                                                                 const double* __restrict__ Ti, double* __restrict__ Or,
                                                                 double* __restrict__ Oi, int first) {
     __shared__ double hb[kMaxAtoms + 1];
-    const unsigned N = 1u << m.n;
+    __shared__ int nb[kMaxAtoms];
+    const unsigned d = (unsigned)blk.d;
     const unsigned r = blockIdx.x;
-    if (threadIdx.x < (unsigned)m.n) hb[threadIdx.x] = h_pair(m, r, threadIdx.x) * dt;
-    if (threadIdx.x == (unsigned)m.n) hb[m.n] = (h_diag(m, r) - mu) * dt;
+    const unsigned s = blk.order ? (unsigned)blk.order[r] : r;
+    if (threadIdx.x < (unsigned)m.n) {
+        const unsigned t = s ^ (1u << threadIdx.x);
+        const unsigned c = blk.pos ? (unsigned)blk.pos[t] : t;
+        nb[threadIdx.x] = c < d ? (int)c : -1;
+        hb[threadIdx.x] = c < d ? h_pair(m, blk.k, s, threadIdx.x) * dt : 0.0;
+    }
+    if (threadIdx.x == (unsigned)m.n) hb[m.n] = (h_diag(m, blk.k, s) - mu) * dt;
     __syncthreads();
-    const double d = hb[m.n];
-    const size_t row = (size_t)r * N;
+    const double dg = hb[m.n];
+    const size_t row = (size_t)r * d;
 #pragma unroll
     for (int j = 0; j < kCols; j++) {
         const unsigned c = (blockIdx.y * kCols + j) * kThreads + threadIdx.x;
-        if (c >= N) break;
+        if (c >= d) break;
         double br = 0.0, bi = 0.0;   // (B T_r)[r][c], (B T_i)[r][c]
         if (first) {
-            const unsigned x = r ^ c;
-            if (x == 0) br = d;
-            else if ((x & (x - 1)) == 0) br = hb[__ffs(x) - 1];
+            if (c == r) {
+                br = dg;
+            } else {
+                for (int b = 0; b < m.n; b++)
+                    if (nb[b] == (int)c) br = hb[b];
+            }
         } else {
-            br = d * Tr[row + c];
-            bi = d * Ti[row + c];
+            br = dg * Tr[row + c];
+            bi = dg * Ti[row + c];
             for (int b = 0; b < m.n; b++) {
-                const size_t o = (size_t)(r ^ (1u << b)) * N + c;
+                if (nb[b] < 0) continue;
+                const size_t o = (size_t)nb[b] * d + c;
                 br += hb[b] * Tr[o];
                 bi += hb[b] * Ti[o];
             }
@@ -78,54 +78,70 @@ __global__ void __launch_bounds__(kThreads) horner_step_kernel(Model m, double m
     }
 }
 
-tc_status launch_horner(const Model& m, double mu, double dt, double inv_k, const double* Tr, const double* Ti,
-                        double* Or, double* Oi, int first, cudaStream_t s) {
-    const unsigned N = 1u << m.n;
-    dim3 grid(N, (N + kCols * kThreads - 1) / (kCols * kThreads));
-    horner_step_kernel<<<grid, kThreads, 0, s>>>(m, mu, dt, inv_k, Tr, Ti, Or, Oi, first);
+tc_status launch_horner(const Model& m, const ExcitationBlock& blk, double mu, double dt, double inv_k,
+                        const double* Tr, const double* Ti, double* Or, double* Oi, int first, cudaStream_t s) {
+    const unsigned d = (unsigned)blk.d;
+    dim3 grid(d, (d + kCols * kThreads - 1) / (kCols * kThreads));
+    horner_step_kernel<<<grid, kThreads, 0, s>>>(m, blk, mu, dt, inv_k, Tr, Ti, Or, Oi, first);
     TC_LAUNCH_CHECK();
     return TC_OK;
 }
 
-// exact ||B||_inf = max_s |H_ss - mu| + sum_b |h(s, s^b)| (times dt), on the host
-double norm_inf_host(const Model& m, double mu, double dt) {
-    const unsigned N = 1u << m.n;
+int popcount_host(unsigned s) {
+    int pc = 0;
+    for (unsigned t = s; t; t >>= 1) pc += (int)(t & 1u);
+    return pc;
+}
+
+// exact ||B||_inf = max over rows of |H_ss - mu| + sum_b |h(s, s^b)| (times dt)
+// and the trace shift mu = Tr H_blk / d, on the host from the block's basis
+void block_norm_and_shift(const Model& m, const ExcitationBlock& blk, const int* host_order, int shift, double dt,
+                          double* norm, double* mu_out) {
+    const unsigned d = (unsigned)blk.d;
+    double tr = 0.0;
+    for (unsigned r = 0; r < d; r++) {
+        const unsigned s = host_order ? (unsigned)host_order[r] : r;
+        const int pc = popcount_host(s);
+        tr += m.omega_c * (double)(blk.k - pc) + m.omega_a * (double)pc;
+    }
+    const double mu = shift ? tr / (double)d : 0.0;
     double best = 0.0;
-    for (unsigned s = 0; s < N; s++) {
-        int pc = 0;
-        for (unsigned t = s; t; t >>= 1) pc += (int)(t & 1u);
-        double row = std::fabs(m.omega_c * (double)(m.n - pc) + m.omega_a * (double)pc - mu);
+    for (unsigned r = 0; r < d; r++) {
+        const unsigned s = host_order ? (unsigned)host_order[r] : r;
+        const int pc = popcount_host(s);
+        double row = std::fabs(m.omega_c * (double)(blk.k - pc) + m.omega_a * (double)pc - mu);
         for (int b = 0; b < m.n; b++) {
-            const unsigned x = 1u << b;
-            const unsigned se = (s & x) ? s : (s ^ x);
-            int pe = 0;
-            for (unsigned t = se; t; t >>= 1) pe += (int)(t & 1u);
+            const unsigned se = s | (1u << b);
+            if (popcount_host(se) > blk.k) continue;   // neighbour outside the block
             const int atom0 = m.n - 1 - b;
-            row += m.coupling == TC_COUPLING_QUBIT_PHOTON ? std::fabs(m.g[atom0])
-                                                           : std::fabs(m.g[atom0]) * std::sqrt((double)(m.n - pe + 1));
+            row += m.coupling == TC_COUPLING_QUBIT_PHOTON
+                       ? std::fabs(m.g[atom0])
+                       : std::fabs(m.g[atom0]) * std::sqrt((double)(blk.k - popcount_host(se) + 1));
         }
         if (row > best) best = row;
     }
-    return best * dt;
+    *norm = best * dt;
+    *mu_out = mu;
 }
 
 }  // namespace
 
-size_t expm_model_bytes(int n) {
-    return 6 * round256(sizeof(double) << (2 * n)) + 256;
+size_t expm_block_bytes(size_t d) {
+    return 6 * round256(sizeof(double) * d * d) + 256;
 }
 
-tc_status expm_model_impl(const Model& m, double dt, const tc_expm_opts* opts, double* U, Arena& ar,
-                          cudaStream_t s, int* used_degree, int* used_squarings) {
-    const int N = 1 << m.n;
+tc_status expm_block_impl(const Model& m, const ExcitationBlock& blk, const int* host_order, double dt,
+                          const tc_expm_opts* opts, double* U, Arena& ar, cudaStream_t s, int* used_degree,
+                          int* used_squarings) {
+    const int N = blk.d;
     const size_t NN = (size_t)N * N;
     double* P[4];
     for (int k = 0; k < 4; k++) P[k] = ar.take<double>(NN);
     double* Q[2] = {ar.take<double>(NN), ar.take<double>(NN)};
     if (!Q[1]) return fail(TC_ERR_WORKSPACE, "expm_model: workspace too small");
     const int shift = opts ? opts->shift : 1;
-    const double mu = shift ? 0.5 * (double)m.n * (m.omega_a + m.omega_c) : 0.0;   // Tr H / N
-    const double bn = norm_inf_host(m, mu, dt);
+    double bn = 0.0, mu = 0.0;   // ||B||_inf, Tr H / d
+    block_norm_and_shift(m, blk, host_order, shift, dt, &bn, &mu);
     const double u = std::ldexp(1.0, -53);
     // smallest degree whose Taylor remainder bound b^{m+1}/(m+1)! / (1 - b/(m+2))
     // is below 2^-53 / 2^s (errors double with each squaring); 0 if above 64
@@ -155,9 +171,9 @@ tc_status expm_model_impl(const Model& m, double dt, const tc_expm_opts* opts, d
 
     // Horner: T_m = I + (-iB) I / m, then T = I + (-iB) T / k down to k = 1
     double *Tr = P[0], *Ti = P[1], *Or = P[2], *Oi = P[3];
-    TC_TRY(launch_horner(m, mu, dts, 1.0 / deg, nullptr, nullptr, Tr, Ti, 1, s));
+    TC_TRY(launch_horner(m, blk, mu, dts, 1.0 / deg, nullptr, nullptr, Tr, Ti, 1, s));
     for (int k = deg - 1; k >= 1; k--) {
-        TC_TRY(launch_horner(m, mu, dts, 1.0 / k, Tr, Ti, Or, Oi, 0, s));
+        TC_TRY(launch_horner(m, blk, mu, dts, 1.0 / k, Tr, Ti, Or, Oi, 0, s));
         std::swap(Tr, Or);
         std::swap(Ti, Oi);
     }
@@ -178,6 +194,16 @@ tc_status expm_model_impl(const Model& m, double dt, const tc_expm_opts* opts, d
     const double coef[1] = {-1.0};
     TC_TRY(launch_lincomb(N, 0.0, 1, mats, coef, Q[0], s));
     return launch_expm_finish(N, Tr, Q[0], std::cos(mu * dt), -std::sin(mu * dt), U, s);
+}
+
+size_t expm_model_bytes(int n) {
+    return expm_block_bytes((size_t)1 << n);
+}
+
+tc_status expm_model_impl(const Model& m, double dt, const tc_expm_opts* opts, double* U, Arena& ar,
+                          cudaStream_t s, int* used_degree, int* used_squarings) {
+    ExcitationBlock blk{m.n, 1 << m.n, nullptr, nullptr};
+    return expm_block_impl(m, blk, nullptr, dt, opts, U, ar, s, used_degree, used_squarings);
 }
 
 }  // namespace tc

@@ -1,0 +1,451 @@
+// lindblad.cu -- the open-system form of the evolution: the quantum master
+// equation of Sec. III.A (Eq. 5) with its Lindblad term switched on.  The
+// paper names the term and sets it to zero; the term used here is photon
+// leakage from the cavity at rate kappa,
+//     L(rho) = kappa (a rho a^dag - {a^dag a, rho} / 2).
+//
+// Structure.  H conserves the excitation number k = popcount(s) + p and a
+// leaked photon lowers it by one, so a state that starts inside one k stays
+// block diagonal: rho = sum_k rho_k, block k living on the d_k atom strings
+// with popcount(s) <= k (photon count k - popcount(s)).  With the strings
+// ordered by popcount (then value), block k's basis is the first d_k strings
+// of one common order, so element (i, j) means the same pair of strings in
+// every block that holds it.  Blocks are stored packed, k = 0..n.
+//
+// One step of length dt is the symmetric split
+//     rho <- D_{dt/2}( U rho U^dag ), after rho <- D_{dt/2}(rho),
+// with U = e^{-iH dt} block by block (each U_k complex symmetric, so the two
+// products are those of the closed form, Eq. 12) and D_tau the exact
+// solution of the damping part alone (the bosonic pure-loss channel):
+//     rho_k'(i, j) = sum_m F[p][m] F[q][m] rho_{k+m}(i, j),
+//     F[p][m] = sqrt((1 - eta)^m / m! * (p + m)! / p!) * eta^{p/2},
+// eta = e^{-kappa tau}, p and q the photon counts of strings i and j in
+// block k.  D_tau is one HBM-bound pass over all blocks; the products are
+// dense complex GEMMs per block.
+#include <algorithm>
+#include <cmath>
+#include <mutex>
+#include <vector>
+
+#include "graph.cuh"
+#include "model_dev.cuh"
+#include "paths.cuh"
+#include "timing.cuh"
+
+namespace tc {
+namespace {
+
+int popcount_host(unsigned s) {
+    int pc = 0;
+    for (unsigned t = s; t; t >>= 1) pc += (int)(t & 1u);
+    return pc;
+}
+
+struct Layout {
+    int n = 0;
+    int N = 0;
+    int dims[kMaxAtoms + 1] = {};
+    size_t off[kMaxAtoms + 2] = {};   // element offsets of the blocks; off[n + 1] = total
+    std::vector<int> order;           // strings by popcount, then value
+};
+
+const Layout& layout_of(int n) {
+    static std::mutex mu;
+    static Layout* cache[kMaxAtoms + 1] = {};
+    std::lock_guard<std::mutex> lk(mu);
+    if (!cache[n]) {
+        Layout* L = new Layout;   // kept for the life of the process
+        L->n = n;
+        L->N = 1 << n;
+        L->order.resize(L->N);
+        for (int s = 0; s < L->N; s++) L->order[s] = s;
+        std::stable_sort(L->order.begin(), L->order.end(),
+                         [](int a, int b) { return popcount_host((unsigned)a) < popcount_host((unsigned)b); });
+        for (int k = 0; k <= n; k++) {
+            int d = 0;
+            for (int s = 0; s < L->N; s++) d += popcount_host((unsigned)s) <= k;
+            L->dims[k] = d;
+            L->off[k + 1] = L->off[k] + (size_t)d * d;
+        }
+        cache[n] = L;
+    }
+    return *cache[n];
+}
+
+// Block dimensions and offsets by value, for kernels.
+struct BlockSet {
+    int n;
+    int d[kMaxAtoms + 1];
+    unsigned long long off[kMaxAtoms + 1];
+    int cum[kMaxAtoms + 2];   // number of strings with popcount < c
+};
+
+BlockSet block_set(const Layout& L) {
+    BlockSet b{};
+    b.n = L.n;
+    for (int k = 0; k <= L.n; k++) {
+        b.d[k] = L.dims[k];
+        b.off[k] = L.off[k];
+    }
+    b.cum[0] = 0;
+    for (int c = 0; c <= L.n; c++) b.cum[c + 1] = L.dims[c];
+    return b;
+}
+
+// Position of string s in the popcount order: the strings of smaller popcount,
+// plus the rank of s among strings of its popcount in increasing value, which
+// is the combinatorial number system sum_t C(b_t, t) over its set bits
+// b_1 < b_2 < ... (t from 1).
+__global__ void layout_kernel(BlockSet bs, int* __restrict__ order, int* __restrict__ pos) {
+    const unsigned N = 1u << bs.n;
+    for (unsigned s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x) {
+        unsigned rank = 0;
+        int t = 0;
+        for (int b = 0; b < bs.n; b++) {
+            if (!((s >> b) & 1u)) continue;
+            t++;
+            unsigned c = 1;   // C(b, t)
+            for (int q = 1; q <= t; q++) c = c * (unsigned)(b - t + q) / (unsigned)q;
+            rank += b >= t ? c : 0u;
+        }
+        const unsigned p = (unsigned)bs.cum[__popc(s)] + rank;
+        pos[s] = (int)p;
+        order[p] = (int)s;
+    }
+}
+
+struct DampTable {
+    double F[kMaxAtoms + 1][kMaxAtoms + 1];   // F[p][m]
+};
+
+DampTable damp_table(int n, double kappa, double tau) {
+    DampTable t{};
+    const double eta = std::exp(-kappa * tau);
+    const double loss = -std::expm1(-kappa * tau);   // 1 - eta without cancellation
+    for (int p = 0; p <= n; p++) {
+        for (int m = 0; p + m <= n; m++) {
+            double ratio = 1.0;   // (p + m)! / p! / m!  =  C(p + m, m)
+            for (int q = 1; q <= m; q++) ratio = ratio * (double)(p + q) / (double)q;
+            t.F[p][m] = std::sqrt(ratio * std::pow(loss, (double)m)) * std::pow(eta, 0.5 * (double)p);
+        }
+    }
+    return t;
+}
+
+// D_tau on all blocks in place.  Block x = row i of every block; threads run
+// along j (coalesced in each block).  Element (i, j) is in blocks
+// k >= max(level(i), level(j)); the new block-k value needs the old values
+// of blocks >= k only, so ascending k can overwrite in place.
+__global__ void __launch_bounds__(256) damping_kernel(BlockSet bs, DampTable t, const int* __restrict__ order,
+                                                      double* __restrict__ re, double* __restrict__ im) {
+    const int n = bs.n;
+    const unsigned N = 1u << n;
+    const unsigned i = blockIdx.x;
+    const int li = __popc((unsigned)order[i]);
+    for (unsigned j = blockIdx.y * blockDim.x + threadIdx.x; j < N; j += gridDim.y * blockDim.x) {
+        const int lj = __popc((unsigned)order[j]);
+        const int k0 = li > lj ? li : lj;
+        double vr[kMaxAtoms + 1], vi[kMaxAtoms + 1];
+#pragma unroll
+        for (int k = 0; k <= kMaxAtoms; k++) {
+            vr[k] = 0.0;
+            vi[k] = 0.0;
+            if (k >= k0 && k <= n) {
+                const size_t o = bs.off[k] + (size_t)i * bs.d[k] + j;
+                vr[k] = re[o];
+                vi[k] = im[o];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k <= kMaxAtoms; k++) {
+            if (k < k0 || k > n) continue;
+            const int p = k - li, q = k - lj;
+            double ar = 0.0, ai = 0.0;
+#pragma unroll
+            for (int m = 0; m + k <= kMaxAtoms; m++) {
+                if (k + m > n) break;
+                const double c = t.F[p][m] * t.F[q][m];
+                ar += c * vr[k + m];
+                ai += c * vi[k + m];
+            }
+            const size_t o = bs.off[k] + (size_t)i * bs.d[k] + j;
+            re[o] = ar;
+            im[o] = ai;
+        }
+    }
+}
+
+// Observable row over all blocks, deterministic: one warp per row of one
+// block (rows of all blocks enumerated block by block), per-CTA partials in a
+// fixed order, then one CTA sums the partials.
+constexpr int kObsWarps = 8;
+constexpr int kMaxStride = 2 * kMaxAtoms + 5;
+
+unsigned obs_grid(const Layout& L) {
+    size_t rows = 0;
+    for (int k = 0; k <= L.n; k++) rows += (size_t)L.dims[k];
+    size_t g = (rows + kObsWarps - 1) / kObsWarps;
+    return (unsigned)(g > 1024 ? 1024 : g);
+}
+
+__global__ void obs_partial_kernel(BlockSet bs, Model m, int has_model, const int* __restrict__ order,
+                                   const int* __restrict__ pos, const double* __restrict__ re,
+                                   const double* __restrict__ im, double* __restrict__ partials) {
+    __shared__ double acc[kObsWarps][kMaxStride];
+    const int n = bs.n;
+    const int stride = 2 * n + 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int j = lane; j < stride; j += 32) acc[warp][j] = 0.0;
+    __syncwarp();
+    unsigned rows = 0;
+    for (int k = 0; k <= n; k++) rows += (unsigned)bs.d[k];
+    double pur = 0.0, epair = 0.0;
+    for (unsigned q = blockIdx.x * kObsWarps + warp; q < rows; q += gridDim.x * kObsWarps) {
+        int k = 0;
+        unsigned i = q;
+        while (i >= (unsigned)bs.d[k]) {
+            i -= (unsigned)bs.d[k];
+            k++;
+        }
+        const unsigned d = (unsigned)bs.d[k];
+        const size_t row = bs.off[k] + (size_t)i * d;
+        for (unsigned c = lane; c < d; c += 32) {
+            const double x = re[row + c], y = im[row + c];
+            pur += x * x + y * y;
+        }
+        const unsigned s = (unsigned)order[i];
+        if (has_model && lane < n) {
+            const unsigned c = (unsigned)pos[s ^ (1u << lane)];
+            if (c < d) epair += h_pair(m, k, s, lane) * re[row + c];
+        }
+        if (lane == 0) {
+            const double v = re[row + i];
+            const int pc = __popc(s), p = k - pc;
+            for (int a = 0; a < n; a++)
+                if ((s >> (n - 1 - a)) & 1u) acc[warp][a] += v;
+            acc[warp][n] += v * (double)p;
+            acc[warp][n + 1 + p] += v;
+            acc[warp][2 * n + 2] += v;
+            if (has_model) acc[warp][2 * n + 4] += h_diag(m, k, s) * v;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        pur += __shfl_xor_sync(0xffffffffu, pur, o);
+        epair += __shfl_xor_sync(0xffffffffu, epair, o);
+    }
+    if (lane == 0) {
+        acc[warp][2 * n + 3] += pur;
+        acc[warp][2 * n + 4] += epair;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < stride; j += blockDim.x) {
+        double sum = 0.0;
+        for (int w = 0; w < kObsWarps; w++) sum += acc[w][j];
+        partials[(size_t)blockIdx.x * stride + j] = sum;
+    }
+}
+
+__global__ void obs_final_kernel(const double* __restrict__ partials, int blocks, int stride,
+                                 double* __restrict__ out) {
+    for (int j = threadIdx.x; j < stride; j += blockDim.x) {
+        double sum = 0.0;
+        for (int b = 0; b < blocks; b++) sum += partials[(size_t)b * stride + j];
+        out[j] = sum;
+    }
+}
+
+struct Tables {
+    int* order;
+    int* pos;
+};
+
+tc_status take_tables(const Layout& L, Arena& ar, Tables* t) {
+    t->order = ar.take<int>((size_t)L.N);
+    t->pos = ar.take<int>((size_t)L.N);
+    if (!t->pos) return fail(TC_ERR_WORKSPACE, "lindblad: workspace too small");
+    return TC_OK;
+}
+
+tc_status launch_layout(const Layout& L, const Tables& t, cudaStream_t s) {
+    const unsigned blocks = (unsigned)((L.N + 255) / 256);
+    layout_kernel<<<blocks, 256, 0, s>>>(block_set(L), t.order, t.pos);
+    TC_LAUNCH_CHECK();
+    return TC_OK;
+}
+
+tc_status launch_damping(const Layout& L, double kappa, double tau, const Tables& t, double* re, double* im,
+                         cudaStream_t s) {
+    dim3 grid((unsigned)L.N, (unsigned)((L.N + 255) / 256));
+    damping_kernel<<<grid, 256, 0, s>>>(block_set(L), damp_table(L.n, kappa, tau), t.order, re, im);
+    TC_LAUNCH_CHECK();
+    return TC_OK;
+}
+
+size_t obs_scratch_bytes(const Layout& L) {
+    return round256((size_t)obs_grid(L) * (2 * L.n + 5) * sizeof(double)) + 256;
+}
+
+tc_status launch_block_observables(const Layout& L, const Model& m, const Tables& t, const double* re,
+                                   const double* im, double* out, double* scratch, cudaStream_t s) {
+    const unsigned grid = obs_grid(L);
+    obs_partial_kernel<<<grid, 32 * kObsWarps, 0, s>>>(block_set(L), m, 1, t.order, t.pos, re, im, scratch);
+    TC_LAUNCH_CHECK();
+    obs_final_kernel<<<1, 64, 0, s>>>(scratch, (int)grid, 2 * L.n + 5, out);
+    TC_LAUNCH_CHECK();
+    return TC_OK;
+}
+
+size_t tables_bytes(int n) {
+    return 2 * round256(sizeof(int) << n);
+}
+
+size_t propagators_bytes(int n) {
+    return tables_bytes(n) + expm_block_bytes((size_t)1 << n) + 256;
+}
+
+size_t evolve_f64_bytes(int n) {
+    const Layout& L = layout_of(n);
+    const size_t total = L.off[n + 1];
+    const size_t NN = (size_t)L.N * L.N;
+    return tables_bytes(n) + 4 * round256(total * sizeof(double)) + 2 * round256(NN * sizeof(double)) +
+           obs_scratch_bytes(L) + 256;
+}
+
+tc_status evolve_f64(const Layout& L, const Model& m, double kappa, double dt, const double* U, double* rho,
+                     int steps, double* obs, Arena& ar, cudaStream_t s) {
+    const int n = L.n;
+    const size_t total = L.off[n + 1];
+    const size_t NN = (size_t)L.N * L.N;
+    Tables t{};
+    TC_TRY(take_tables(L, ar, &t));
+    double* Ur = ar.take<double>(total);
+    double* Ui = ar.take<double>(total);
+    double* Rr = ar.take<double>(total);
+    double* Ri = ar.take<double>(total);
+    double* Xr = ar.take<double>(NN);
+    double* Xi = ar.take<double>(NN);
+    double* scratch = ar.take<double>(obs_scratch_bytes(L) / sizeof(double));
+    if (!scratch) return fail(TC_ERR_WORKSPACE, "lindblad evolve: workspace too small");
+    const int stride = TC_OBS_STRIDE(n);
+    const bool damp = kappa > 0.0;
+
+    auto products = [&](cudaStream_t cs) -> tc_status {
+        for (int k = 0; k <= n; k++) {
+            const int d = L.dims[k];
+            const size_t o = L.off[k];
+            GemmF64 g1{};
+            g1.M = g1.N = g1.K = d;
+            g1.Ar = Ur + o; g1.Ai = Ui + o; g1.lda = d;
+            g1.Br = Rr + o; g1.Bi = Ri + o; g1.ldb = d;
+            g1.Cr = Xr; g1.Ci = Xi; g1.ldc = d;
+            g1.alpha = 1.0;
+            g1.cplx = 1;
+            GemmF64 g2 = g1;
+            g2.Ar = Xr; g2.Ai = Xi;
+            g2.Br = Ur + o; g2.Bi = Ui + o; g2.conjB = 1;
+            g2.Cr = Rr + o; g2.Ci = Ri + o;
+            g2.herm_lower = 1;
+            const double d3 = (double)d * d * d;
+            {
+                ProductTimer pt(8.0 * d3, cs);   // X = U_k rho_k
+                TC_TRY(gemm_f64(g1, cs));
+            }
+            {
+                ProductTimer pt(4.0 * d3, cs);   // rho_k = X U_k^dag, Hermitian half
+                TC_TRY(gemm_f64(g2, cs));
+            }
+        }
+        return TC_OK;
+    };
+    auto one_step = [&](int k, cudaStream_t cs) -> tc_status {
+        if (damp) TC_TRY(launch_damping(L, kappa, 0.5 * dt, t, Rr, Ri, cs));
+        TC_TRY(products(cs));
+        if (damp) TC_TRY(launch_damping(L, kappa, 0.5 * dt, t, Rr, Ri, cs));
+        if (obs) TC_TRY(launch_block_observables(L, m, t, Rr, Ri, obs + (size_t)k * stride, scratch, cs));
+        return TC_OK;
+    };
+    auto first = [&](cudaStream_t cs) -> tc_status {
+        TC_TRY(launch_layout(L, t, cs));
+        TC_TRY(launch_split_c128(U, Ur, Ui, total, cs));
+        TC_TRY(launch_split_c128(rho, Rr, Ri, total, cs));
+        if (obs) TC_TRY(launch_block_observables(L, m, t, Rr, Ri, obs, scratch, cs));
+        if (steps >= 1) TC_TRY(one_step(1, cs));
+        return TC_OK;
+    };
+    auto rest = [&](cudaStream_t cs) -> tc_status {
+        for (int k = 2; k <= steps; k++) TC_TRY(one_step(k, cs));
+        return TC_OK;
+    };
+    auto tail = [&](cudaStream_t cs) -> tc_status { return launch_join_c128(Rr, Ri, rho, total, cs); };
+    return run_captured(s, first, rest, tail, steps > 2 && !timing_enabled());
+}
+
+}  // namespace
+
+size_t lindblad_bytes(int n, int precision) {
+    if (precision != TC_FP64) return 0;
+    return std::max(propagators_bytes(n), evolve_f64_bytes(n));
+}
+
+}  // namespace tc
+
+using namespace tc;
+
+extern "C" TC_API tc_status tc_lindblad_layout(int n, int* dims, size_t* offsets, int* basis) {
+    if (n < 1 || n > kMaxAtoms) return fail(TC_ERR_INVALID_ARG, "n = %d outside 1..16", n);
+    const Layout& L = layout_of(n);
+    if (dims)
+        for (int k = 0; k <= n; k++) dims[k] = L.dims[k];
+    if (offsets)
+        for (int k = 0; k <= n + 1; k++) offsets[k] = L.off[k];
+    if (basis)
+        for (int s = 0; s < L.N; s++) basis[s] = L.order[s];
+    return TC_OK;
+}
+
+extern "C" TC_API tc_status tc_lindblad_propagators(const tc_params* params, double dt, void* U, void* work,
+                                                    size_t work_bytes, void* stream) {
+    Model m;
+    TC_TRY(make_model(params, &m));
+    if (!U) return fail(TC_ERR_INVALID_ARG, "U is NULL");
+    if (reinterpret_cast<uintptr_t>(U) & 15u) return fail(TC_ERR_INVALID_ARG, "U must be 16-byte aligned");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(TC_ERR_INVALID_ARG, "dt must be finite and > 0");
+    TC_TRY(check_work(work, work_bytes, propagators_bytes(m.n)));
+    TC_TRY(check_device());
+    const Layout& L = layout_of(m.n);
+    cudaStream_t s = as_stream(stream);
+    Arena ar{static_cast<char*>(work), work_bytes, 0};
+    Tables t{};
+    TC_TRY(take_tables(L, ar, &t));
+    TC_TRY(launch_layout(L, t, s));
+    double* Ud = static_cast<double*>(U);
+    for (int k = 0; k <= m.n; k++) {
+        Arena blk_ar = ar;   // every block reuses the same scratch
+        ExcitationBlock blk{k, L.dims[k], t.order, t.pos};
+        TC_TRY(expm_block_impl(m, blk, L.order.data(), dt, nullptr, Ud + 2 * L.off[k], blk_ar, s, nullptr,
+                               nullptr));
+    }
+    return TC_OK;
+}
+
+extern "C" TC_API tc_status tc_lindblad_evolve(const tc_params* params, double kappa, double dt, const void* U,
+                                               void* rho, int steps, int precision, double* obs, void* work,
+                                               size_t work_bytes, void* stream) {
+    Model m;
+    TC_TRY(make_model(params, &m));
+    if (!U || !rho) return fail(TC_ERR_INVALID_ARG, "U or rho is NULL");
+    if ((reinterpret_cast<uintptr_t>(U) | reinterpret_cast<uintptr_t>(rho)) & 15u)
+        return fail(TC_ERR_INVALID_ARG, "U and rho must be 16-byte aligned");
+    if (obs && (reinterpret_cast<uintptr_t>(obs) & 7u)) return fail(TC_ERR_INVALID_ARG, "obs must be 8-byte aligned");
+    if (!(kappa >= 0.0) || !std::isfinite(kappa)) return fail(TC_ERR_INVALID_ARG, "kappa must be finite and >= 0");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(TC_ERR_INVALID_ARG, "dt must be finite and > 0");
+    if (steps < 0) return fail(TC_ERR_INVALID_ARG, "steps < 0");
+    if (precision != TC_FP64)
+        return fail(TC_ERR_INVALID_ARG, "open-system form: precision %d not built (TC_FP64 only)", precision);
+    TC_TRY(check_work(work, work_bytes, evolve_f64_bytes(m.n)));
+    TC_TRY(check_device());
+    const Layout& L = layout_of(m.n);
+    Arena ar{static_cast<char*>(work), work_bytes, 0};
+    return evolve_f64(L, m, kappa, dt, static_cast<const double*>(U), static_cast<double*>(rho), steps, obs, ar,
+                      as_stream(stream));
+}

@@ -9,8 +9,23 @@ namespace tc {
 tc_status expm_impl(const double* H, int n, double dt, const tc_expm_opts* opts, double* U, Arena& ar,
                     cudaStream_t s, int* used_degree, int* used_squarings);
 
+// One excitation block of the model: the atom strings basis[0..d) (popcount
+// at most k, sorted by popcount) with photon count k - popcount(s); pos is
+// the inverse permutation over all 2^n strings.  order == pos == nullptr is
+// the closed model (k = n, d = 2^n, identity order).
+struct ExcitationBlock {
+    int k;
+    int d;
+    const int* order;   // device
+    const int* pos;     // device
+};
+
 // e^{-iHdt} from the model by Horner's rule with H applied as a stencil.
 size_t expm_model_bytes(int n);
+size_t expm_block_bytes(size_t d);
+tc_status expm_block_impl(const Model& m, const ExcitationBlock& blk, const int* host_order, double dt,
+                          const tc_expm_opts* opts, double* U, Arena& ar, cudaStream_t s, int* used_degree,
+                          int* used_squarings);
 tc_status expm_model_impl(const Model& m, double dt, const tc_expm_opts* opts, double* U, Arena& ar,
                           cudaStream_t s, int* used_degree, int* used_squarings);
 
@@ -22,6 +37,9 @@ tc_status evolve_f64(const double* U, double* rho, int n, int steps, int renorm_
 size_t evolve_lowp_bytes(int n, int precision);
 tc_status evolve_lowp(const double* U, double* rho, int n, int steps, int precision, int renorm_every,
                       const Model* m, double* obs, Arena& ar, cudaStream_t s);
+
+// Open-system form (packed excitation blocks).
+size_t lindblad_bytes(int n, int precision);
 
 // Reverse-mode gradient.
 size_t backward_bytes(int n, int steps, int ckpt_every);
