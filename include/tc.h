@@ -293,16 +293,23 @@ TC_API tc_status tc_lindblad_propagators(const tc_params* params, double dt, voi
  * with D_tau the exact damping over tau (the bosonic pure-loss channel,
  * mixing block k+m into block k) and U from tc_lindblad_propagators with the
  * same dt.  Second order in dt; kappa = 0 is the closed evolution of Eq. 6.
- *  U, rho   : device packed complex128; rho in/out (Hermitian blocks).
- *  precision: TC_FP64.
- *  obs      : device f64[(steps+1) * TC_OBS_STRIDE(n)] or NULL; the row of
- *             tc_observables summed over blocks, P(m) = probability of m
- *             photons, E = Tr(H rho).
- *  work     : device, >= tc_workspace_size(n, precision, TC_OP_LINDBLAD, 0, 0).
- *  Errors: TC_ERR_INVALID_ARG, TC_ERR_WORKSPACE, TC_ERR_CUDA. */
+ * The block products run on the DMMA GEMM (TC_FP64) or on the tcgen05
+ * tensor cores (split forms, as tc_evolve: one persistent launch over the
+ * tiles of every block per product, rho stored FP32 between steps).
+ *  U, rho      : device packed complex128; rho in/out (Hermitian blocks).
+ *  precision   : TC_FP64, TC_BF16X3, TC_TF32, TC_TF32X3.
+ *  renorm_every: 0 = never; else after every renorm_every-th step all
+ *                blocks are divided by the total trace (taken in FP64).
+ *  obs         : device f64[(steps+1) * TC_OBS_STRIDE(n)] or NULL; the row
+ *                of tc_observables summed over blocks, P(m) = probability
+ *                of m photons, E = Tr(H rho).
+ *  work        : device, >= tc_workspace_size(n, precision, TC_OP_LINDBLAD,
+ *                0, 0).
+ *  Errors: TC_ERR_INVALID_ARG, TC_ERR_WORKSPACE, TC_ERR_CUDA; a vanishing or
+ *  non-finite trace at renormalisation sets TC_ERR_NUMERIC (tc_sync_status). */
 TC_API tc_status tc_lindblad_evolve(const tc_params* params, double kappa, double dt, const void* U, void* rho,
-                                    int steps, int precision, double* obs, void* work, size_t work_bytes,
-                                    void* stream);
+                                    int steps, int precision, int renorm_every, double* obs, void* work,
+                                    size_t work_bytes, void* stream);
 
 /* tc_evolve_backward -- gradient of L = Tr(O rho_K), O = diag(O_diag), with
  * rho_K = U^K rho_0 U^-K and U = e^{-iH dt}, with respect to

@@ -27,6 +27,7 @@ d_k = #{s : popcount(s) <= k}) and written from the definitions:
                      rho(tau) = sum_m K_m rho K_m^dag,
                      K_m = sqrt((1 - eta)^m / m!) eta^{a^dag a / 2} a^m,
                      eta = e^{-kappa tau} (the bosonic pure-loss channel).
+* ``block_propagator`` e^{-iH dt} on the states of one excitation number.
 * ``split_step``     one symmetric (Strang) split step of length dt:
                      D_{dt/2}, then rho <- U rho U^dag with U = e^{-iH dt}
                      (from the oracle's Jacobi eigen-decomposition,
@@ -153,6 +154,16 @@ def propagator(n, g, omega_a, omega_c, dt, coupling=COUPLING_BOSONIC) -> np.ndar
     """U = e^{-iH dt} = V e^{-i w dt} V^T from the Jacobi eigen-decomposition."""
     w, V = jacobi_eig(hamiltonian(n, g, omega_a, omega_c, coupling))
     return (V * np.exp(-1j * w * dt)[None, :]) @ V.T
+
+
+def block_propagator(n, g, omega_a, omega_c, dt, k, coupling=COUPLING_BOSONIC):
+    """e^{-iH dt} restricted to the states of excitation number k (H maps that
+    set to itself), by Jacobi on the restriction; returns (U_k, indices of
+    those states in ``basis`` order)."""
+    sel = [i for i, (s, p) in enumerate(basis(n)) if _popcount(s) + p == k]
+    H = hamiltonian(n, g, omega_a, omega_c, coupling)[np.ix_(sel, sel)]
+    w, V = jacobi_eig(H)
+    return (V * np.exp(-1j * w * dt)[None, :]) @ V.T, sel
 
 
 def split_step(rho, U, n: int, kappa: float, dt: float) -> np.ndarray:

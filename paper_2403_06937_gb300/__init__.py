@@ -167,8 +167,8 @@ def lindblad_propagators(params: Params, dt: float, device="cuda", stream=None,
 
 
 def lindblad_evolve(params: Params, kappa: float, dt: float, U: torch.Tensor, rho: torch.Tensor, steps: int,
-                    precision="fp64", observe: bool = True, inplace: bool = False, stream=None,
-                    work: Optional[torch.Tensor] = None):
+                    precision="fp64", renorm_every: int = 0, observe: bool = True, inplace: bool = False,
+                    stream=None, work: Optional[torch.Tensor] = None):
     """tc_lindblad_evolve: `steps` split steps of Eq. 5 with photon leakage.  Returns (rho_T, obs or None)."""
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     n = params.n
@@ -182,7 +182,7 @@ def lindblad_evolve(params: Params, kappa: float, dt: float, U: torch.Tensor, rh
         work = _work(need, rho.device)
     p = params.c()
     _abi.call("tc_lindblad_evolve", ctypes.byref(p), float(kappa), float(dt), _ptr(U), _ptr(out), int(steps), prec,
-              _ptr(obs), _ptr(work), work.numel(), ctypes.c_void_p(_stream(stream)))
+              int(renorm_every), _ptr(obs), _ptr(work), work.numel(), ctypes.c_void_p(_stream(stream)))
     return out, obs
 
 

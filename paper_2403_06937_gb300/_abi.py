@@ -56,7 +56,7 @@ SIGNATURES = {
     "tc_expm_model": (I, [ctypes.POINTER(tc_params), D, ctypes.POINTER(tc_expm_opts), VP, VP, SZ, VP]),
     "tc_lindblad_layout": (I, [I, VP, VP, VP]),
     "tc_lindblad_propagators": (I, [ctypes.POINTER(tc_params), D, VP, VP, SZ, VP]),
-    "tc_lindblad_evolve": (I, [ctypes.POINTER(tc_params), D, D, VP, VP, I, I, VP, VP, SZ, VP]),
+    "tc_lindblad_evolve": (I, [ctypes.POINTER(tc_params), D, D, VP, VP, I, I, I, VP, VP, SZ, VP]),
     "tc_evolve": (I, [VP, VP, I, I, I, I, ctypes.POINTER(tc_params), VP, VP, SZ, VP]),
     "tc_observables": (I, [VP, I, ctypes.POINTER(tc_params), VP, VP, SZ, VP]),
     "tc_observables_noalloc": (I, [VP, I, ctypes.POINTER(tc_params), VP, VP]),

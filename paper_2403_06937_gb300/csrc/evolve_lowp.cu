@@ -34,12 +34,6 @@ unsigned grid_for(size_t work) {
     return (unsigned)(want < cap ? (want ? want : 1) : cap);
 }
 
-__device__ __forceinline__ float tf32_rna(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
-}
-
 // parts of a double (U): the split is taken in FP64
 template <int KIND, int S>
 __device__ __forceinline__ void split_f64(double v, void* base, size_t plane, size_t idx, int part) {
@@ -60,30 +54,6 @@ __device__ __forceinline__ void split_f64(double v, void* base, size_t plane, si
             float t = tf32_rna((float)r);
             p[(size_t)(part * S + s) * plane + idx] = t;
             r -= (double)t;
-        }
-    }
-}
-
-// parts of an FP32 value (rho): the split is taken in FP32
-template <int KIND, int S>
-__device__ __forceinline__ void split_f32(float v, void* base, size_t plane, size_t idx, int part) {
-    if constexpr (KIND == 0) {
-        __nv_bfloat16* p = static_cast<__nv_bfloat16*>(base);
-        float r = v;
-#pragma unroll
-        for (int s = 0; s < S; s++) {
-            __nv_bfloat16 b = __float2bfloat16_rn(r);
-            p[(size_t)(part * S + s) * plane + idx] = b;
-            r -= __bfloat162float(b);
-        }
-    } else {
-        float* p = static_cast<float*>(base);
-        float r = v;
-#pragma unroll
-        for (int s = 0; s < S; s++) {
-            float t = tf32_rna(r);
-            p[(size_t)(part * S + s) * plane + idx] = t;
-            r -= t;
         }
     }
 }

@@ -21,13 +21,21 @@
 //     F[p][m] = sqrt((1 - eta)^m / m! * (p + m)! / p!) * eta^{p/2},
 // eta = e^{-kappa tau}, p and q the photon counts of strings i and j in
 // block k.  D_tau is one HBM-bound pass over all blocks; the products are
-// dense complex GEMMs per block.
+// dense complex GEMMs per block: the FP64 DMMA GEMM block by block, or, in
+// the tensor-core forms, one persistent launch over the tiles of every block
+// per product (the batch GEMM, blocks zero-padded to multiples of 128, U_k in
+// increment form, rho_k in FP32 planes plus operand parts), with D_tau then
+// reading and writing the FP32 planes and rebuilding the parts.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <mutex>
 #include <vector>
 
+#include "cgemm_batch.cuh"
+#include "cgemm_tc.cuh"
 #include "graph.cuh"
+#include "lowp.cuh"
 #include "model_dev.cuh"
 #include "paths.cuh"
 #include "timing.cuh"
@@ -72,25 +80,44 @@ const Layout& layout_of(int n) {
     return *cache[n];
 }
 
-// Block dimensions and offsets by value, for kernels.
+// Block dimensions, row strides and plane offsets by value, for kernels.
+// FP64 packed planes: ld = d, off = the packed offsets.  FP32 planes of the
+// tensor-core forms: ld = Np (d rounded up to 128), off = sum of Np^2.
 struct BlockSet {
     int n;
     int d[kMaxAtoms + 1];
+    int ld[kMaxAtoms + 1];
     unsigned long long off[kMaxAtoms + 1];
     int cum[kMaxAtoms + 2];   // number of strings with popcount < c
 };
 
-BlockSet block_set(const Layout& L) {
+int padded(int d) { return d < 128 ? 128 : (d + 127) / 128 * 128; }
+
+BlockSet block_set(const Layout& L, bool pad = false) {
     BlockSet b{};
     b.n = L.n;
+    unsigned long long o = 0;
     for (int k = 0; k <= L.n; k++) {
         b.d[k] = L.dims[k];
-        b.off[k] = L.off[k];
+        b.ld[k] = pad ? padded(L.dims[k]) : L.dims[k];
+        b.off[k] = pad ? o : (unsigned long long)L.off[k];
+        o += (unsigned long long)b.ld[k] * b.ld[k];
     }
     b.cum[0] = 0;
     for (int c = 0; c <= L.n; c++) b.cum[c + 1] = L.dims[c];
     return b;
 }
+
+size_t padded_total(const Layout& L) {
+    size_t t = 0;
+    for (int k = 0; k <= L.n; k++) t += (size_t)padded(L.dims[k]) * padded(L.dims[k]);
+    return t;
+}
+
+// Operand-part planes of each block (tensor-core forms): [2 S][Np][Np].
+struct PartsSet {
+    void* p[kMaxAtoms + 1];
+};
 
 // Position of string s in the popcount order: the strings of smaller popcount,
 // plus the rank of s among strings of its popcount in increasing value, which
@@ -135,9 +162,11 @@ DampTable damp_table(int n, double kappa, double tau) {
 // D_tau on all blocks in place.  Block x = row i of every block; threads run
 // along j (coalesced in each block).  Element (i, j) is in blocks
 // k >= max(level(i), level(j)); the new block-k value needs the old values
-// of blocks >= k only, so ascending k can overwrite in place.
+// of blocks >= k only, so ascending k can overwrite in place.  Arithmetic in
+// FP64; T = float stores FP32 and, with S > 0, rebuilds the operand parts.
+template <typename T, int KIND, int S>
 __global__ void __launch_bounds__(256) damping_kernel(BlockSet bs, DampTable t, const int* __restrict__ order,
-                                                      double* __restrict__ re, double* __restrict__ im) {
+                                                      T* __restrict__ re, T* __restrict__ im, PartsSet ps) {
     const int n = bs.n;
     const unsigned N = 1u << n;
     const unsigned i = blockIdx.x;
@@ -151,9 +180,9 @@ __global__ void __launch_bounds__(256) damping_kernel(BlockSet bs, DampTable t, 
             vr[k] = 0.0;
             vi[k] = 0.0;
             if (k >= k0 && k <= n) {
-                const size_t o = bs.off[k] + (size_t)i * bs.d[k] + j;
-                vr[k] = re[o];
-                vi[k] = im[o];
+                const size_t o = bs.off[k] + (size_t)i * bs.ld[k] + j;
+                vr[k] = (double)re[o];
+                vi[k] = (double)im[o];
             }
         }
 #pragma unroll
@@ -168,9 +197,58 @@ __global__ void __launch_bounds__(256) damping_kernel(BlockSet bs, DampTable t, 
                 ar += c * vr[k + m];
                 ai += c * vi[k + m];
             }
-            const size_t o = bs.off[k] + (size_t)i * bs.d[k] + j;
-            re[o] = ar;
-            im[o] = ai;
+            const size_t idx = (size_t)i * bs.ld[k] + j;
+            const size_t o = bs.off[k] + idx;
+            const T wr = (T)ar, wi = (T)ai;
+            re[o] = wr;
+            im[o] = wi;
+            if constexpr (S > 0) {
+                const size_t plane = (size_t)bs.ld[k] * bs.ld[k];
+                split_f32<KIND, S>((float)wr, ps.p[k], plane, idx, 0);
+                split_f32<KIND, S>((float)wi, ps.p[k], plane, idx, 1);
+            }
+        }
+    }
+}
+
+// Trace over all blocks in FP64, one CTA, fixed order.
+template <typename T>
+__global__ void block_trace_kernel(BlockSet bs, const T* __restrict__ re, double* __restrict__ out) {
+    __shared__ double sh[1024];
+    double a = 0.0;
+    for (int k = 0; k <= bs.n; k++)
+        for (int i = threadIdx.x; i < bs.d[k]; i += blockDim.x)
+            a += (double)re[bs.off[k] + (size_t)i * bs.ld[k] + i];
+    sh[threadIdx.x] = a;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = sh[0];
+}
+
+// rho <- rho / Tr rho on every block (grid y = block); parts rebuilt when S > 0.
+template <typename T, int KIND, int S>
+__global__ void block_rescale_kernel(BlockSet bs, T* __restrict__ re, T* __restrict__ im, PartsSet ps,
+                                     const double* __restrict__ trace, unsigned* status) {
+    const double tr = trace[0];
+    if (!(tr > 0.0) || !isfinite(tr)) {
+        if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) atomicOr(status, kStatusNumeric);
+        return;
+    }
+    const double inv = 1.0 / tr;
+    const int k = blockIdx.y;
+    const size_t d = (size_t)bs.d[k], ld = (size_t)bs.ld[k];
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < d * d; e += (size_t)gridDim.x * blockDim.x) {
+        const size_t idx = (e / d) * ld + e % d;
+        const size_t o = bs.off[k] + idx;
+        const T wr = (T)((double)re[o] * inv), wi = (T)((double)im[o] * inv);
+        re[o] = wr;
+        im[o] = wi;
+        if constexpr (S > 0) {
+            split_f32<KIND, S>((float)wr, ps.p[k], ld * ld, idx, 0);
+            split_f32<KIND, S>((float)wi, ps.p[k], ld * ld, idx, 1);
         }
     }
 }
@@ -188,9 +266,10 @@ unsigned obs_grid(const Layout& L) {
     return (unsigned)(g > 1024 ? 1024 : g);
 }
 
+template <typename T>
 __global__ void obs_partial_kernel(BlockSet bs, Model m, int has_model, const int* __restrict__ order,
-                                   const int* __restrict__ pos, const double* __restrict__ re,
-                                   const double* __restrict__ im, double* __restrict__ partials) {
+                                   const int* __restrict__ pos, const T* __restrict__ re, const T* __restrict__ im,
+                                   double* __restrict__ partials) {
     __shared__ double acc[kObsWarps][kMaxStride];
     const int n = bs.n;
     const int stride = 2 * n + 5;
@@ -208,18 +287,18 @@ __global__ void obs_partial_kernel(BlockSet bs, Model m, int has_model, const in
             k++;
         }
         const unsigned d = (unsigned)bs.d[k];
-        const size_t row = bs.off[k] + (size_t)i * d;
+        const size_t row = bs.off[k] + (size_t)i * bs.ld[k];
         for (unsigned c = lane; c < d; c += 32) {
-            const double x = re[row + c], y = im[row + c];
+            const double x = (double)re[row + c], y = (double)im[row + c];
             pur += x * x + y * y;
         }
         const unsigned s = (unsigned)order[i];
         if (has_model && lane < n) {
             const unsigned c = (unsigned)pos[s ^ (1u << lane)];
-            if (c < d) epair += h_pair(m, k, s, lane) * re[row + c];
+            if (c < d) epair += h_pair(m, k, s, lane) * (double)re[row + c];
         }
         if (lane == 0) {
-            const double v = re[row + i];
+            const double v = (double)re[row + i];
             const int pc = __popc(s), p = k - pc;
             for (int a = 0; a < n; a++)
                 if ((s >> (n - 1 - a)) & 1u) acc[warp][a] += v;
@@ -273,10 +352,22 @@ tc_status launch_layout(const Layout& L, const Tables& t, cudaStream_t s) {
     return TC_OK;
 }
 
-tc_status launch_damping(const Layout& L, double kappa, double tau, const Tables& t, double* re, double* im,
-                         cudaStream_t s) {
+template <typename T, int KIND, int S>
+tc_status launch_damping(const Layout& L, const BlockSet& bs, double kappa, double tau, const Tables& t, T* re, T* im,
+                         const PartsSet& ps, cudaStream_t s) {
     dim3 grid((unsigned)L.N, (unsigned)((L.N + 255) / 256));
-    damping_kernel<<<grid, 256, 0, s>>>(block_set(L), damp_table(L.n, kappa, tau), t.order, re, im);
+    damping_kernel<T, KIND, S><<<grid, 256, 0, s>>>(bs, damp_table(L.n, kappa, tau), t.order, re, im, ps);
+    TC_LAUNCH_CHECK();
+    return TC_OK;
+}
+
+template <typename T, int KIND, int S>
+tc_status launch_block_renorm(const Layout& L, const BlockSet& bs, T* re, T* im, const PartsSet& ps, double* scratch,
+                              cudaStream_t s) {
+    block_trace_kernel<T><<<1, 1024, 0, s>>>(bs, re, scratch);
+    TC_LAUNCH_CHECK();
+    dim3 grid(256, (unsigned)(L.n + 1));
+    block_rescale_kernel<T, KIND, S><<<grid, 256, 0, s>>>(bs, re, im, ps, scratch, device_status_word());
     TC_LAUNCH_CHECK();
     return TC_OK;
 }
@@ -285,10 +376,11 @@ size_t obs_scratch_bytes(const Layout& L) {
     return round256((size_t)obs_grid(L) * (2 * L.n + 5) * sizeof(double)) + 256;
 }
 
-tc_status launch_block_observables(const Layout& L, const Model& m, const Tables& t, const double* re,
-                                   const double* im, double* out, double* scratch, cudaStream_t s) {
+template <typename T>
+tc_status launch_block_observables(const Layout& L, const BlockSet& bs, const Model& m, const Tables& t, const T* re,
+                                   const T* im, double* out, double* scratch, cudaStream_t s) {
     const unsigned grid = obs_grid(L);
-    obs_partial_kernel<<<grid, 32 * kObsWarps, 0, s>>>(block_set(L), m, 1, t.order, t.pos, re, im, scratch);
+    obs_partial_kernel<T><<<grid, 32 * kObsWarps, 0, s>>>(bs, m, 1, t.order, t.pos, re, im, scratch);
     TC_LAUNCH_CHECK();
     obs_final_kernel<<<1, 64, 0, s>>>(scratch, (int)grid, 2 * L.n + 5, out);
     TC_LAUNCH_CHECK();
@@ -312,7 +404,7 @@ size_t evolve_f64_bytes(int n) {
 }
 
 tc_status evolve_f64(const Layout& L, const Model& m, double kappa, double dt, const double* U, double* rho,
-                     int steps, double* obs, Arena& ar, cudaStream_t s) {
+                     int steps, int renorm_every, double* obs, Arena& ar, cudaStream_t s) {
     const int n = L.n;
     const size_t total = L.off[n + 1];
     const size_t NN = (size_t)L.N * L.N;
@@ -328,6 +420,8 @@ tc_status evolve_f64(const Layout& L, const Model& m, double kappa, double dt, c
     if (!scratch) return fail(TC_ERR_WORKSPACE, "lindblad evolve: workspace too small");
     const int stride = TC_OBS_STRIDE(n);
     const bool damp = kappa > 0.0;
+    const BlockSet bs = block_set(L);
+    const PartsSet none{};
 
     auto products = [&](cudaStream_t cs) -> tc_status {
         for (int k = 0; k <= n; k++) {
@@ -358,17 +452,19 @@ tc_status evolve_f64(const Layout& L, const Model& m, double kappa, double dt, c
         return TC_OK;
     };
     auto one_step = [&](int k, cudaStream_t cs) -> tc_status {
-        if (damp) TC_TRY(launch_damping(L, kappa, 0.5 * dt, t, Rr, Ri, cs));
+        if (damp) TC_TRY((launch_damping<double, 0, 0>(L, bs, kappa, 0.5 * dt, t, Rr, Ri, none, cs)));
         TC_TRY(products(cs));
-        if (damp) TC_TRY(launch_damping(L, kappa, 0.5 * dt, t, Rr, Ri, cs));
-        if (obs) TC_TRY(launch_block_observables(L, m, t, Rr, Ri, obs + (size_t)k * stride, scratch, cs));
+        if (damp) TC_TRY((launch_damping<double, 0, 0>(L, bs, kappa, 0.5 * dt, t, Rr, Ri, none, cs)));
+        if (renorm_every > 0 && k % renorm_every == 0)
+            TC_TRY((launch_block_renorm<double, 0, 0>(L, bs, Rr, Ri, none, scratch, cs)));
+        if (obs) TC_TRY(launch_block_observables<double>(L, bs, m, t, Rr, Ri, obs + (size_t)k * stride, scratch, cs));
         return TC_OK;
     };
     auto first = [&](cudaStream_t cs) -> tc_status {
         TC_TRY(launch_layout(L, t, cs));
         TC_TRY(launch_split_c128(U, Ur, Ui, total, cs));
         TC_TRY(launch_split_c128(rho, Rr, Ri, total, cs));
-        if (obs) TC_TRY(launch_block_observables(L, m, t, Rr, Ri, obs, scratch, cs));
+        if (obs) TC_TRY(launch_block_observables<double>(L, bs, m, t, Rr, Ri, obs, scratch, cs));
         if (steps >= 1) TC_TRY(one_step(1, cs));
         return TC_OK;
     };
@@ -380,11 +476,150 @@ tc_status evolve_f64(const Layout& L, const Model& m, double kappa, double dt, c
     return run_captured(s, first, rest, tail, steps > 2 && !timing_enabled());
 }
 
+// ---------------------------------------------------------------- tensor-core forms
+size_t evolve_lowp_bytes_blocks(int n, int precision) {
+    const Layout& L = layout_of(n);
+    const int S = cgemm_parts(precision);
+    const size_t E = cgemm_elem_bytes(precision);
+    size_t b = tables_bytes(n) + round256(sizeof(BatchSys) * (n + 1)) + 256;
+    for (int k = 0; k <= n; k++) b += 3 * (size_t)(2 * S) * plane_bytes(padded(L.dims[k]), E);
+    b += 4 * round256(padded_total(L) * sizeof(float));
+    return b + obs_scratch_bytes(L) + 256;
+}
+
+template <int KIND, int S>
+tc_status evolve_lowp_t(const Layout& L, const Model& m, int precision, double kappa, double dt, const double* U,
+                        double* rho, int steps, int renorm_every, double* obs, Arena& ar, cudaStream_t s) {
+    const int n = L.n;
+    const size_t E = cgemm_elem_bytes(precision);
+    const size_t PT = padded_total(L);
+    Tables t{};
+    TC_TRY(take_tables(L, ar, &t));
+    BatchSys* sys_dev = ar.take<BatchSys>((size_t)(n + 1));
+    float* Rr = ar.take<float>(PT);
+    float* Ri = ar.take<float>(PT);
+    float* Xr = ar.take<float>(PT);
+    float* Xi = ar.take<float>(PT);
+    PartsSet up{}, rp{}, xp{};
+    for (int k = 0; k <= n; k++) {
+        const size_t pb = (size_t)(2 * S) * plane_bytes(padded(L.dims[k]), E);
+        up.p[k] = ar.take<uint8_t>(pb);
+        rp.p[k] = ar.take<uint8_t>(pb);
+        xp.p[k] = ar.take<uint8_t>(pb);
+    }
+    double* scratch = ar.take<double>(obs_scratch_bytes(L) / sizeof(double));
+    if (!scratch) return fail(TC_ERR_WORKSPACE, "lindblad evolve: workspace too small");
+    const BlockSet bs = block_set(L, true);
+    const int stride = TC_OBS_STRIDE(n);
+    const bool damp = kappa > 0.0;
+    unsigned* status = device_status_word();
+
+    // descriptors, blocks in decreasing size (the longest tiles first)
+    std::vector<BatchSys> host(n + 1);
+    int tiles[2] = {0, 0};
+    double flops = 0.0;
+    for (int q = 0; q <= n; q++) {
+        const int k = n - q;
+        const int Np = bs.ld[k];
+        BatchSys& h = host[q];
+        std::memset(&h, 0, sizeof(h));
+        TC_TRY(make_part_map(&h.tmU, up.p[k], Np, 2 * S, precision));
+        TC_TRY(make_part_map(&h.tmR, rp.p[k], Np, 2 * S, precision));
+        TC_TRY(make_part_map(&h.tmX, xp.p[k], Np, 2 * S, precision));
+        h.Rr = Rr + bs.off[k];
+        h.Ri = Ri + bs.off[k];
+        h.Rparts = rp.p[k];
+        h.Xr = Xr + bs.off[k];
+        h.Xi = Xi + bs.off[k];
+        h.Xparts = xp.p[k];
+        h.Np = Np;
+        h.tiles = Np / 128;
+        h.tile_begin[0] = tiles[0];
+        h.tile_begin[1] = tiles[1];
+        tiles[0] += h.tiles * h.tiles;
+        tiles[1] += h.tiles * (h.tiles + 1) / 2;
+        flops += 12.0 * (double)L.dims[k] * L.dims[k] * L.dims[k];
+    }
+    const double prod = (double)cgemm_products(precision);
+
+    auto one_step = [&](int k, cudaStream_t cs) -> tc_status {
+        if (damp) TC_TRY((launch_damping<float, KIND, S>(L, bs, kappa, 0.5 * dt, t, Rr, Ri, rp, cs)));
+        {
+            ProductTimer pt(flops * prod * (8.0 / 12.0), cs);   // X_k = U_k rho_k, every block
+            TC_TRY(cgemm_batch(precision, 0, sys_dev, n + 1, tiles[0], status, cs));
+        }
+        {
+            ProductTimer pt(flops * prod * (4.0 / 12.0), cs);   // rho_k = X_k U_k^dag, Hermitian halves
+            TC_TRY(cgemm_batch(precision, 1, sys_dev, n + 1, tiles[1], status, cs));
+        }
+        if (damp) TC_TRY((launch_damping<float, KIND, S>(L, bs, kappa, 0.5 * dt, t, Rr, Ri, rp, cs)));
+        if (renorm_every > 0 && k % renorm_every == 0)
+            TC_TRY((launch_block_renorm<float, KIND, S>(L, bs, Rr, Ri, rp, scratch, cs)));
+        if (obs) TC_TRY(launch_block_observables<float>(L, bs, m, t, Rr, Ri, obs + (size_t)k * stride, scratch, cs));
+        return TC_OK;
+    };
+    auto block_bufs = [&](int k) {
+        LowpBufs b{};
+        b.N = L.dims[k];
+        b.Np = bs.ld[k];
+        b.S = S;
+        b.E = E;
+        b.Uparts = up.p[k];
+        b.Rr = Rr + bs.off[k];
+        b.Ri = Ri + bs.off[k];
+        b.Rparts = rp.p[k];
+        b.Xr = Xr + bs.off[k];
+        b.Xi = Xi + bs.off[k];
+        b.Xparts = xp.p[k];
+        b.scratch = scratch;
+        return b;
+    };
+    auto first = [&](cudaStream_t cs) -> tc_status {
+        TC_CUDA(cudaMemcpyAsync(sys_dev, host.data(), sizeof(BatchSys) * (n + 1), cudaMemcpyHostToDevice, cs));
+        TC_CUDA(cudaStreamSynchronize(cs));   // the host copy of the descriptors may go
+        TC_TRY(launch_layout(L, t, cs));
+        for (int k = 0; k <= n; k++) {
+            LowpBufs b = block_bufs(k);
+            TC_TRY(lowp_prep(precision, U + 2 * L.off[k], rho + 2 * L.off[k], b, cs));
+        }
+        if (obs) TC_TRY(launch_block_observables<float>(L, bs, m, t, Rr, Ri, obs, scratch, cs));
+        if (steps >= 1) TC_TRY(one_step(1, cs));
+        return TC_OK;
+    };
+    auto rest = [&](cudaStream_t cs) -> tc_status {
+        for (int k = 2; k <= steps; k++) TC_TRY(one_step(k, cs));
+        return TC_OK;
+    };
+    auto tail = [&](cudaStream_t cs) -> tc_status {
+        for (int k = 0; k <= n; k++) TC_TRY(lowp_finish(block_bufs(k), rho + 2 * L.off[k], cs));
+        return TC_OK;
+    };
+    return run_captured(s, first, rest, tail, steps > 2 && !timing_enabled());
+}
+
+tc_status evolve_lowp_blocks(const Layout& L, const Model& m, int precision, double kappa, double dt,
+                             const double* U, double* rho, int steps, int renorm_every, double* obs, Arena& ar,
+                             cudaStream_t s) {
+    switch (precision) {
+        case TC_BF16X3:
+            return evolve_lowp_t<0, 3>(L, m, precision, kappa, dt, U, rho, steps, renorm_every, obs, ar, s);
+        case TC_TF32:
+            return evolve_lowp_t<1, 1>(L, m, precision, kappa, dt, U, rho, steps, renorm_every, obs, ar, s);
+        case TC_TF32X3:
+            return evolve_lowp_t<1, 2>(L, m, precision, kappa, dt, U, rho, steps, renorm_every, obs, ar, s);
+    }
+    return fail(TC_ERR_INVALID_ARG, "unknown precision %d", precision);
+}
+
+size_t evolve_bytes(int n, int precision) {
+    return precision == TC_FP64 ? evolve_f64_bytes(n) : evolve_lowp_bytes_blocks(n, precision);
+}
+
 }  // namespace
 
 size_t lindblad_bytes(int n, int precision) {
-    if (precision != TC_FP64) return 0;
-    return std::max(propagators_bytes(n), evolve_f64_bytes(n));
+    if (precision < TC_FP64 || precision > TC_TF32X3) return 0;
+    return std::max(propagators_bytes(n), evolve_bytes(n, precision));
 }
 
 }  // namespace tc
@@ -429,8 +664,8 @@ extern "C" TC_API tc_status tc_lindblad_propagators(const tc_params* params, dou
 }
 
 extern "C" TC_API tc_status tc_lindblad_evolve(const tc_params* params, double kappa, double dt, const void* U,
-                                               void* rho, int steps, int precision, double* obs, void* work,
-                                               size_t work_bytes, void* stream) {
+                                               void* rho, int steps, int precision, int renorm_every, double* obs,
+                                               void* work, size_t work_bytes, void* stream) {
     Model m;
     TC_TRY(make_model(params, &m));
     if (!U || !rho) return fail(TC_ERR_INVALID_ARG, "U or rho is NULL");
@@ -439,13 +674,15 @@ extern "C" TC_API tc_status tc_lindblad_evolve(const tc_params* params, double k
     if (obs && (reinterpret_cast<uintptr_t>(obs) & 7u)) return fail(TC_ERR_INVALID_ARG, "obs must be 8-byte aligned");
     if (!(kappa >= 0.0) || !std::isfinite(kappa)) return fail(TC_ERR_INVALID_ARG, "kappa must be finite and >= 0");
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(TC_ERR_INVALID_ARG, "dt must be finite and > 0");
-    if (steps < 0) return fail(TC_ERR_INVALID_ARG, "steps < 0");
-    if (precision != TC_FP64)
-        return fail(TC_ERR_INVALID_ARG, "open-system form: precision %d not built (TC_FP64 only)", precision);
-    TC_TRY(check_work(work, work_bytes, evolve_f64_bytes(m.n)));
+    if (steps < 0 || renorm_every < 0) return fail(TC_ERR_INVALID_ARG, "steps / renorm_every < 0");
+    if (precision < TC_FP64 || precision > TC_TF32X3) return fail(TC_ERR_INVALID_ARG, "unknown precision %d", precision);
+    TC_TRY(check_work(work, work_bytes, evolve_bytes(m.n, precision)));
     TC_TRY(check_device());
     const Layout& L = layout_of(m.n);
     Arena ar{static_cast<char*>(work), work_bytes, 0};
-    return evolve_f64(L, m, kappa, dt, static_cast<const double*>(U), static_cast<double*>(rho), steps, obs, ar,
-                      as_stream(stream));
+    const double* Ud = static_cast<const double*>(U);
+    double* Rd = static_cast<double*>(rho);
+    if (precision == TC_FP64)
+        return evolve_f64(L, m, kappa, dt, Ud, Rd, steps, renorm_every, obs, ar, as_stream(stream));
+    return evolve_lowp_blocks(L, m, precision, kappa, dt, Ud, Rd, steps, renorm_every, obs, ar, as_stream(stream));
 }

@@ -2,9 +2,41 @@
 // shared by the single-system loop (evolve_lowp.cu) and the batch (batch.cu).
 #pragma once
 
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 
 namespace tc {
+
+__device__ __forceinline__ float tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// parts of an FP32 value (rho): the split is taken in FP32
+template <int KIND, int S>
+__device__ __forceinline__ void split_f32(float v, void* base, size_t plane, size_t idx, int part) {
+    if constexpr (KIND == 0) {
+        __nv_bfloat16* p = static_cast<__nv_bfloat16*>(base);
+        float r = v;
+#pragma unroll
+        for (int s = 0; s < S; s++) {
+            __nv_bfloat16 b = __float2bfloat16_rn(r);
+            p[(size_t)(part * S + s) * plane + idx] = b;
+            r -= __bfloat162float(b);
+        }
+    } else {
+        float* p = static_cast<float*>(base);
+        float r = v;
+#pragma unroll
+        for (int s = 0; s < S; s++) {
+            float t = tf32_rna(r);
+            p[(size_t)(part * S + s) * plane + idx] = t;
+            r -= t;
+        }
+    }
+}
 
 struct LowpBufs {
     int N, Np, S;

@@ -187,6 +187,100 @@ def test_invariants_n10(tc):
         assert torch.max(torch.abs(blk - blk.conj().T)).item() == 0.0
 
 
+# ---------------------------------------------------------------- tensor-core forms
+ACC = {"bf16x3": (6, 16), "tf32x3": (3, 8), "tf32": (1, 8)}   # part products, K per MMA
+
+
+def lowp_step_bound(precision, K, vnorm, scale, damped):
+    """One split step of a tensor-core form (the closed-form bound of the
+    increment-form products, plus two FP32 stores per damping pass):
+    2^-24 (4 + 2 n_acc 2 ||V||) max|rho| for the two products, TF32 adding
+    4 2^-11 ||V|| max|rho| for its one-part operands."""
+    prod, kstep = ACC[precision]
+    n_acc = prod * K / kstep
+    stores = 4.0 + (4.0 if damped else 0.0)
+    b = 2.0 ** -24 * (stores + 2.0 * n_acc * 2.0 * vnorm) * scale
+    if precision == "tf32":
+        b += 4.0 * 2.0 ** -11 * vnorm * scale
+    return b
+
+
+def _block_vnorm(U):
+    tr = np.trace(U)
+    c = tr / abs(tr)
+    return float(np.abs(U / c - np.eye(U.shape[0])).sum(1).max())
+
+
+@pytest.mark.parametrize("precision", ["bf16x3", "tf32x3", "tf32"])
+def test_lowp_matches_oracle_n6(tc, L, precision):
+    """n = 6 (blocks 1..64, each one padded tile), kappa = 0.3, 30 steps."""
+    n, dt, steps, kappa = 6, 0.1, 30, 0.3
+    g = W.draw_couplings(n, 70) * 20
+    p = _params(tc, n, g, 1.002, 1.0)
+    lay = tc.lindblad_layout(n)
+    rho0 = _random_block_rho(L, n, 71)
+    Uo = L.propagator(n, g, 1.002, 1.0, dt)
+    vnorm = max(_block_vnorm(Uo[np.ix_(sel, sel)]) for sel in (_oracle_index(L, lay, k) for k in range(n + 1)))
+    U = tc.lindblad_propagators(p, dt)
+    rho = torch.from_numpy(_pack(L, lay, rho0)).cuda()
+    out, obs = tc.lindblad_evolve(p, kappa, dt, U, rho, steps, precision)
+    ref, rows = L.propagate(n, g, 1.002, 1.0, kappa, dt, steps, rho0)
+    got = _unpack(L, lay, out.cpu().numpy())
+    scale = np.max(np.abs(rho0))
+    tol = steps * lowp_step_bound(precision, 128, vnorm, scale, True)
+    err = np.max(np.abs(got - ref))
+    assert err < tol, (err, tol)
+    D = got.shape[0]
+    o = obs.cpu().numpy()
+    assert np.max(np.abs(o[:, :n + 1] - rows[:, :n + 1])) < D * tol
+
+
+@pytest.mark.parametrize("precision", ["bf16x3", "tf32x3"])
+def test_lowp_matches_fp64_path_n8(tc, L, precision):
+    """n = 8: blocks up to 256 (two tiles, ragged 163 / 219 / 247 / 255), against the
+    FP64 open-system path (itself at oracle parity); ||V_k|| of the oracle's
+    block propagators bounds the error."""
+    n, dt, steps, kappa = 8, 0.05, 40, 0.4
+    g = W.draw_couplings(n, 80) * 20
+    p = _params(tc, n, g, 1.002, 1.0)
+    lay = tc.lindblad_layout(n)
+    U = tc.lindblad_propagators(p, dt)
+    vnorm = max(_block_vnorm(L.block_propagator(n, g, 1.002, 1.0, dt, k)[0]) for k in range(n + 1))
+    rho = torch.zeros(lay.total, dtype=torch.complex128, device="cuda")
+    top = lay.blocks(rho)[n]
+    j = lay.basis.index((1 << n) - 1)
+    top[j, j] = 1.0
+    ref, obs_ref = tc.lindblad_evolve(p, kappa, dt, U, rho, steps, "fp64")
+    out, obs = tc.lindblad_evolve(p, kappa, dt, U, rho, steps, precision)
+    tol = steps * lowp_step_bound(precision, 256, vnorm, 1.0, True)
+    err = torch.max(torch.abs(out - ref)).item()
+    assert err < tol, (err, tol)
+    pops = torch.max(torch.abs(obs[:, :n] - obs_ref[:, :n])).item()
+    assert pops < 1e-5   # the stated target of the split forms on populations
+
+
+def test_lowp_renormalisation_n10(tc):
+    """Split-BF16 at n = 10 with renormalisation every 10 steps: the total trace is
+    back to 1 to FP32 rounding after each renormalisation, and the blocks stay Hermitian."""
+    n, dt, steps, kappa = 10, 0.05, 30, 0.5
+    g = W.draw_couplings(n, 90) * 20
+    p = _params(tc, n, g, 1.002, 1.0)
+    lay = tc.lindblad_layout(n)
+    rho = torch.zeros(lay.total, dtype=torch.complex128, device="cuda")
+    top = lay.blocks(rho)[n]
+    j = lay.basis.index((1 << n) - 1)
+    top[j, j] = 1.0
+    out, obs = tc.lindblad_evolve(p, kappa, dt, tc.lindblad_propagators(p, dt), rho, steps, "bf16x3",
+                                  renorm_every=10)
+    o = obs.cpu().numpy()
+    for k in (10, 20, 30):
+        assert abs(o[k, 2 * n + 2] - 1.0) < 1024 * 2.0 ** -24
+    for blk in lay.blocks(out):
+        assert torch.max(torch.abs(blk - blk.conj().T)).item() == 0.0
+    exc = o[:, :n].sum(axis=1) + o[:, n]
+    assert exc[-1] < exc[0] - 0.05
+
+
 def test_errors(tc):
     import ctypes
     from paper_2403_06937_gb300 import _abi
@@ -198,8 +292,10 @@ def test_errors(tc):
     w = torch.empty(1024, dtype=torch.uint8, device="cuda")
     lib = _abi.load()
     st = lib.tc_lindblad_evolve(ctypes.byref(p), 0.1, 0.1, ctypes.c_void_p(U.data_ptr()),
-                                ctypes.c_void_p(rho.data_ptr()), 3, 0, None, ctypes.c_void_p(w.data_ptr()), 1024, None)
+                                ctypes.c_void_p(rho.data_ptr()), 3, 0, 0, None, ctypes.c_void_p(w.data_ptr()), 1024,
+                                None)
     assert st == 3 and "need" in _abi.last_error()
     st = lib.tc_lindblad_evolve(ctypes.byref(p), -1.0, 0.1, ctypes.c_void_p(U.data_ptr()),
-                                ctypes.c_void_p(rho.data_ptr()), 3, 0, None, ctypes.c_void_p(w.data_ptr()), 1024, None)
+                                ctypes.c_void_p(rho.data_ptr()), 3, 0, 0, None, ctypes.c_void_p(w.data_ptr()), 1024,
+                                None)
     assert st == 1

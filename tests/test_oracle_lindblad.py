@@ -177,7 +177,16 @@ def pin_split_step_keeps_blocks_and_trace(L):
     assert kk[1] < kk[0]
 
 
-PINS = [pin_basis_and_annihilation, pin_damping_is_the_superoperator_exponential, pin_damping_one_photon_by_hand,
+def pin_block_propagator_is_a_block_of_the_full_one(L):
+    n, dt = 4, 0.3
+    g = W.draw_couplings(n, 12) * 30
+    U = L.propagator(n, g, 1.01, 0.99, dt)
+    for k in range(n + 1):
+        Uk, sel = L.block_propagator(n, g, 1.01, 0.99, dt, k)
+        np.testing.assert_allclose(Uk, U[np.ix_(sel, sel)], atol=1e-13)
+
+
+PINS = [pin_block_propagator_is_a_block_of_the_full_one, pin_basis_and_annihilation, pin_damping_is_the_superoperator_exponential, pin_damping_one_photon_by_hand,
         pin_damping_is_cptp, pin_damped_jaynes_cummings, pin_excitation_balance, pin_split_step_is_second_order,
         pin_split_step_keeps_blocks_and_trace]
 PINS_WITH_ORACLE = [pin_hamiltonian_top_block_is_the_closed_model, pin_kappa_zero_is_the_closed_oracle]
