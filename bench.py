@@ -53,7 +53,8 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["bf16x3", "tf32x3", "tf32", "fp64"], default="bf16x3")
-    ap.add_argument("--workload", choices=["n14", "n15", "n12", "n8", "batch", "grad"], default="n14",
+    ap.add_argument("--workload", choices=["n14", "n15", "n12", "n8", "batch", "grad", "open14", "open12"],
+                    default="n14",
                     help="n14 (default, the metric's workload), n12, n8; batch: 64 systems n=6..12 "
                          "(aggregate system-steps/s vs per-system sequential calls); grad: n=11 gradient")
     ap.add_argument("--no-e2e", action="store_true")
@@ -482,10 +483,107 @@ def run_grad(a):
     return 0
 
 
+def run_open(a):
+    """Open system (Eq. 5 with photon leakage): split steps of tc_lindblad_evolve on the excitation blocks."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2403_06937_gb300 as tc
+    tc.device_check()
+    n = int(a.workload[4:])
+    cfg = W.config_open(n)
+    prec = a.precision
+    p = tc.Params(n, list(map(float, cfg.g)), cfg.omega_a, cfg.omega_c)
+    lay = tc.lindblad_layout(n)
+    work = torch.empty(tc.workspace_size(n, tc.PRECISIONS[prec], tc._abi.TC_OP_LINDBLAD), dtype=torch.uint8,
+                       device="cuda")
+    t_setup = time.perf_counter()
+    U = tc.lindblad_propagators(p, cfg.dt, work=work)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t_setup
+    rho = torch.zeros(lay.total, dtype=torch.complex128, device="cuda")
+    j = lay.basis.index((1 << n) - 1)
+    lay.blocks(rho)[n][j, j] = 1.0
+    stream = torch.cuda.current_stream()
+    renorm = cfg.renorm_every if prec != "fp64" else 0
+    if a.warmup:
+        tc.lindblad_evolve(p, cfg.kappa, cfg.dt, U, rho, a.warmup, prec, renorm_every=renorm, inplace=True, work=work)
+    torch.cuda.synchronize()
+    tc.timing_read()
+    tc.timing_enable(True)
+    l0 = tc.launch_count()
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    rho, obs = tc.lindblad_evolve(p, cfg.kappa, cfg.dt, U, rho, a.steps, prec, renorm_every=renorm, inplace=True,
+                                  work=work)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    tc.timing_enable(False)
+    launches = tc.launch_count() - l0
+    tc.sync_status()
+    ms = e0.elapsed_time(e1)
+    klaunch, kms, kflops = tc.timing_read()
+    o = obs.cpu().numpy()
+    credited = sum(12.0 * d ** 3 for d in lay.dims)
+    peaks, peak_src = _measured_peaks()
+    peak = peaks["bf16_tflops_sustained"] if prec == "bf16x3" else (
+        peaks["bf16_tflops_sustained"] / 2 if prec in ("tf32", "tf32x3") else _fp64_peak_live(torch))
+    achieved = kflops / (kms * 1e-3) / 1e12 if kms > 0 else 0.0
+    value = a.steps / (ms * 1e-3)
+    line = {"metric": "open-system split steps/s (Eq. 5 with photon leakage)", "value": value, "unit": "steps/s",
+            "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "bf16x3": "bf16", "tf32": "tf32", "tf32x3": "tf32"}[prec], "data": "synthetic",
+            "config": {"workload": cfg.description, "precision": prec, "blocks": lay.dims,
+                       "state_elements": lay.total, "setup_s": t_setup,
+                       "l2": "inputs larger than L2 (packed state %d MiB in complex128)" % (16 * lay.total >> 20)},
+            "credited_flops_per_step": credited, "credited_tflops": credited * value / 1e12,
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak if peak else None, "traffic": None,
+                         "kernel": "batched complex GEMM over the excitation blocks (%s), %d launches, %.3f ms avg"
+                                   % (prec, klaunch, kms / max(klaunch, 1)),
+                         "peak_source": peak_src},
+            "clocks": ck, "gpu_launches": launches,
+            "error": {"kind": "conserved total trace after %d steps (oracle-free)" % (a.warmup + a.steps),
+                      "trace": float(abs(o[-1, 2 * n + 2] - 1.0)),
+                      "mean_photons": float(o[-1, n]), "excitation": float(o[-1, :n].sum() + o[-1, n])}}
+    if not a.no_e2e:
+        # end to end: the packed state from pinned host memory, one split step, the state and its row back
+        rho_h = torch.empty(lay.total, dtype=torch.complex128, pin_memory=True)
+        rho_h.copy_(rho)
+        obs_h = torch.empty((2, 2 * n + 5), dtype=torch.float64, pin_memory=True)
+        k = max(1, min(a.steps, 5))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(k):
+            rho.copy_(rho_h, non_blocking=True)
+            rho, ob = tc.lindblad_evolve(p, cfg.kappa, cfg.dt, U, rho, 1, prec, inplace=True, work=work)
+            rho_h.copy_(rho, non_blocking=True)
+            obs_h.copy_(ob, non_blocking=True)
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        line["e2e"] = {"value": k / te, "unit": "steps/s", "h2d_bytes_per_step": 16 * lay.total,
+                       "d2h_bytes_per_step": 16 * lay.total + obs_h.numel() * 8,
+                       "api": "tc_lindblad_evolve (C ABI) with the packed state copied from and to pinned host memory"}
+    if not a.no_cpu:
+        v, cores, sample, _ = _cpu_sample(W.config_n14() if n == 14 else W.config_n12(), a.cpu_seconds)
+        scale = (1 << n) ** 3 / sum(d ** 3 for d in lay.dims)
+        line["cpu_baseline"] = {"value": v * scale, "unit": "steps/s", "cores": cores, "kind": "oracle",
+                                "sample": sample + "; scaled by N^3 / sum_k d_k^3 = %.3f to the block products "
+                                                   "(the damping pass is O(sum d_k^2))" % scale}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     a = _args()
     if a.workload == "batch":
         return run_batch(a)
+    if a.workload.startswith("open"):
+        return run_open(a)
     if a.workload == "grad":
         return run_grad(a)
     cfg = _workload(a.workload)

@@ -141,31 +141,39 @@ __global__ void layout_kernel(BlockSet bs, int* __restrict__ order, int* __restr
     }
 }
 
+template <typename A>
 struct DampTable {
-    double F[kMaxAtoms + 1][kMaxAtoms + 1];   // F[p][m]
+    A F[kMaxAtoms + 1][kMaxAtoms + 1];   // F[p][m]
 };
 
-DampTable damp_table(int n, double kappa, double tau) {
-    DampTable t{};
+// F[p][m] = sqrt(C(p + m, m) (1 - eta)^m) eta^{p/2}, evaluated in FP64 and
+// stored in the arithmetic type of the pass
+template <typename A>
+DampTable<A> damp_table(int n, double kappa, double tau) {
+    DampTable<A> t{};
     const double eta = std::exp(-kappa * tau);
     const double loss = -std::expm1(-kappa * tau);   // 1 - eta without cancellation
     for (int p = 0; p <= n; p++) {
         for (int m = 0; p + m <= n; m++) {
             double ratio = 1.0;   // (p + m)! / p! / m!  =  C(p + m, m)
             for (int q = 1; q <= m; q++) ratio = ratio * (double)(p + q) / (double)q;
-            t.F[p][m] = std::sqrt(ratio * std::pow(loss, (double)m)) * std::pow(eta, 0.5 * (double)p);
+            t.F[p][m] = (A)(std::sqrt(ratio * std::pow(loss, (double)m)) * std::pow(eta, 0.5 * (double)p));
         }
     }
     return t;
 }
 
 // D_tau on all blocks in place.  Block x = row i of every block; threads run
-// along j (coalesced in each block).  Element (i, j) is in blocks
-// k >= max(level(i), level(j)); the new block-k value needs the old values
-// of blocks >= k only, so ascending k can overwrite in place.  Arithmetic in
-// FP64; T = float stores FP32 and, with S > 0, rebuilds the operand parts.
+// along j (coalesced in each block; consecutive positions mostly share a
+// popcount, so the block range below is nearly warp-uniform).  Element (i, j)
+// is in blocks k >= max(level(i), level(j)); the new block-k value needs the
+// old values of blocks >= k only, so ascending k can overwrite in place.
+// The arithmetic is that of the storage: FP64 for the FP64 form; FP32 for
+// the FP32 planes of the tensor-core forms (about (n + 2) 2^-24 relative per
+// pass, the order of the FP32 store itself; FP64 arithmetic here would make
+// the pass FP64-issue-bound), which with S > 0 also rebuild the operand parts.
 template <typename T, int KIND, int S>
-__global__ void __launch_bounds__(256) damping_kernel(BlockSet bs, DampTable t, const int* __restrict__ order,
+__global__ void __launch_bounds__(256) damping_kernel(BlockSet bs, DampTable<T> t, const int* __restrict__ order,
                                                       T* __restrict__ re, T* __restrict__ im, PartsSet ps) {
     const int n = bs.n;
     const unsigned N = 1u << n;
@@ -174,38 +182,37 @@ __global__ void __launch_bounds__(256) damping_kernel(BlockSet bs, DampTable t, 
     for (unsigned j = blockIdx.y * blockDim.x + threadIdx.x; j < N; j += gridDim.y * blockDim.x) {
         const int lj = __popc((unsigned)order[j]);
         const int k0 = li > lj ? li : lj;
-        double vr[kMaxAtoms + 1], vi[kMaxAtoms + 1];
+        T vr[kMaxAtoms + 1], vi[kMaxAtoms + 1];
 #pragma unroll
         for (int k = 0; k <= kMaxAtoms; k++) {
-            vr[k] = 0.0;
-            vi[k] = 0.0;
+            vr[k] = 0;
+            vi[k] = 0;
             if (k >= k0 && k <= n) {
                 const size_t o = bs.off[k] + (size_t)i * bs.ld[k] + j;
-                vr[k] = (double)re[o];
-                vi[k] = (double)im[o];
+                vr[k] = re[o];
+                vi[k] = im[o];
             }
         }
 #pragma unroll
         for (int k = 0; k <= kMaxAtoms; k++) {
             if (k < k0 || k > n) continue;
             const int p = k - li, q = k - lj;
-            double ar = 0.0, ai = 0.0;
+            T ar = 0, ai = 0;
 #pragma unroll
             for (int m = 0; m + k <= kMaxAtoms; m++) {
                 if (k + m > n) break;
-                const double c = t.F[p][m] * t.F[q][m];
+                const T c = t.F[p][m] * t.F[q][m];
                 ar += c * vr[k + m];
                 ai += c * vi[k + m];
             }
             const size_t idx = (size_t)i * bs.ld[k] + j;
             const size_t o = bs.off[k] + idx;
-            const T wr = (T)ar, wi = (T)ai;
-            re[o] = wr;
-            im[o] = wi;
+            re[o] = ar;
+            im[o] = ai;
             if constexpr (S > 0) {
                 const size_t plane = (size_t)bs.ld[k] * bs.ld[k];
-                split_f32<KIND, S>((float)wr, ps.p[k], plane, idx, 0);
-                split_f32<KIND, S>((float)wi, ps.p[k], plane, idx, 1);
+                split_f32<KIND, S>((float)ar, ps.p[k], plane, idx, 0);
+                split_f32<KIND, S>((float)ai, ps.p[k], plane, idx, 1);
             }
         }
     }
@@ -356,7 +363,7 @@ template <typename T, int KIND, int S>
 tc_status launch_damping(const Layout& L, const BlockSet& bs, double kappa, double tau, const Tables& t, T* re, T* im,
                          const PartsSet& ps, cudaStream_t s) {
     dim3 grid((unsigned)L.N, (unsigned)((L.N + 255) / 256));
-    damping_kernel<T, KIND, S><<<grid, 256, 0, s>>>(bs, damp_table(L.n, kappa, tau), t.order, re, im, ps);
+    damping_kernel<T, KIND, S><<<grid, 256, 0, s>>>(bs, damp_table<T>(L.n, kappa, tau), t.order, re, im, ps);
     TC_LAUNCH_CHECK();
     return TC_OK;
 }

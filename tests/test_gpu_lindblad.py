@@ -191,14 +191,17 @@ def test_invariants_n10(tc):
 ACC = {"bf16x3": (6, 16), "tf32x3": (3, 8), "tf32": (1, 8)}   # part products, K per MMA
 
 
-def lowp_step_bound(precision, K, vnorm, scale, damped):
-    """One split step of a tensor-core form (the closed-form bound of the
-    increment-form products, plus two FP32 stores per damping pass):
-    2^-24 (4 + 2 n_acc 2 ||V||) max|rho| for the two products, TF32 adding
-    4 2^-11 ||V|| max|rho| for its one-part operands."""
+def lowp_step_bound(precision, K, vnorm, scale, n_damped):
+    """One split step of a tensor-core form: the closed-form bound of the
+    increment-form products, 2^-24 (4 + 2 n_acc 2 ||V||) max|rho| (TF32
+    adding 4 2^-11 ||V|| max|rho| for its one-part operands), plus, for each
+    of the two damping passes in FP32, (n + 1) rounded multiply-adds and one
+    store per entry: 2 (n + 2) 2^-24 max|rho| (the channel's weights of one
+    output sum to at most 1 / eta ~ 1, by Cauchy-Schwarz and the negative
+    binomial series)."""
     prod, kstep = ACC[precision]
     n_acc = prod * K / kstep
-    stores = 4.0 + (4.0 if damped else 0.0)
+    stores = 4.0 + (2.0 * (n_damped + 2) if n_damped else 0.0)
     b = 2.0 ** -24 * (stores + 2.0 * n_acc * 2.0 * vnorm) * scale
     if precision == "tf32":
         b += 4.0 * 2.0 ** -11 * vnorm * scale
@@ -227,7 +230,7 @@ def test_lowp_matches_oracle_n6(tc, L, precision):
     ref, rows = L.propagate(n, g, 1.002, 1.0, kappa, dt, steps, rho0)
     got = _unpack(L, lay, out.cpu().numpy())
     scale = np.max(np.abs(rho0))
-    tol = steps * lowp_step_bound(precision, 128, vnorm, scale, True)
+    tol = steps * lowp_step_bound(precision, 128, vnorm, scale, n)
     err = np.max(np.abs(got - ref))
     assert err < tol, (err, tol)
     D = got.shape[0]
@@ -252,7 +255,7 @@ def test_lowp_matches_fp64_path_n8(tc, L, precision):
     top[j, j] = 1.0
     ref, obs_ref = tc.lindblad_evolve(p, kappa, dt, U, rho, steps, "fp64")
     out, obs = tc.lindblad_evolve(p, kappa, dt, U, rho, steps, precision)
-    tol = steps * lowp_step_bound(precision, 256, vnorm, 1.0, True)
+    tol = steps * lowp_step_bound(precision, 256, vnorm, 1.0, n)
     err = torch.max(torch.abs(out - ref)).item()
     assert err < tol, (err, tol)
     pops = torch.max(torch.abs(obs[:, :n] - obs_ref[:, :n])).item()

@@ -34,6 +34,7 @@ class TCConfig:
     ckpt_every: int = 0
     loss_atom: int = 0
     description: str = ""
+    kappa: float = 0.0     # photon leakage rate of the open-system form (0: closed)
 
     @property
     def N(self) -> int:
@@ -69,6 +70,14 @@ def config_n15() -> TCConfig:
     return TCConfig("n15_precision", 15, draw_couplings(15, 0), 1.002, 1.0, 0.05, 500,
                     renorm_every=50,
                     description="n=15, dim 32768, g~U[0.005,0.015] seed 0, detuning 0.002, dt=0.05, renorm every 50")
+
+
+def config_open(n: int = 14, kappa: float = 0.02) -> TCConfig:
+    """Open system (photon leakage at rate kappa): g seed 0, detuning 0.002, dt = 0.05, renorm every 50."""
+    return TCConfig("open%d" % n, n, draw_couplings(n, 0), 1.002, 1.0, 0.05, 500, renorm_every=50,
+                    description="open system n=%d (excitation blocks k=0..%d), g~U[0.005,0.015] seed 0, "
+                                "detuning 0.002, kappa=%g, dt=0.05, renorm every 50" % (n, n, kappa),
+                    kappa=kappa)
 
 
 def config_n11_grad() -> TCConfig:
