@@ -354,26 +354,6 @@ def run_ours(a, cfg):
         "error": r["drift"],
     }
 
-    if not a.no_compare:
-        # the other forms on the same workload: split-TF32, TF32 and one FP64 step
-        others = {}
-        for p2, k2, w2 in (("tf32x3", a.steps, a.warmup), ("tf32", a.steps, a.warmup), ("fp64", 1, 0)):
-            if p2 == prec:
-                continue
-            if p2 == "fp64" and n >= 15:
-                others["fp64"] = {"omitted": "one FP64 step takes about %.0f s at n=%d" % (credited / 1.1e12, n)}
-                continue
-            r2 = _time_form(tc, torch, U, n, params, p2, k2, w2, renorm if p2 != "fp64" else 0, stream)
-            v2 = k2 / (r2["ms"] * 1e-3)
-            pk, _ = peak_of(p2, fp64_peak)
-            ach = r2["kflops"] / (r2["kms"] * 1e-3) / 1e12 if r2["kms"] > 0 else 0.0
-            others[p2] = {"value": v2, "unit": "steps/s", "steps": k2, "warmup": w2,
-                          "credited_tflops": credited * v2 / 1e12, "achieved_tflops": ach, "peak": pk,
-                          "frac": ach / pk if pk else None, "error": r2["drift"]}
-        line["other_forms"] = others
-        if "value" in others.get("fp64", {}):
-            line["speedup_vs_fp64"] = (value / world) / others["fp64"]["value"]
-
     if not a.no_e2e:
         # end to end through the public C ABI call with host buffers: every step copies
         # rho (pinned host) in, runs one step, copies rho and the observable rows back.
@@ -394,6 +374,26 @@ def run_ours(a, cfg):
                        "d2h_bytes_per_step": 16 * N * N + 2 * (2 * n + 5) * 8,
                        "api": "tc_evolve_host (C ABI, pinned host rho, one step per call)"}
         del rho_h, hw
+
+    if not a.no_compare:
+        # the other forms on the same workload: split-TF32, TF32 and one FP64 step
+        others = {}
+        for p2, k2, w2 in (("tf32x3", a.steps, a.warmup), ("tf32", a.steps, a.warmup), ("fp64", 1, 0)):
+            if p2 == prec:
+                continue
+            if p2 == "fp64" and n >= 15:
+                others["fp64"] = {"omitted": "one FP64 step takes about %.0f s at n=%d" % (credited / 1.1e12, n)}
+                continue
+            r2 = _time_form(tc, torch, U, n, params, p2, k2, w2, renorm if p2 != "fp64" else 0, stream)
+            v2 = k2 / (r2["ms"] * 1e-3)
+            pk, _ = peak_of(p2, fp64_peak)
+            ach = r2["kflops"] / (r2["kms"] * 1e-3) / 1e12 if r2["kms"] > 0 else 0.0
+            others[p2] = {"value": v2, "unit": "steps/s", "steps": k2, "warmup": w2,
+                          "credited_tflops": credited * v2 / 1e12, "achieved_tflops": ach, "peak": pk,
+                          "frac": ach / pk if pk else None, "error": r2["drift"]}
+        line["other_forms"] = others
+        if "value" in others.get("fp64", {}):
+            line["speedup_vs_fp64"] = (value / world) / others["fp64"]["value"]
 
     if rank == 0 and not a.no_cpu:
         v, cores, sample, _ = _cpu_sample(cfg, a.cpu_seconds)

@@ -95,3 +95,17 @@ def test_short_workspace_is_an_error(tc):
                                    ctypes.c_void_p(w.data_ptr()), 1024, None)
     assert st == 3
     assert "need" in _abi.last_error()
+
+
+def test_n15_rows_are_unitary(tc):
+    """n = 15 (dim 32768, the paper's largest): a sample of rows of U U^dag is the
+    identity to 1e-13, and U is symmetric on the sampled block."""
+    cfg = W.config_n15()
+    p = _params(tc, cfg.n, cfg.g, cfg.omega_a, cfg.omega_c)
+    U = tc.expm_model(p, cfg.dt)
+    rows = torch.arange(0, 1 << cfg.n, 4093, device="cuda")
+    G = U[rows] @ U[rows].conj().T
+    assert torch.max(torch.abs(G - torch.eye(len(rows), dtype=G.dtype, device="cuda"))).item() < 1e-13
+    assert torch.equal(U[rows][:, rows], U[rows][:, rows].T)
+    del U, G
+    torch.cuda.empty_cache()
