@@ -173,7 +173,7 @@ DampTable<A> damp_table(int n, double kappa, double tau) {
 // pass, the order of the FP32 store itself; FP64 arithmetic here would make
 // the pass FP64-issue-bound), which with S > 0 also rebuild the operand parts.
 template <typename T, int KIND, int S>
-__global__ void __launch_bounds__(256) damping_kernel(BlockSet bs, DampTable<T> t, const int* __restrict__ order,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) damping_kernel(BlockSet bs, DampTable<T> t, const int* __restrict__ order,
                                                       T* __restrict__ re, T* __restrict__ im, PartsSet ps) {
     const int n = bs.n;
     const unsigned N = 1u << n;
@@ -295,10 +295,24 @@ __global__ void obs_partial_kernel(BlockSet bs, Model m, int has_model, const in
         }
         const unsigned d = (unsigned)bs.d[k];
         const size_t row = bs.off[k] + (size_t)i * bs.ld[k];
-        for (unsigned c = lane; c < d; c += 32) {
-            const double x = (double)re[row + c], y = (double)im[row + c];
-            pur += x * x + y * y;
+        // four independent loads per lane in flight, fixed summation order
+        double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
+        unsigned c = lane;
+        for (; c + 96 < d; c += 128) {
+            const double x0 = (double)re[row + c], x1 = (double)re[row + c + 32], x2 = (double)re[row + c + 64],
+                         x3 = (double)re[row + c + 96];
+            const double y0 = (double)im[row + c], y1 = (double)im[row + c + 32], y2 = (double)im[row + c + 64],
+                         y3 = (double)im[row + c + 96];
+            p0 += x0 * x0 + y0 * y0;
+            p1 += x1 * x1 + y1 * y1;
+            p2 += x2 * x2 + y2 * y2;
+            p3 += x3 * x3 + y3 * y3;
         }
+        for (; c < d; c += 32) {
+            const double x = (double)re[row + c], y = (double)im[row + c];
+            p0 += x * x + y * y;
+        }
+        pur += (p0 + p1) + (p2 + p3);
         const unsigned s = (unsigned)order[i];
         if (has_model && lane < n) {
             const unsigned c = (unsigned)pos[s ^ (1u << lane)];

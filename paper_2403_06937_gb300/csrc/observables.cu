@@ -55,10 +55,24 @@ __global__ void obs_partial_kernel(Rho<L> rho, Model m, int has_model, int n, do
     double pur = 0.0, epair = 0.0;
     for (unsigned r = blockIdx.x * kObsWarps + warp; r < N; r += gridDim.x * kObsWarps) {
         const size_t row = (size_t)r * rho.ld;
-        for (unsigned c = lane; c < N; c += 32) {
-            double x = rho.re(row + c), y = rho.im(row + c);
-            pur += x * x + y * y;
+        // four independent loads per lane in flight, fixed summation order
+        double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
+        unsigned c = lane;
+        for (; c + 96 < N; c += 128) {
+            const double x0 = rho.re(row + c), x1 = rho.re(row + c + 32), x2 = rho.re(row + c + 64),
+                         x3 = rho.re(row + c + 96);
+            const double y0 = rho.im(row + c), y1 = rho.im(row + c + 32), y2 = rho.im(row + c + 64),
+                         y3 = rho.im(row + c + 96);
+            p0 += x0 * x0 + y0 * y0;
+            p1 += x1 * x1 + y1 * y1;
+            p2 += x2 * x2 + y2 * y2;
+            p3 += x3 * x3 + y3 * y3;
         }
+        for (; c < N; c += 32) {
+            const double x = rho.re(row + c), y = rho.im(row + c);
+            p0 += x * x + y * y;
+        }
+        pur += (p0 + p1) + (p2 + p3);
         // energy pair of atom `lane` when that atom is excited in r
         if (has_model && lane < n) {
             unsigned bit = 1u << (n - 1 - lane);
