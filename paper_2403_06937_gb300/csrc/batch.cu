@@ -23,6 +23,13 @@ size_t f64_system_bytes(int n) {
     return 3 * cm + observables_scratch_bytes(n) + 256;   // U, rho, X planar
 }
 
+// one split-K scratch shared by the systems' products (they run one after another)
+size_t f64_shared_bytes(const int* n, int count) {
+    for (int b = 0; b < count; b++)
+        if ((1 << n[b]) <= kSplitMaxDim) return gemm_f64_splitk_bytes();
+    return 0;
+}
+
 struct F64Sys {
     int n, N;
     double *Ur, *Ui, *Rr, *Ri, *Xr, *Xi, *scratch;
@@ -36,6 +43,7 @@ size_t batch_bytes(int count, const int* n, int precision) {
         if (n[b] < 1 || n[b] > kMaxAtoms) return 0;
         total += precision == TC_FP64 ? f64_system_bytes(n[b]) : lowp_system_bytes(n[b], precision) + 512;
     }
+    if (precision == TC_FP64) total += f64_shared_bytes(n, count);
     return total;
 }
 
@@ -86,6 +94,7 @@ TC_API tc_status tc_batch_evolve(int count, const int* n, const void* const* U, 
 
     std::vector<LowpBufs> lb(count);
     std::vector<F64Sys> fb(count);
+    double* f64_partial = nullptr;   // split-K scratch shared by the FP64 products
     std::vector<BatchSys> host(count);
     int tiles[2] = {0, 0};
     auto observe = [&](int k, int row) -> tc_status {
@@ -111,6 +120,7 @@ TC_API tc_status tc_batch_evolve(int count, const int* n, const void* const* U, 
                 g1.Br = f.Rr; g1.Bi = f.Ri; g1.ldb = f.N;
                 g1.Cr = f.Xr; g1.Ci = f.Xi; g1.ldc = f.N;
                 g1.alpha = 1.0; g1.cplx = 1;
+                g1.partial = f64_partial;
                 GemmF64 g2 = g1;
                 g2.Ar = f.Xr; g2.Ai = f.Xi;
                 g2.Br = f.Ur; g2.Bi = f.Ui; g2.conjB = 1;
@@ -148,6 +158,10 @@ TC_API tc_status tc_batch_evolve(int count, const int* n, const void* const* U, 
                 if (!f.scratch) return fail(TC_ERR_WORKSPACE, "batch: workspace too small");
                 TC_TRY(launch_split_c128(static_cast<const double*>(U[b]), f.Ur, f.Ui, NN, s));
                 TC_TRY(launch_split_c128(static_cast<const double*>(rho[b]), f.Rr, f.Ri, NN, s));
+            }
+            if (f64_shared_bytes(n, count)) {
+                f64_partial = ar.take<double>(f64_shared_bytes(n, count) / sizeof(double));
+                if (!f64_partial) return fail(TC_ERR_WORKSPACE, "batch: workspace too small");
             }
         } else {
             for (int k = 0; k < count; k++) {

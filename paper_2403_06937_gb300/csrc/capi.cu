@@ -92,7 +92,8 @@ size_t expm_bytes(int n) {
 }
 
 size_t evolve_f64_bytes(int n) {
-    return 6 * mat_bytes(n, 8) + observables_scratch_bytes(n) + 256;
+    return 6 * mat_bytes(n, 8) + observables_scratch_bytes(n) + 256 +
+           (((size_t)1 << n) <= (size_t)kSplitMaxDim ? gemm_f64_splitk_bytes() : 0);
 }
 
 size_t evolve_bytes(int n, int precision) {

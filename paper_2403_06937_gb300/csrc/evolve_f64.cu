@@ -21,7 +21,8 @@ tc_status evolve_f64(const double* U, double* rho, int n, int steps, int renorm_
     double* Xr = ar.take<double>(NN);
     double* Xi = ar.take<double>(NN);
     double* scratch = ar.take<double>(observables_scratch_bytes(n) / sizeof(double));
-    if (!scratch) return fail(TC_ERR_WORKSPACE, "evolve: workspace too small");
+    double* partial = N <= kSplitMaxDim ? ar.take<double>(gemm_f64_splitk_bytes() / sizeof(double)) : nullptr;
+    if (!scratch || (N <= kSplitMaxDim && !partial)) return fail(TC_ERR_WORKSPACE, "evolve: workspace too small");
     const int stride = TC_OBS_STRIDE(n);
 
     GemmF64 g1{};
@@ -31,6 +32,7 @@ tc_status evolve_f64(const double* U, double* rho, int n, int steps, int renorm_
     g1.Cr = Xr; g1.Ci = Xi; g1.ldc = N;
     g1.alpha = 1.0; g1.beta = 0.0;
     g1.cplx = 1;
+    g1.partial = partial;
     GemmF64 g2 = g1;
     g2.Ar = Xr; g2.Ai = Xi;
     g2.Br = Ur; g2.Bi = Ui; g2.conjB = 1;

@@ -10,6 +10,8 @@
 // the design goal is only that every warp always has independent DMMA
 // instructions to issue.  Complex products use four real m16n8k8 DMMAs per
 // fragment on planar (re, im) operands.
+#include <algorithm>
+
 #include "kernels.cuh"
 
 namespace tc {
@@ -36,8 +38,14 @@ __device__ __forceinline__ void lower_tile(int b, int& bi, int& bj) {
     bj = b - i * (i + 1) / 2;
 }
 
+constexpr int kMaxSplit = 8;
+
+// Split-K: CTA (x, y, z) covers K range [z kc, (z + 1) kc) and, when
+// `partial` is set, stores its raw complex accumulator (no alpha, beta or
+// mirror) to partial[z][row][col] (re planes, then im planes at offset
+// kMaxSplit M N).
 template <bool CPLX, int BT>
-__global__ void __launch_bounds__(kThreads, 1) gemm_f64_kernel(GemmF64 p) {
+__global__ void __launch_bounds__(kThreads, 1) gemm_f64_kernel(GemmF64 p, int kc) {
     constexpr int BM = BT, BN = BT;
     constexpr int LDB_S = BN + 4;
     constexpr int MI = BT / 32, NI = BT / 16;   // m16 / n8 fragments per warp
@@ -69,14 +77,16 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_f64_kernel(GemmF64 p) {
     const double sa = p.conjA ? -1.0 : 1.0;
     const double sb = p.conjB ? -1.0 : 1.0;
 
-    for (int k0 = 0; k0 < p.K; k0 += BK) {
+    const int kbeg = blockIdx.z * kc;
+    const int kend = min(p.K, kbeg + kc);
+    for (int k0 = kbeg; k0 < kend; k0 += BK) {
         // stage A (BM x BK) and B (BK x BN), zero-filled outside the matrix
 #pragma unroll
         for (int r = 0; r < (BM * BK) / kThreads; r++) {
             int e = tid + r * kThreads;
             int row = e / BK, col = e % BK;
             int gm = m0 + row, gk = k0 + col;
-            bool ok = gm < p.M && gk < p.K;
+            bool ok = gm < p.M && gk < kend;
             long off = (long)gm * p.lda + gk;
             sAr[row * LDA_S + col] = ok ? p.Ar[off] : 0.0;
             if (CPLX) sAi[row * LDA_S + col] = ok ? sa * p.Ai[off] : 0.0;
@@ -86,7 +96,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_f64_kernel(GemmF64 p) {
             int e = tid + r * kThreads;
             int row = e / BN, col = e % BN;
             int gk = k0 + row, gn = n0 + col;
-            bool ok = gk < p.K && gn < p.N;
+            bool ok = gk < kend && gn < p.N;
             long off = (long)gk * p.ldb + gn;
             sBr[row * LDB_S + col] = ok ? p.Br[off] : 0.0;
             if (CPLX) sBi[row * LDB_S + col] = ok ? sb * p.Bi[off] : 0.0;
@@ -148,6 +158,13 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_f64_kernel(GemmF64 p) {
                 int row = m0 + wm + mi * 16 + gq + ((q >> 1) << 3);
                 int col = n0 + wn + ni * 8 + 2 * tq + (q & 1);
                 if (row >= p.M || col >= p.N) continue;
+                if (p.partial) {
+                    const size_t MN = (size_t)p.M * p.N;
+                    const size_t o = (size_t)blockIdx.z * MN + (size_t)row * p.N + col;
+                    p.partial[o] = accr[mi][ni][q];
+                    if (CPLX) p.partial[(size_t)kMaxSplit * MN + o] = acci[mi][ni][q];
+                    continue;
+                }
                 double vr = p.alpha * accr[mi][ni][q];
                 double vi = CPLX ? p.alpha * acci[mi][ni][q] : 0.0;
                 long off = (long)row * p.ldc + col;
@@ -174,27 +191,102 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_f64_kernel(GemmF64 p) {
             }
 }
 
+// Sum of the split-K partials in chunk order, then C = alpha sum + beta C,
+// or the Hermitian lower triangle and its mirror.
+template <bool CPLX>
+__global__ void splitk_reduce_kernel(GemmF64 p, int splits) {
+    const size_t MN = (size_t)p.M * p.N;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < MN; e += (size_t)gridDim.x * blockDim.x) {
+        const int row = (int)(e / p.N), col = (int)(e % p.N);
+        if (p.herm_lower && row < col) continue;   // the upper half is written as the mirror
+        double sr = 0.0, si = 0.0;
+        for (int z = 0; z < splits; z++) {
+            sr += p.partial[(size_t)z * MN + e];
+            if (CPLX) si += p.partial[(size_t)(kMaxSplit + z) * MN + e];
+        }
+        double vr = p.alpha * sr;
+        double vi = CPLX ? p.alpha * si : 0.0;
+        const long off = (long)row * p.ldc + col;
+        if (p.beta != 0.0) {
+            vr += p.beta * p.Cr[off];
+            if (CPLX) vi += p.beta * p.Ci[off];
+        }
+        if (!p.herm_lower) {
+            p.Cr[off] = vr;
+            if (CPLX) p.Ci[off] = vi;
+        } else if (row == col) {
+            p.Cr[off] = vr;
+            if (CPLX) p.Ci[off] = 0.0;
+        } else {
+            const long mir = (long)col * p.ldc + row;
+            p.Cr[off] = vr;
+            p.Cr[mir] = vr;
+            if (CPLX) {
+                p.Ci[off] = vi;
+                p.Ci[mir] = -vi;
+            }
+        }
+    }
+}
+
+int sm_count() {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
+
 template <int BT>
 tc_status launch_bt(const GemmF64& g, cudaStream_t s) {
     dim3 block(kThreads);
     dim3 grid;
+    long tiles;
     if (g.herm_lower) {
         long t = (g.N + BT - 1) / BT;
-        grid = dim3((unsigned)(t * (t + 1) / 2));
+        tiles = t * (t + 1) / 2;
+        grid = dim3((unsigned)tiles);
     } else {
         grid = dim3((g.N + BT - 1) / BT, (g.M + BT - 1) / BT);
+        tiles = (long)grid.x * grid.y;
     }
+    // split K while the tiles leave SMs idle: about two CTAs per SM, chunks of
+    // at least four BK steps
+    int splits = 1, kc = g.K;
+    if (g.partial && g.M <= kSplitMaxDim && g.N <= kSplitMaxDim) {
+        const long want = (2L * sm_count() + tiles - 1) / tiles;
+        const int most = g.K / (4 * BK);
+        splits = (int)std::min<long>(std::min<long>(want, most), kMaxSplit);
+        if (splits < 1) splits = 1;
+        kc = ((g.K + splits - 1) / splits + BK - 1) / BK * BK;
+        splits = (g.K + kc - 1) / kc;
+    }
+    GemmF64 gk = g;
+    if (splits <= 1) gk.partial = nullptr;
+    grid.z = (unsigned)splits;
     if (g.cplx)
-        gemm_f64_kernel<true, BT><<<grid, block, 0, s>>>(g);
+        gemm_f64_kernel<true, BT><<<grid, block, 0, s>>>(gk, kc);
     else
-        gemm_f64_kernel<false, BT><<<grid, block, 0, s>>>(g);
+        gemm_f64_kernel<false, BT><<<grid, block, 0, s>>>(gk, kc);
     TC_LAUNCH_CHECK();
+    if (splits > 1) {
+        const size_t MN = (size_t)g.M * g.N;
+        const unsigned blocks = (unsigned)std::min<size_t>((MN + 255) / 256, (size_t)sm_count() * 8);
+        if (g.cplx)
+            splitk_reduce_kernel<true><<<blocks, 256, 0, s>>>(gk, splits);
+        else
+            splitk_reduce_kernel<false><<<blocks, 256, 0, s>>>(gk, splits);
+        TC_LAUNCH_CHECK();
+    }
     return TC_OK;
 }
 
 }  // namespace
 
 int gemm_f64_default_tile(int N) { return N >= 4096 ? 64 : 32; }
+
+size_t gemm_f64_splitk_bytes() {
+    return round256(2 * (size_t)kMaxSplit * kSplitMaxDim * kSplitMaxDim * sizeof(double));
+}
 
 tc_status gemm_f64(const GemmF64& g, cudaStream_t s) {
     if (g.M <= 0 || g.N <= 0 || g.K <= 0) return TC_OK;

@@ -32,9 +32,17 @@ struct GemmF64 {
     int cplx;
     int herm_lower;
     int tile;        // 32 or 64 (square CTA tile); 0 = the tuned or default choice for this size
+    // Split-K for products too small to fill the GPU: when `partial` is given
+    // (gemm_f64_splitk_bytes() bytes of scratch), M, N <= kSplitMaxDim and the
+    // tiles are fewer than the SMs, K is cut into chunks whose partial products
+    // go to `partial` and a second kernel sums them in chunk order
+    // (deterministic), applying alpha / beta and the Hermitian mirror.
+    double* partial;
 };
 tc_status gemm_f64(const GemmF64& g, cudaStream_t s);
 int gemm_f64_default_tile(int N);
+constexpr int kSplitMaxDim = 1024;
+size_t gemm_f64_splitk_bytes();
 
 // ---------------------------------------------------------------- tuning
 // Kernel configuration chosen by tc_autotune (or the default) per (N, precision).

@@ -421,7 +421,7 @@ size_t evolve_f64_bytes(int n) {
     const size_t total = L.off[n + 1];
     const size_t NN = (size_t)L.N * L.N;
     return tables_bytes(n) + 4 * round256(total * sizeof(double)) + 2 * round256(NN * sizeof(double)) +
-           obs_scratch_bytes(L) + 256;
+           obs_scratch_bytes(L) + gemm_f64_splitk_bytes() + 256;
 }
 
 tc_status evolve_f64(const Layout& L, const Model& m, double kappa, double dt, const double* U, double* rho,
@@ -438,7 +438,8 @@ tc_status evolve_f64(const Layout& L, const Model& m, double kappa, double dt, c
     double* Xr = ar.take<double>(NN);
     double* Xi = ar.take<double>(NN);
     double* scratch = ar.take<double>(obs_scratch_bytes(L) / sizeof(double));
-    if (!scratch) return fail(TC_ERR_WORKSPACE, "lindblad evolve: workspace too small");
+    double* partial = ar.take<double>(gemm_f64_splitk_bytes() / sizeof(double));
+    if (!partial) return fail(TC_ERR_WORKSPACE, "lindblad evolve: workspace too small");
     const int stride = TC_OBS_STRIDE(n);
     const bool damp = kappa > 0.0;
     const BlockSet bs = block_set(L);
@@ -455,6 +456,7 @@ tc_status evolve_f64(const Layout& L, const Model& m, double kappa, double dt, c
             g1.Cr = Xr; g1.Ci = Xi; g1.ldc = d;
             g1.alpha = 1.0;
             g1.cplx = 1;
+            g1.partial = partial;   // used by the blocks of dimension <= 1024
             GemmF64 g2 = g1;
             g2.Ar = Xr; g2.Ai = Xi;
             g2.Br = Ur + o; g2.Bi = Ui + o; g2.conjB = 1;
