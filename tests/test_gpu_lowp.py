@@ -164,7 +164,7 @@ def test_n14_workload_sampled_bf16x3(tc, oracle):
     cfg = W.config_n14()
     steps = 3
     p = tc.Params(cfg.n, list(cfg.g), cfg.omega_a, cfg.omega_c)
-    U = tc.expm(tc.build_hamiltonian(p), cfg.n, cfg.dt)
+    U = tc.expm_model(p, cfg.dt)   # as the benchmark builds it
     rho0 = torch.zeros((cfg.N, cfg.N), dtype=torch.complex128, device="cuda")
     rho0[-1, -1] = 1.0
     rho, obs = tc.evolve(U, rho0, cfg.n, steps, "bf16x3", renorm_every=cfg.renorm_every, params=p)
@@ -183,3 +183,68 @@ def test_n14_workload_sampled_bf16x3(tc, oracle):
     ii, jj = ii.cpu().numpy(), jj.cpu().numpy()
     want = psi[ii] * psi[jj].conj()
     assert np.max(np.abs(got - want)) < 1e-5
+
+
+def _jc_excited(t, g, delta):
+    """One atom of the qubit-photon reading from |e, 0>: the Rabi formula."""
+    om2 = 4 * g * g + delta * delta
+    return 1.0 - (4 * g * g / om2) * np.sin(np.sqrt(om2) * t / 2.0) ** 2
+
+
+@pytest.mark.parametrize("n,precision,steps,tol", [(10, "fp64", 100, 1e-10), (14, "bf16x3", 100, 1e-5)])
+def test_qubit_photon_closed_form(tc, n, precision, steps, tol):
+    """Qubit-photon coupling: H = const + sum_i (Delta l_i + g_i sigma^x_i) factorises, so from the
+    all-excited state every P_i(t) is the Rabi formula with its own g_i and P(m) is the
+    Poisson-binomial distribution of the 1 - P_i.  An analytic pin of the whole dense path
+    (H, U, the step loop, the observables) at the benchmark's size."""
+    g = W.draw_couplings(n, 3) * 20
+    wa, wc, dt = 1.002, 1.0, 0.05
+    p = tc.Params(n, list(map(float, g)), wa, wc, 1)
+    U = tc.expm_model(p, dt)
+    N = 1 << n
+    rho0 = torch.zeros((N, N), dtype=torch.complex128, device="cuda")
+    rho0[-1, -1] = 1.0
+    _, obs = tc.evolve(U, rho0, n, steps, precision, renorm_every=50 if precision != "fp64" else 0, params=p)
+    o = obs.cpu().numpy()
+    t = np.arange(steps + 1) * dt
+    P = np.stack([_jc_excited(t, gi, wa - wc) for gi in g], axis=1)
+    assert np.max(np.abs(o[:, :n] - P)) < tol
+    # P(m): the probability of m photons = m atoms relaxed, Poisson-binomial
+    for r in (steps // 2, steps):
+        dist = np.array([1.0])
+        for q in 1.0 - P[r]:
+            dist = np.convolve(dist, [1.0 - q, q])
+        assert np.max(np.abs(o[r, n + 1:2 * n + 2] - dist)) < tol
+
+
+def test_zero_steps_round_trip_is_one_fp32_rounding(tc):
+    """The split forms store rho in FP32 planes: in and out again is one rounding, 2^-24 relative."""
+    n = 6
+    p = tc.Params(n, list(map(float, W.draw_couplings(n, 2))), 1.0, 1.0)
+    U = tc.expm_model(p, 0.1)
+    rho0, _, _ = W.random_mixed_state(n, 3, 4)
+    r0 = torch.from_numpy(rho0).cuda()
+    for precision in ("bf16x3", "tf32x3", "tf32"):
+        rho, _ = tc.evolve(U, r0, n, 0, precision, params=p)
+        d = (rho - r0).cpu().numpy()
+        a = np.abs(rho0)
+        assert np.all(np.abs(d.real) <= 2.0 ** -24 * np.abs(rho0.real))
+        assert np.all(np.abs(d.imag) <= 2.0 ** -24 * np.abs(rho0.imag))
+        assert a.max() > 0
+
+
+@pytest.mark.slow
+def test_n14_500_steps_populations_bf16x3(tc, oracle):
+    """The n = 14 workload over all 500 steps (renormalised every 50) against the oracle's
+    pure-state propagation: populations, <p> and P(m) within the stated 1e-5 target."""
+    cfg = W.config_n14()
+    n = cfg.n
+    p = tc.Params(n, list(map(float, cfg.g)), cfg.omega_a, cfg.omega_c)
+    U = tc.expm_model(p, cfg.dt)
+    rho0 = torch.zeros((cfg.N, cfg.N), dtype=torch.complex128, device="cuda")
+    rho0[-1, -1] = 1.0
+    _, obs = tc.evolve(U, rho0, n, cfg.steps, "bf16x3", renorm_every=cfg.renorm_every, params=p)
+    tc.sync_status()
+    _, oobs = oracle.propagate(n, cfg.g, cfg.omega_a, cfg.omega_c, cfg.dt, cfg.steps, W.all_excited_state(n))
+    o = obs.cpu().numpy()
+    assert np.max(np.abs(o[:, :2 * n + 2] - oobs[:, :2 * n + 2])) < 1e-5
