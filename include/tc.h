@@ -69,13 +69,22 @@ typedef enum tc_status {
  *              accumulated in FP32 in tensor memory (tcgen05 kind::f16).
  *  TC_TF32   : one TF32 product, FP32 accumulate (tcgen05 kind::tf32).
  *  TC_TF32X3 : big/small TF32 split, three products (kind::tf32).
- * In all low-precision forms U is computed in FP64 and rho is stored in FP32
+ *  TC_FP64_OZAKI : FP64-accurate products on the BF16 tensor cores: every
+ *              operand row scaled by a power of two and written as nine
+ *              balanced base-64 integer digits (exact in BF16); the 45 digit
+ *              products with t + u <= 8 accumulate exactly in FP32 (sums
+ *              stay below 2^24 for K <= 16384) and are scaled and summed in
+ *              FP64.  About 2^-48 of the row and column scales per product;
+ *              rho stored in FP64.  Single systems only (tc_evolve,
+ *              tc_evolve_host).
+ * In the BF16/TF32 forms U is computed in FP64 and rho is stored in FP32
  * between steps. */
 typedef enum tc_precision {
     TC_FP64 = 0,
     TC_BF16X3 = 1,
     TC_TF32 = 2,
-    TC_TF32X3 = 3
+    TC_TF32X3 = 3,
+    TC_FP64_OZAKI = 4
 } tc_precision;
 
 /* Coupling matrix element between s_e (atom i excited, p photons) and s_g

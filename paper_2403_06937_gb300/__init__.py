@@ -22,7 +22,8 @@ from . import _abi
 from ._abi import (TC_BF16X3, TC_COUPLING_BOSONIC, TC_COUPLING_QUBIT_PHOTON, TC_FP64, TC_OP_BACKWARD,
                    TC_OP_EVOLVE, TC_OP_EXPM, TC_OP_OBSERVABLES, TC_TF32, TC_TF32X3, TCError)
 
-PRECISIONS = {"fp64": TC_FP64, "bf16x3": TC_BF16X3, "tf32": TC_TF32, "tf32x3": TC_TF32X3}
+PRECISIONS = {"fp64": TC_FP64, "bf16x3": TC_BF16X3, "tf32": TC_TF32, "tf32x3": TC_TF32X3,
+              "ozaki": _abi.TC_FP64_OZAKI}
 
 
 @dataclass

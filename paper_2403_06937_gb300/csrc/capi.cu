@@ -97,6 +97,7 @@ size_t evolve_f64_bytes(int n) {
 }
 
 size_t evolve_bytes(int n, int precision) {
+    if (precision == TC_FP64_OZAKI) return evolve_oz_bytes(n);
     return precision == TC_FP64 ? evolve_f64_bytes(n) : evolve_lowp_bytes(n, precision);
 }
 
@@ -350,10 +351,7 @@ TC_API size_t tc_workspace_size(int n, int precision, int ops, int steps, int ck
     size_t need = 0;
     auto upd = [&](size_t b) { if (b > need) need = b; };
     if (ops & TC_OP_EXPM) upd(expm_bytes(n));
-    if (ops & TC_OP_EVOLVE) {
-        if (precision == TC_FP64) upd(evolve_f64_bytes(n));
-        else upd(evolve_lowp_bytes(n, precision));
-    }
+    if (ops & TC_OP_EVOLVE) upd(evolve_bytes(n, precision));
     if (ops & TC_OP_OBSERVABLES) upd(observables_scratch_bytes(n));
     if (ops & TC_OP_EXPM_MODEL) upd(expm_model_bytes(n));
     if (ops & TC_OP_LINDBLAD) upd(lindblad_bytes(n, precision));
@@ -413,7 +411,8 @@ TC_API tc_status tc_evolve(const void* U, void* rho, int n, int steps, int preci
     if (obs && (reinterpret_cast<uintptr_t>(obs) & 7u)) return fail(TC_ERR_INVALID_ARG, "obs must be 8-byte aligned");
     if (steps < 0) return fail(TC_ERR_INVALID_ARG, "steps < 0");
     if (renorm_every < 0) return fail(TC_ERR_INVALID_ARG, "renorm_every < 0");
-    if (precision < TC_FP64 || precision > TC_TF32X3) return fail(TC_ERR_INVALID_ARG, "unknown precision %d", precision);
+    if (precision < TC_FP64 || precision > TC_FP64_OZAKI)
+        return fail(TC_ERR_INVALID_ARG, "unknown precision %d", precision);
     Model m;
     const Model* mp = nullptr;
     if (params) {
@@ -421,11 +420,13 @@ TC_API tc_status tc_evolve(const void* U, void* rho, int n, int steps, int preci
         if (m.n != n) return fail(TC_ERR_INVALID_ARG, "params->n != n");
         mp = &m;
     }
-    size_t need = precision == TC_FP64 ? evolve_f64_bytes(n) : evolve_lowp_bytes(n, precision);
-    TC_TRY(check_work(work, work_bytes, need));
+    TC_TRY(check_work(work, work_bytes, evolve_bytes(n, precision)));
     TC_TRY(check_device());
     cudaStream_t s = as_stream(stream);
     Arena ar{static_cast<char*>(work), work_bytes, 0};
+    if (precision == TC_FP64_OZAKI)
+        return evolve_oz(static_cast<const double*>(U), static_cast<double*>(rho), n, steps, renorm_every, mp, obs,
+                         ar, s);
     if (precision != TC_FP64)
         return evolve_lowp(static_cast<const double*>(U), static_cast<double*>(rho), n, steps, precision,
                            renorm_every, mp, obs, ar, s);
@@ -440,7 +441,8 @@ TC_API tc_status tc_evolve_host(const void* U, void* rho_host, int n, int steps,
     if (!U || !rho_host) return fail(TC_ERR_INVALID_ARG, "U or rho_host is NULL");
     if (reinterpret_cast<uintptr_t>(U) & 15u) return fail(TC_ERR_INVALID_ARG, "U must be 16-byte aligned");
     if (steps < 0 || renorm_every < 0) return fail(TC_ERR_INVALID_ARG, "steps / renorm_every < 0");
-    if (precision < TC_FP64 || precision > TC_TF32X3) return fail(TC_ERR_INVALID_ARG, "unknown precision %d", precision);
+    if (precision < TC_FP64 || precision > TC_FP64_OZAKI)
+        return fail(TC_ERR_INVALID_ARG, "unknown precision %d", precision);
     Model m;
     const Model* mp = nullptr;
     if (params) {
@@ -456,11 +458,12 @@ TC_API tc_status tc_evolve_host(const void* U, void* rho_host, int n, int steps,
     double* rho_dev = ar.take<double>(2 * N * N);
     double* obs_dev = ar.take<double>((size_t)(steps + 1) * (2 * n + 5));
     TC_CUDA(cudaMemcpyAsync(rho_dev, rho_host, 16 * N * N, cudaMemcpyHostToDevice, s));
-    tc_status st = precision == TC_FP64
-                       ? evolve_f64(static_cast<const double*>(U), rho_dev, n, steps, renorm_every, mp,
-                                    obs_host ? obs_dev : nullptr, ar, s)
-                       : evolve_lowp(static_cast<const double*>(U), rho_dev, n, steps, precision, renorm_every,
-                                     mp, obs_host ? obs_dev : nullptr, ar, s);
+    double* od = obs_host ? obs_dev : nullptr;
+    const double* Ud = static_cast<const double*>(U);
+    tc_status st = precision == TC_FP64         ? evolve_f64(Ud, rho_dev, n, steps, renorm_every, mp, od, ar, s)
+                   : precision == TC_FP64_OZAKI ? evolve_oz(Ud, rho_dev, n, steps, renorm_every, mp, od, ar, s)
+                                                : evolve_lowp(Ud, rho_dev, n, steps, precision, renorm_every, mp,
+                                                              od, ar, s);
     if (st != TC_OK) return st;
     TC_CUDA(cudaMemcpyAsync(rho_host, rho_dev, 16 * N * N, cudaMemcpyDeviceToHost, s));
     if (obs_host)

@@ -1,0 +1,383 @@
+// cgemm_oz.cu -- FP64-accurate complex GEMM Y = U P^H on the BF16 tensor
+// cores by exact integer slices (the Ozaki splitting), for the step
+// rho <- U rho U^dag (Sec. III.A, Eqs. 6, 12) at FP64 accuracy.
+//
+// Slicing.  Every row r of an operand (both planes together) gets an
+// exponent e_r with max |x| < 2^(e_r - 1); then x 2^(54 - e_r) is rounded to
+// a 54-bit integer and written in balanced base-64 digits,
+//     x = 2^e_r sum_{t=0..8} d_t 2^(-6(t+1)),   d_t integers, |d_t| <= 32,
+// each digit stored as an exact BF16 value (slice t).
+//
+// Products.  For slices t of U and u of P, sum_k d_t(U) d_u(P) is a sum of
+// integers of size <= 32^2 = 2^10; over K <= 16384 terms it stays within
+// 2^24, so the FP32 accumulation of the tensor cores is exact (no rounding,
+// hence no truncation).  One pass of the K loop per slice pair (t, u) with
+// t + u <= 8 (45 pairs; the first dropped level is ~2^-48 of the row and
+// column scales) accumulates that pair in TMEM; the epilogue then adds the
+// exact integer result times 2^(e_i + f_j - 6(t + u + 2)) into FP64 planes
+// of Y.  K above 16384 is cut into chunks of 16384, one pass each.
+//
+// Tile and roles as the split-BF16 kernel (cgemm_tc.cu): one CTA per 128 x 128
+// complex tile, A = slice t of U_r and U_i (M = 128), B = slice u of
+// [P_r; P_i] (N = 256), two FP32 accumulators (512 TMEM columns); a stage is
+// one K step of one pair (16 KB), 12 stages.  Warp 4 issues TMA, warp 5 the
+// MMAs, warps 0-3 the epilogue; the MMA issuer starts a pass only after the
+// epilogue has read the previous one out of TMEM.  Every wait is bounded.
+//   mode 0: all tiles (X = U rho).
+//   mode 1: block-lower tiles (rho' = U X^H); oz_mirror fills the upper half.
+#include <cuda_bf16.h>
+
+#include "cgemm_dev.cuh"
+#include "cgemm_oz.cuh"
+
+namespace tc {
+namespace {
+
+using namespace sm100;
+using namespace cg;
+
+constexpr int kThreads = 192;
+constexpr int kStages = 12;
+constexpr int kStage = 2 * kATile + kBTile;   // 16 KB
+constexpr int kKPerStage = kRowBytes / 2;     // 16 BF16 values of K
+constexpr int kKMax = 16384;                  // K per pass: 16384 * 32 * 32 = 2^24
+constexpr int kZeroExp = -100000;             // exponent of an all-zero row
+
+// pair q (by level L = t + u, then t) -> (t, u)
+__device__ __forceinline__ void oz_pair(int q, int& t, int& u) {
+    int L = 0, base = 0;
+    while (base + L + 1 <= q) {
+        base += L + 1;
+        L++;
+    }
+    t = q - base;
+    u = L - t;
+}
+
+__device__ __forceinline__ double pow2(int e) {
+    if (e < -1022) return 0.0;
+    if (e > 1023) e = 1023;
+    return __longlong_as_double((long long)(e + 1023) << 52);
+}
+
+// Epilogue of one pass: rows of the tile from TMEM lanes, Y += v 2^(e_i + f_j - 6(L + 2)).
+__device__ __forceinline__ void oz_epilogue(uint32_t tmem, int warp, int lane, int I, int J, const OzEpi& ep, int L,
+                                            bool first) {
+    const int row = warp * 32 + lane;
+    const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+    const size_t Np = (size_t)ep.Np;
+    const size_t gi = (size_t)I * 128 + row;
+    const int ei = ep.eU[gi];
+#pragma unroll 1
+    for (int c = 0; c < 128; c += 16) {
+        float d1r[16], d1i[16], d2r[16], d2i[16];
+        tmem_ld16(tl + c, d1r);            // U_r P_r^T
+        tmem_ld16(tl + 128 + c, d1i);      // U_r P_i^T
+        tmem_ld16(tl + 256 + c, d2r);      // U_i P_r^T
+        tmem_ld16(tl + 384 + c, d2i);      // U_i P_i^T
+        tmem_wait_ld();
+        const size_t gj0 = (size_t)J * 128 + c;
+        double2* yr = reinterpret_cast<double2*>(ep.yr + gi * Np + gj0);
+        double2* yi = reinterpret_cast<double2*>(ep.yi + gi * Np + gj0);
+#pragma unroll
+        for (int h = 0; h < 8; h++) {
+            double vr[2], vi[2];
+#pragma unroll
+            for (int w = 0; w < 2; w++) {
+                const int q = 2 * h + w;
+                const double sc = pow2(ei + ep.eP[gj0 + q] - 6 * (L + 2));
+                // exact integers: Y_r = U_r P_r^T + U_i P_i^T, Y_i = U_i P_r^T - U_r P_i^T
+                vr[w] = ((double)d1r[q] + (double)d2i[q]) * sc;
+                vi[w] = ((double)d2r[q] - (double)d1i[q]) * sc;
+            }
+            if (first) {
+                yr[h] = make_double2(vr[0], vr[1]);
+                yi[h] = make_double2(vi[0], vi[1]);
+            } else {
+                const double2 a = yr[h], b = yi[h];
+                yr[h] = make_double2(a.x + vr[0], a.y + vr[1]);
+                yi[h] = make_double2(b.x + vi[0], b.y + vi[1]);
+            }
+        }
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, 1)
+    cgemm_oz_kernel(const __grid_constant__ CUtensorMap tmU, const __grid_constant__ CUtensorMap tmP, OzEpi ep) {
+    constexpr uint32_t kIdesc = make_idesc(1u, 128u, 256u);   // BF16 x BF16 -> FP32, M 128, N 256
+
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStage);
+    uint64_t* empty = full + kStages;
+    uint64_t* accum = empty + kStages;      // MMA -> epilogue, once per pass
+    uint64_t* tmem_empty = accum + 1;       // epilogue -> MMA, once per pass
+    uint64_t* drain = tmem_empty + 1;       // MMA issuer's own completion wait at teardown
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint64_t lim = ep.wait_ns ? ep.wait_ns : kWaitLimitNs;
+    int I, J;
+    tile_of(MODE, ep.tiles, ep.group, blockIdx.x, I, J);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; s++) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(accum, 1);
+        mbar_init(tmem_empty, 1);
+        mbar_init(drain, 1);
+        *abort = 0;
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        tmem_alloc(saddr(tmem_slot), 512);
+        tmem_relinquish();
+    }
+    if (warp == 4 && lane == 0) {
+        prefetch_tmap(&tmU);
+        prefetch_tmap(&tmP);
+    }
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int Kc = ep.Np < kKMax ? ep.Np : kKMax;
+    const int chunks = ep.Np / Kc;
+    const int KBc = Kc / kKPerStage;
+    const int passes = kOzPairs * chunks;
+
+    if (warp == 4) {
+        // ---------------------------------------------------------- producer
+        if (lane == 0) {
+            uint32_t it = 0;
+            bool ok = true;
+            for (int p = 0; p < passes && ok; p++) {
+                int t, u;
+                oz_pair(p / chunks, t, u);
+                const int c = p % chunks;
+                for (int kb = 0; kb < KBc; kb++, it++) {
+                    const int s = it % kStages;
+                    const uint32_t ph = (it / kStages) & 1u;
+                    if (!mbar_wait_bounded(&empty[s], ph ^ 1u, abort, lim, 0)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&full[s], kStage);
+                    uint8_t* st = smem + s * kStage;
+                    const uint32_t fb = saddr(&full[s]);
+                    const int kx = c * Kc + kb * kKPerStage;
+                    tma_load_3d(saddr(st), &tmU, fb, kx, I * 128, t);                            // U_r slice t
+                    tma_load_3d(saddr(st + kATile), &tmU, fb, kx, I * 128, kOzSlices + t);       // U_i slice t
+                    tma_load_3d(saddr(st + 2 * kATile), &tmP, fb, kx, J * 128, u);               // P_r slice u
+                    tma_load_3d(saddr(st + 2 * kATile + 128 * kRowBytes), &tmP, fb, kx, J * 128,
+                                kOzSlices + u);                                                  // P_i slice u
+                }
+            }
+            if (*abort) {
+                // let the copies already issued land before the CTA goes away
+                for (uint32_t k = it > (uint32_t)kStages ? it - kStages : 0u; k < it; k++)
+                    (void)mbar_wait_bounded(&full[k % kStages], (k / kStages) & 1u, nullptr, lim, 0);
+            }
+        }
+    } else if (warp == 5) {
+        // ---------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            uint32_t it = 0;
+            bool ok = true;
+            for (int p = 0; p < passes && ok; p++) {
+                if (p > 0 && !mbar_wait_bounded(tmem_empty, (uint32_t)(p - 1) & 1u, abort, lim, 0)) break;
+                tc_fence_after();
+                for (int kb = 0; kb < KBc; kb++, it++) {
+                    const int s = it % kStages;
+                    const uint32_t ph = (it / kStages) & 1u;
+                    if (!mbar_wait_bounded(&full[s], ph, abort, lim, 0)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    uint8_t* st = smem + s * kStage;
+                    const uint64_t bd = desc_kmajor_sw32(saddr(st + 2 * kATile));
+                    umma<0>(tmem, desc_kmajor_sw32(saddr(st)), bd, kIdesc, kb > 0 ? 1u : 0u);
+                    umma<0>(tmem + 256, desc_kmajor_sw32(saddr(st + kATile)), bd, kIdesc, kb > 0 ? 1u : 0u);
+                    umma_commit(saddr(&empty[s]));
+                }
+                umma_commit(saddr(accum));
+            }
+            // own MMAs complete before the CTA frees TMEM
+            umma_commit(saddr(drain));
+            (void)mbar_wait_bounded(drain, 0u, nullptr, lim, 0);
+        }
+    } else {
+        // ---------------------------------------------------------- epilogue
+        for (int p = 0; p < passes; p++) {
+            const bool ok = mbar_wait_bounded(accum, (uint32_t)p & 1u, abort, lim, 128);
+            tc_fence_after();
+            // the four epilogue warps leave together or not at all
+            uint32_t bad = (!ok || *abort) ? 1u : 0u, any;
+            asm volatile(
+                "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+                "bar.red.or.pred q, 1, 128, p;\n\tselp.u32 %0, 1, 0, q;\n}"
+                : "=r"(any)
+                : "r"(bad)
+                : "memory");
+            if (any) {
+                if (threadIdx.x == 0) *abort = 1;
+                break;
+            }
+            int t, u;
+            oz_pair(p / chunks, t, u);
+            oz_epilogue(tmem, warp, lane, I, J, ep, t + u, p == 0);
+            tc_fence_before();
+            asm volatile("bar.sync 1, 128;" ::: "memory");   // all four epilogue warps have read TMEM
+            if (threadIdx.x == 0)
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(tmem_empty)) : "memory");
+        }
+        if (*abort && threadIdx.x == 0) atomicOr(ep.status, kStatusTimeout);
+    }
+
+    __syncwarp();
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 512);
+    }
+}
+
+constexpr int kSmem = kStages * kStage + 1024 /*align*/ + 256 /*barriers*/;
+
+// One warp per row r < Np: the row exponent over both planes, then the nine
+// balanced base-64 digits of every entry (zero beyond the valid N x N block).
+// INTERLEAVED: re/im interleaved complex128 with row stride ld (complex
+// elements); else planar FP64 planes re, im with row stride ld.
+template <bool INTERLEAVED>
+__global__ void oz_slice_kernel(const double* __restrict__ re, const double* __restrict__ im, int N, size_t ld,
+                                int Np, __nv_bfloat16* __restrict__ slices, int* __restrict__ ex) {
+    const int warps = (int)(gridDim.x * blockDim.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const size_t plane = (size_t)Np * Np;
+    for (int r = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); r < Np; r += warps) {
+        auto at = [&](int c, double& xr, double& xi) {
+            if (r < N && c < N) {
+                if (INTERLEAVED) {
+                    xr = re[2 * ((size_t)r * ld + c)];
+                    xi = re[2 * ((size_t)r * ld + c) + 1];
+                } else {
+                    xr = re[(size_t)r * ld + c];
+                    xi = im[(size_t)r * ld + c];
+                }
+            } else {
+                xr = 0.0;
+                xi = 0.0;
+            }
+        };
+        double m = 0.0;
+        for (int c = lane; c < N; c += 32) {
+            double xr, xi;
+            at(c, xr, xi);
+            m = fmax(m, fmax(fabs(xr), fabs(xi)));
+        }
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        const int e = m > 0.0 ? ilogb(m) + 2 : kZeroExp;   // max |x| < 2^(e - 1)
+        if (lane == 0) ex[r] = e;
+        // x 2^(54 - e) as two exact power-of-two factors (54 - e exceeds the
+        // FP64 exponent range for rows below 2^-969)
+        const int sh = 54 - e;
+        const double sc1 = m > 0.0 ? pow2(sh < 1000 ? sh : 1000) : 0.0;
+        const double sc2 = m > 0.0 ? pow2(sh < 1000 ? 0 : sh - 1000) : 0.0;
+        for (int c = lane; c < Np; c += 32) {
+            double xv[2];
+            at(c, xv[0], xv[1]);
+#pragma unroll
+            for (int part = 0; part < 2; part++) {
+                long long v = __double2ll_rn(xv[part] * sc1 * sc2);   // |v| < 2^53
+                __nv_bfloat16* dst = slices + (size_t)part * kOzSlices * plane + (size_t)r * Np + c;
+#pragma unroll
+                for (int t = kOzSlices - 1; t >= 1; t--) {
+                    const long long d = ((v + 32) & 63) - 32;   // balanced digit in [-32, 31]
+                    v = (v - d) >> 6;
+                    dst[(size_t)t * plane] = __float2bfloat16_rn((float)d);
+                }
+                dst[0] = __float2bfloat16_rn((float)v);   // |v| <= 32
+            }
+        }
+    }
+}
+
+// Upper triangle of a Hermitian result from its lower triangle; real diagonal.
+__global__ void oz_mirror_kernel(double* __restrict__ yr, double* __restrict__ yi, int Np) {
+    const size_t count = (size_t)Np * Np;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x) {
+        const size_t i = e / Np, j = e % Np;
+        if (i == j) {
+            yi[e] = 0.0;
+        } else if (i < j) {
+            yr[e] = yr[j * Np + i];
+            yi[e] = -yi[j * Np + i];
+        }
+    }
+}
+
+unsigned grid_for(size_t work) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    size_t want = (work + 255) / 256;
+    size_t cap = (size_t)sms * 16;
+    return (unsigned)(want < cap ? (want ? want : 1) : cap);
+}
+
+template <int MODE>
+tc_status launch(const CUtensorMap& tmU, const CUtensorMap& tmP, const OzEpi& ep, cudaStream_t s) {
+    auto k = cgemm_oz_kernel<MODE>;
+    static bool attr_set[64] = {};
+    int dev = 0;
+    TC_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(TC_ERR_UNSUPPORTED_DEVICE, "device index out of range");
+    if (!attr_set[dev]) {
+        TC_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem));
+        attr_set[dev] = true;
+    }
+    const int T = ep.tiles;
+    const unsigned grid = MODE == 0 ? (unsigned)(T * T) : (unsigned)(T * (T + 1) / 2);
+    k<<<grid, kThreads, kSmem, s>>>(tmU, tmP, ep);
+    TC_LAUNCH_CHECK();
+    return TC_OK;
+}
+
+}  // namespace
+
+tc_status oz_slice(const double* re, const double* im, bool interleaved, int N, size_t ld, int Np, void* slices,
+                   int* ex, cudaStream_t s) {
+    const unsigned blocks = (unsigned)(((size_t)Np * 32 + 255) / 256);
+    const unsigned g = blocks < grid_for((size_t)Np * 32) ? blocks : grid_for((size_t)Np * 32);
+    if (interleaved)
+        oz_slice_kernel<true><<<g, 256, 0, s>>>(re, im, N, ld, Np, static_cast<__nv_bfloat16*>(slices), ex);
+    else
+        oz_slice_kernel<false><<<g, 256, 0, s>>>(re, im, N, ld, Np, static_cast<__nv_bfloat16*>(slices), ex);
+    TC_LAUNCH_CHECK();
+    return TC_OK;
+}
+
+tc_status oz_mirror(double* yr, double* yi, int Np, cudaStream_t s) {
+    oz_mirror_kernel<<<grid_for((size_t)Np * Np), 256, 0, s>>>(yr, yi, Np);
+    TC_LAUNCH_CHECK();
+    return TC_OK;
+}
+
+tc_status cgemm_oz(int mode, const CUtensorMap& tmU, const CUtensorMap& tmP, const OzEpi& ep, cudaStream_t s) {
+    if (ep.Np < 128 || ep.Np % 128 != 0 || ep.tiles * 128 != ep.Np)
+        return fail(TC_ERR_INVALID_ARG, "cgemm_oz: padded dimension must be a multiple of 128");
+    if (ep.Np > kKMax && ep.Np % kKMax != 0)
+        return fail(TC_ERR_INVALID_ARG, "cgemm_oz: dimension above %d must be a multiple of it", kKMax);
+    if (mode == 0) return launch<0>(tmU, tmP, ep, s);
+    if (mode == 1) return launch<1>(tmU, tmP, ep, s);
+    return fail(TC_ERR_INVALID_ARG, "cgemm_oz: mode");
+}
+
+size_t oz_slice_bytes(int Np) { return round256((size_t)2 * kOzSlices * Np * Np * sizeof(__nv_bfloat16)); }
+
+}  // namespace tc

@@ -1,0 +1,35 @@
+// cgemm_oz.cuh -- FP64-accurate complex GEMM Y = U P^H from exact integer
+// slices on the BF16 tensor cores (see cgemm_oz.cu).
+#pragma once
+
+#include <cuda.h>
+
+#include "common.cuh"
+
+namespace tc {
+
+constexpr int kOzSlices = 9;                                   // base-64 digits per entry (54 bits)
+constexpr int kOzPairs = kOzSlices * (kOzSlices + 1) / 2;      // slice pairs with t + u <= 8
+
+struct OzEpi {
+    int Np;             // padded dimension, a multiple of 128
+    int tiles;          // Np / 128
+    int group;          // mode 0 raster group (row tiles)
+    const int* eU;      // row exponents of U [Np]
+    const int* eP;      // row exponents of P [Np]
+    double* yr;         // FP64 planes of Y [Np][Np]
+    double* yi;
+    unsigned* status;
+    unsigned long long wait_ns;   // limit of every barrier wait (0 = 2 s)
+};
+
+// Slices [2 * kOzSlices][Np][Np] (BF16 digits: re slices, then im slices) and
+// row exponents ex[Np] of the N x N matrix (zero-padded to Np).
+tc_status oz_slice(const double* re, const double* im, bool interleaved, int N, size_t ld, int Np, void* slices,
+                   int* ex, cudaStream_t s);
+size_t oz_slice_bytes(int Np);
+// Y = U P^H (mode 0: all tiles; mode 1: block-lower tiles, then oz_mirror)
+tc_status cgemm_oz(int mode, const CUtensorMap& tmU, const CUtensorMap& tmP, const OzEpi& ep, cudaStream_t s);
+tc_status oz_mirror(double* yr, double* yi, int Np, cudaStream_t s);
+
+}  // namespace tc

@@ -52,56 +52,6 @@ using namespace cg;
 
 constexpr int kThreads = 192;
 
-__device__ __forceinline__ void tri_decode(int b, int& i, int& j) {
-    int r = (int)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
-    while ((r + 1) * (r + 2) / 2 <= b) ++r;
-    while (r * (r + 1) / 2 > b) --r;
-    i = r;
-    j = b - r * (r + 1) / 2;
-}
-
-// Tile b of the launch -> (I, J).  Both orders keep the CTAs that run at the
-// same time on few operand panels, so the panels are re-read from L2:
-//  mode 0 (all T x T tiles): groups of G row tiles, column by column;
-//  mode 1 (block-lower tiles): G x G super-blocks of the lower triangle, row
-//  by row; inside a super-block the tiles go column by column (the diagonal
-//  super-blocks hold only their lower half).
-__device__ __forceinline__ void tile_of(int mode, int T, int G, int b, int& I, int& J) {
-    if (G < 1) G = 1;
-    if (mode == 0) {
-        int per_group = G * T;
-        int g = b / per_group;
-        int first = g * G;
-        int rows = min(G, T - first);
-        int in = b % per_group;
-        I = first + in % rows;
-        J = in / rows;
-        return;
-    }
-    const int SB = (T + G - 1) / G;
-    for (int bi = 0; bi < SB; bi++) {
-        const int rows = min(G, T - bi * G);
-        for (int bj = 0; bj <= bi; bj++) {
-            const int cols = min(G, T - bj * G);
-            const int cnt = (bi == bj) ? rows * (rows + 1) / 2 : rows * cols;
-            if (b < cnt) {
-                if (bi == bj) {
-                    int ti, tj;
-                    tri_decode(b, ti, tj);
-                    I = bi * G + ti;
-                    J = bj * G + tj;
-                } else {
-                    I = bi * G + b % rows;
-                    J = bj * G + b / rows;
-                }
-                return;
-            }
-            b -= cnt;
-        }
-    }
-    I = J = 0;   // not reached for b < T (T + 1) / 2
-}
-
 template <int KIND, int S, int STAGES, int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
     cgemm_tc_kernel(const __grid_constant__ CUtensorMap tmU, const __grid_constant__ CUtensorMap tmP, CgemmEpi ep) {

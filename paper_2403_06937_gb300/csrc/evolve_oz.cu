@@ -1,0 +1,167 @@
+// evolve_oz.cu -- the FP64-accurate tensor-core form of the step loop
+// rho <- U rho U^dag (Sec. III.A, Eqs. 6, 12): both products on the BF16
+// tensor cores from exact integer slices (cgemm_oz.cu), rho and X kept in
+// FP64 planes (row stride Np = max(N, 128), zero padding).
+//
+// Per step: slice rho, X = U rho^H (all tiles), slice X, rho' = U X^H
+// (block-lower tiles, then the mirrored upper half), observables from the
+// FP64 planes; U is sliced once per call.  U enters as it is (no increment
+// form): the slice products are exact, so there is no accumulation bias to
+// scale down.
+#include "cgemm_oz.cuh"
+#include "cgemm_tc.cuh"
+#include "graph.cuh"
+#include "paths.cuh"
+#include "timing.cuh"
+
+namespace tc {
+namespace {
+
+unsigned grid_for(size_t work) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    size_t want = (work + 255) / 256;
+    size_t cap = (size_t)sms * 16;
+    return (unsigned)(want < cap ? (want ? want : 1) : cap);
+}
+
+// interleaved N x N complex128 -> FP64 planes of stride Np (zero outside N x N)
+__global__ void split_pad_kernel(const double2* __restrict__ src, int N, int Np, double* __restrict__ re,
+                                 double* __restrict__ im) {
+    const size_t count = (size_t)Np * Np;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x) {
+        const size_t i = e / Np, j = e % Np;
+        double2 v = make_double2(0.0, 0.0);
+        if (i < (size_t)N && j < (size_t)N) v = src[i * N + j];
+        re[e] = v.x;
+        im[e] = v.y;
+    }
+}
+
+__global__ void join_pad_kernel(const double* __restrict__ re, const double* __restrict__ im, int N, int Np,
+                                double2* __restrict__ dst) {
+    const size_t count = (size_t)N * N;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x) {
+        const size_t i = e / N, j = e % N;
+        dst[e] = make_double2(re[i * Np + j], im[i * Np + j]);
+    }
+}
+
+// trace of the N x N block in FP64 (one CTA, fixed order), then rho / trace
+__global__ void trace_pad_kernel(const double* __restrict__ re, int N, int Np, double* __restrict__ out) {
+    __shared__ double sh[1024];
+    double a = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) a += re[(size_t)i * Np + i];
+    sh[threadIdx.x] = a;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = sh[0];
+}
+
+__global__ void scale_pad_kernel(double* __restrict__ re, double* __restrict__ im, int Np,
+                                 const double* __restrict__ trace, unsigned* status) {
+    const double tr = trace[0];
+    if (!(tr > 0.0) || !isfinite(tr)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, kStatusNumeric);
+        return;
+    }
+    const double inv = 1.0 / tr;
+    const size_t count = (size_t)Np * Np;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x) {
+        re[e] *= inv;
+        im[e] *= inv;
+    }
+}
+
+int padded_dim(int n) { return (1 << n) < 128 ? 128 : (1 << n); }
+
+}  // namespace
+
+size_t evolve_oz_bytes(int n) {
+    const size_t Np = (size_t)padded_dim(n);
+    return 2 * oz_slice_bytes((int)Np) + 4 * round256(Np * Np * sizeof(double)) + 2 * round256(Np * sizeof(int)) +
+           observables_scratch_bytes(n) + 512;
+}
+
+tc_status evolve_oz(const double* U, double* rho, int n, int steps, int renorm_every, const Model* m, double* obs,
+                    Arena& ar, cudaStream_t s) {
+    const int N = 1 << n;
+    const int Np = padded_dim(n);
+    const size_t NN = (size_t)Np * Np;
+    void* Us = ar.take<uint8_t>(oz_slice_bytes(Np));
+    void* Ps = ar.take<uint8_t>(oz_slice_bytes(Np));
+    double* Rr = ar.take<double>(NN);
+    double* Ri = ar.take<double>(NN);
+    double* Xr = ar.take<double>(NN);
+    double* Xi = ar.take<double>(NN);
+    int* eU = ar.take<int>((size_t)Np);
+    int* eP = ar.take<int>((size_t)Np);
+    double* scratch = ar.take<double>(observables_scratch_bytes(n) / sizeof(double));
+    if (!scratch) return fail(TC_ERR_WORKSPACE, "evolve: workspace too small");
+
+    CUtensorMap tmU, tmP;
+    TC_TRY(make_part_map(&tmU, Us, Np, 2 * kOzSlices, TC_BF16X3));
+    TC_TRY(make_part_map(&tmP, Ps, Np, 2 * kOzSlices, TC_BF16X3));
+    const TuneChoice tune = tune_lookup(n, TC_BF16X3);
+    OzEpi e1{};                    // X = U rho^H
+    e1.Np = Np;
+    e1.tiles = Np / 128;
+    e1.group = tune.tc_group;
+    e1.eU = eU;
+    e1.eP = eP;
+    e1.yr = Xr;
+    e1.yi = Xi;
+    e1.status = device_status_word();
+    OzEpi e2 = e1;                 // rho' = U X^H
+    e2.yr = Rr;
+    e2.yi = Ri;
+
+    const int stride = TC_OBS_STRIDE(n);
+    const double N3 = (double)N * N * N;
+    auto one_step = [&](int k, cudaStream_t cs) -> tc_status {
+        TC_TRY(oz_slice(Rr, Ri, false, N, (size_t)Np, Np, Ps, eP, cs));
+        {
+            ProductTimer t(8.0 * N3 * kOzPairs, cs);
+            TC_TRY(cgemm_oz(0, tmU, tmP, e1, cs));
+        }
+        TC_TRY(oz_slice(Xr, Xi, false, N, (size_t)Np, Np, Ps, eP, cs));
+        {
+            ProductTimer t(4.0 * N3 * kOzPairs, cs);
+            TC_TRY(cgemm_oz(1, tmU, tmP, e2, cs));
+        }
+        TC_TRY(oz_mirror(Rr, Ri, Np, cs));
+        if (renorm_every > 0 && k % renorm_every == 0) {
+            trace_pad_kernel<<<1, 1024, 0, cs>>>(Rr, N, Np, scratch);
+            TC_LAUNCH_CHECK();
+            scale_pad_kernel<<<grid_for(NN), 256, 0, cs>>>(Rr, Ri, Np, scratch, device_status_word());
+            TC_LAUNCH_CHECK();
+        }
+        if (obs)
+            TC_TRY(launch_observables(kRhoPlanarF64, Rr, Ri, m, n, obs + (size_t)k * stride, scratch, cs, (size_t)Np));
+        return TC_OK;
+    };
+    auto first = [&](cudaStream_t cs) -> tc_status {
+        TC_TRY(oz_slice(U, nullptr, true, N, (size_t)N, Np, Us, eU, cs));
+        split_pad_kernel<<<grid_for(NN), 256, 0, cs>>>(reinterpret_cast<const double2*>(rho), N, Np, Rr, Ri);
+        TC_LAUNCH_CHECK();
+        if (obs) TC_TRY(launch_observables(kRhoPlanarF64, Rr, Ri, m, n, obs, scratch, cs, (size_t)Np));
+        if (steps >= 1) TC_TRY(one_step(1, cs));
+        return TC_OK;
+    };
+    auto rest = [&](cudaStream_t cs) -> tc_status {
+        for (int k = 2; k <= steps; k++) TC_TRY(one_step(k, cs));
+        return TC_OK;
+    };
+    auto tail = [&](cudaStream_t cs) -> tc_status {
+        join_pad_kernel<<<grid_for((size_t)N * N), 256, 0, cs>>>(Rr, Ri, N, Np, reinterpret_cast<double2*>(rho));
+        TC_LAUNCH_CHECK();
+        return TC_OK;
+    };
+    return run_captured(s, first, rest, tail, steps > 2 && !timing_enabled());
+}
+
+}  // namespace tc

@@ -33,6 +33,11 @@ tc_status expm_model_impl(const Model& m, double dt, const tc_expm_opts* opts, d
 tc_status evolve_f64(const double* U, double* rho, int n, int steps, int renorm_every, const Model* m,
                      double* obs, Arena& ar, cudaStream_t s);
 
+// FP64-accurate step loop on the BF16 tensor cores (exact integer slices).
+size_t evolve_oz_bytes(int n);
+tc_status evolve_oz(const double* U, double* rho, int n, int steps, int renorm_every, const Model* m, double* obs,
+                    Arena& ar, cudaStream_t s);
+
 // Low-precision step loop (tcgen05 products).
 size_t evolve_lowp_bytes(int n, int precision);
 tc_status evolve_lowp(const double* U, double* rho, int n, int steps, int precision, int renorm_every,
