@@ -53,7 +53,7 @@ def _args():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["bf16x3", "tf32x3", "tf32", "fp64"], default="bf16x3")
+    ap.add_argument("--precision", choices=["bf16x3", "tf32x3", "tf32", "fp64", "ozaki"], default="bf16x3")
     ap.add_argument("--workload", choices=["n14", "n15", "n12", "n8", "batch", "grad", "open14", "open12"],
                     default="n14",
                     help="n14 (default, the metric's workload), n12, n8; batch: 64 systems n=6..12 "
@@ -249,6 +249,9 @@ def _compulsory_bytes(prec, N):
     the FP32 result plus its split planes written."""
     if prec == "fp64":
         return 3 * 16 * N * N
+    if prec == "ozaki":
+        # nine BF16 digit planes of U and of P read, the FP64 result written
+        return (2 * 2 * 9 * 2 + 16) * N * N
     parts, pbytes = {"bf16x3": (3, 2), "tf32": (1, 4), "tf32x3": (2, 4)}[prec]
     planes = 2 * parts * pbytes
     return (3 * planes + 8 + 8) * N * N
@@ -356,10 +359,10 @@ def run_ours(a, cfg):
     line = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": {"fp64": "f64", "bf16x3": "bf16", "tf32": "tf32", "tf32x3": "tf32"}[prec],
+        "vs_baseline": None, "dtype": {"fp64": "f64", "bf16x3": "bf16", "tf32": "tf32", "tf32x3": "tf32", "ozaki": "bf16"}[prec],
         "data": "synthetic",
         "config": {"workload": cfg.description, "precision": prec, "dim": N,
-                   "products_per_complex_product": {"fp64": 1, "bf16x3": 6, "tf32": 1, "tf32x3": 3}[prec],
+                   "products_per_complex_product": {"fp64": 1, "bf16x3": 6, "tf32": 1, "tf32x3": 3, "ozaki": 45}[prec],
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (U and rho are %d MiB each in complex128)" % (16 * N * N >> 20),
                    "setup_s": t_setup},
@@ -395,7 +398,8 @@ def run_ours(a, cfg):
     if not a.no_compare:
         # the other forms on the same workload: split-TF32, TF32 and one FP64 step
         others = {}
-        for p2, k2, w2 in (("tf32x3", a.steps, a.warmup), ("tf32", a.steps, a.warmup), ("fp64", 1, 0)):
+        for p2, k2, w2 in (("tf32x3", a.steps, a.warmup), ("tf32", a.steps, a.warmup), ("ozaki", 2, 1),
+                           ("fp64", 1, 0)):
             if p2 == prec:
                 continue
             if p2 == "fp64" and n >= 15:
@@ -411,6 +415,8 @@ def run_ours(a, cfg):
         line["other_forms"] = others
         if "value" in others.get("fp64", {}):
             line["speedup_vs_fp64"] = (value / world) / others["fp64"]["value"]
+            if "value" in others.get("ozaki", {}):
+                others["ozaki"]["speedup_vs_fp64"] = others["ozaki"]["value"] / others["fp64"]["value"]
 
     if rank == 0 and not a.no_cpu:
         v, cores, sample, _ = _cpu_sample(cfg, a.cpu_seconds)

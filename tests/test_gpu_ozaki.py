@@ -1,0 +1,157 @@
+"""Parity of the FP64-accurate tensor-core form (TC_FP64_OZAKI: exact integer
+slices on the BF16 tensor cores) with the FP64 DMMA path and the oracle.
+
+Tolerance, from the arithmetic: every entry x of an operand row with scale
+2^e (max |x| < 2^(e-1)) is held to 2^(e-55) (one rounding of x 2^(54-e) to an
+integer), the slice-pair sums are exact, and the dropped pairs (t + u >= 9)
+contribute at most 8 * 2^10 * 2^-66 2^(e_i + f_j) per term; with
+2^e <= 4 max|row| each of the K terms of a product is within
+2^-48 max|A_i| max|B_j|, so one product is within K 2^-48 max|U| max|P|,
+two products per step.  (The FP64 DMMA reference adds its own K 2^-53.)
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def bound(n, steps, umax=1.0, pmax=1.0):
+    K = max(1 << n, 128)
+    return steps * 2 * K * 2.0 ** -48 * umax * pmax * 1.01 + steps * 2 * K * 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def tc():
+    from paper_2403_06937_gb300 import build
+    build.build()
+    import paper_2403_06937_gb300 as tc
+    tc.device_check()
+    return tc
+
+
+def _params(tc, n, g, wa, wc, coupling=0):
+    return tc.Params(n, list(map(float, g)), wa, wc, coupling)
+
+
+@pytest.mark.parametrize("n,steps", [(1, 30), (3, 20), (6, 20), (7, 10), (9, 10), (10, 5)])
+def test_matches_fp64_path(tc, n, steps):
+    g = W.draw_couplings(n, 60 + n) * 5
+    p = _params(tc, n, g, 1.013, 1.0)
+    U = tc.expm_model(p, 0.1)
+    rho0, _, _ = W.random_mixed_state(n, min(3, 1 << n), 30 + n)
+    r0 = torch.from_numpy(rho0).cuda()
+    a, oa = tc.evolve(U, r0, n, steps, "fp64", params=p)
+    b, ob = tc.evolve(U, r0, n, steps, "ozaki", params=p)
+    tc.sync_status()
+    umax = torch.max(torch.abs(U)).item()
+    tol = bound(n, steps, umax, 1.0)
+    assert torch.max(torch.abs(a - b)).item() < tol
+    assert torch.max(torch.abs(oa - ob)[:, :2 * n + 3]).item() < (1 << n) * tol
+    assert torch.equal(b, b.conj().T)   # exactly Hermitian: the upper half is the mirrored lower half
+
+
+def test_n8_workload_against_oracle(tc, oracle):
+    """n = 8, 100 steps from the all-excited state: the FP64 target 1e-10 on rho and the rows."""
+    cfg = W.config_n8()
+    n = cfg.n
+    p = _params(tc, n, cfg.g, cfg.omega_a, cfg.omega_c)
+    U = tc.expm_model(p, cfg.dt)
+    rho0 = torch.from_numpy(W.all_excited_rho(n)).cuda()
+    rho, obs = tc.evolve(U, rho0, n, cfg.steps, "ozaki", params=p)
+    psi, oobs = oracle.propagate(n, cfg.g, cfg.omega_a, cfg.omega_c, cfg.dt, cfg.steps, W.all_excited_state(n))
+    assert np.max(np.abs(rho.cpu().numpy() - np.outer(psi, psi.conj()))) < 1e-10
+    assert np.max(np.abs(obs.cpu().numpy() - oobs)) < 1e-10
+
+
+def test_runs_are_bitwise_reproducible(tc):
+    n = 8
+    p = _params(tc, n, W.draw_couplings(n, 4) * 10, 1.0, 1.0)
+    U = tc.expm_model(p, 0.1)
+    rho0, _, _ = W.random_mixed_state(n, 2, 9)
+    r0 = torch.from_numpy(rho0).cuda()
+    a, oa = tc.evolve(U, r0, n, 7, "ozaki", params=p)
+    b, ob = tc.evolve(U, r0, n, 7, "ozaki", params=p)
+    assert torch.equal(a, b) and torch.equal(oa, ob)
+
+
+def test_zero_steps_and_tiny_rows(tc):
+    """Zero steps return rho unchanged (FP64 storage); a state scaled by 2^-950 keeps its relative
+    accuracy (its rows' 2^(54 - e) exceeds the FP64 exponent range and is applied as two factors;
+    the smallest slice products, 2^(e_i + e_j - 60), stay normal)."""
+    n = 5
+    p = _params(tc, n, W.draw_couplings(n, 5), 1.0, 1.0)
+    U = tc.expm_model(p, 0.1)
+    rho0, _, _ = W.random_mixed_state(n, 2, 3)
+    r0 = torch.from_numpy(rho0).cuda()
+    out, _ = tc.evolve(U, r0, n, 0, "ozaki", params=p)
+    assert torch.equal(out, r0)
+    tiny = r0 * 2.0 ** -950
+    a, _ = tc.evolve(U, tiny, n, 2, "fp64", params=p)
+    b, _ = tc.evolve(U, tiny, n, 2, "ozaki", params=p)
+    assert torch.max(torch.abs(a - b)).item() < 2.0 ** -950 * bound(n, 2, 1.0, 1.0)
+    assert torch.max(torch.abs(b)).item() > 2.0 ** -960
+
+
+def test_n12_workload_against_fp64_path(tc):
+    cfg = W.config_n12()
+    n = cfg.n
+    p = _params(tc, n, cfg.g, cfg.omega_a, cfg.omega_c)
+    U = tc.expm_model(p, cfg.dt)
+    N = 1 << n
+    rho0 = torch.zeros((N, N), dtype=torch.complex128, device="cuda")
+    rho0[-1, -1] = 1.0
+    a, oa = tc.evolve(U, rho0, n, 3, "fp64", params=p)
+    b, ob = tc.evolve(U, rho0, n, 3, "ozaki", params=p)
+    assert torch.max(torch.abs(a - b)).item() < bound(n, 3)
+    assert torch.max(torch.abs(oa - ob)).item() < bound(n, 3) * 64
+
+
+def test_n14_workload_sampled(tc, oracle):
+    """n = 14 (the benchmark's size), 3 steps: sampled entries and the observable rows against the
+    oracle's pure-state propagation."""
+    cfg = W.config_n14()
+    n = cfg.n
+    p = _params(tc, n, cfg.g, cfg.omega_a, cfg.omega_c)
+    U = tc.expm_model(p, cfg.dt)
+    rho0 = torch.zeros((cfg.N, cfg.N), dtype=torch.complex128, device="cuda")
+    rho0[-1, -1] = 1.0
+    steps = 3
+    rho, obs = tc.evolve(U, rho0, n, steps, "ozaki", params=p)
+    tc.sync_status()
+    psi, oobs = oracle.propagate(n, cfg.g, cfg.omega_a, cfg.omega_c, cfg.dt, steps, W.all_excited_state(n))
+    tol = bound(n, steps) + 1e-13
+    assert np.max(np.abs(obs.cpu().numpy()[:, :2 * n + 3] - oobs[:, :2 * n + 3])) < tol
+    rng = np.random.default_rng(7)
+    idx = rng.integers(0, cfg.N, size=(20000, 2))
+    top = np.argsort(-np.abs(psi))[:48]
+    ii = np.concatenate([idx[:, 0], np.repeat(top, len(top))])
+    jj = np.concatenate([idx[:, 1], np.tile(top, len(top))])
+    got = rho[torch.from_numpy(ii).cuda(), torch.from_numpy(jj).cuda()].cpu().numpy()
+    assert np.max(np.abs(got - psi[ii] * psi[jj].conj())) < tol
+    del rho, rho0, U
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.slow
+def test_n15_one_step_two_k_chunks(tc, oracle):
+    """n = 15: K = 32768 is summed in two exact passes of 16384 per slice pair."""
+    cfg = W.config_n15()
+    n = cfg.n
+    p = _params(tc, n, cfg.g, cfg.omega_a, cfg.omega_c)
+    U = tc.expm_model(p, cfg.dt)
+    rho0 = torch.zeros((cfg.N, cfg.N), dtype=torch.complex128, device="cuda")
+    rho0[-1, -1] = 1.0
+    rho, obs = tc.evolve(U, rho0, n, 1, "ozaki", params=p)
+    tc.sync_status()
+    psi, oobs = oracle.propagate(n, cfg.g, cfg.omega_a, cfg.omega_c, cfg.dt, 1, W.all_excited_state(n))
+    tol = bound(n, 1) + 1e-13
+    assert np.max(np.abs(obs.cpu().numpy()[:, :2 * n + 3] - oobs[:, :2 * n + 3])) < tol
+    top = np.argsort(-np.abs(psi))[:64]
+    ii, jj = np.repeat(top, len(top)), np.tile(top, len(top))
+    got = rho[torch.from_numpy(ii).cuda(), torch.from_numpy(jj).cuda()].cpu().numpy()
+    assert np.max(np.abs(got - psi[ii] * psi[jj].conj())) < tol
+    del rho, rho0, U
+    torch.cuda.empty_cache()
