@@ -13,9 +13,10 @@
 // 2^24, so the FP32 accumulation of the tensor cores is exact (no rounding,
 // hence no truncation).  One pass of the K loop per slice pair (t, u) with
 // t + u <= 8 (45 pairs; the first dropped level is ~2^-48 of the row and
-// column scales) accumulates that pair in TMEM; the epilogue then adds the
-// exact integer result times 2^(e_i + f_j - 6(t + u + 2)) into FP64 planes
-// of Y.  K above 16384 is cut into chunks of 16384, one pass each.
+// column scales) accumulates that pair in TMEM; the epilogue accumulates the
+// exact integer results in int64 with the level weights as shifts and the
+// last pass writes Y = sum 2^(e_i + f_j - 6(t + u + 2)) (integer) in FP64.
+// K above 16384 is cut into chunks of 16384, one pass each.
 //
 // Tile and roles as the split-BF16 kernel (cgemm_tc.cu): one CTA per 128 x 128
 // complex tile, A = slice t of U_r and U_i (M = 128), B = slice u of
@@ -60,13 +61,25 @@ __device__ __forceinline__ double pow2(int e) {
     return __longlong_as_double((long long)(e + 1023) << 52);
 }
 
-// Epilogue of one pass: rows of the tile from TMEM lanes, Y += v 2^(e_i + f_j - 6(L + 2)).
+// Epilogue of one pass (slice pair of level L = t + u).  The pass's sums are
+// exact integers below 2^24; Y_r = U_r P_r^T + U_i P_i^T and
+// Y_i = U_i P_r^T - U_r P_i^T are formed exactly in int32 and accumulated
+// exactly in int64, with the level's weight as a shift: levels 0-3 into
+// `hi` (unit 2^(e_i + f_j - 30), kept in the FP64 output planes until the
+// last pass), levels 4-8 into `lo` (unit 2^(e_i + f_j - 60)).  Bounds:
+// hi <= chunks * 10 * 2^25 * 2^18, lo <= chunks * 35 * 2^25 * 2^24, within
+// int64 for up to 2^8 K chunks.  The last pass writes
+//     Y = hi 2^(e_i + f_j - 30) + lo 2^(e_i + f_j - 60)
+// in FP64.  Integer work only, except that final combination.
 __device__ __forceinline__ void oz_epilogue(uint32_t tmem, int warp, int lane, int I, int J, const OzEpi& ep, int L,
-                                            bool first) {
+                                            bool first_hi, bool first_lo, bool last) {
     const int row = warp * 32 + lane;
     const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
     const size_t Np = (size_t)ep.Np;
     const size_t gi = (size_t)I * 128 + row;
+    const bool to_hi = L <= 3;
+    const int shift = to_hi ? 6 * (3 - L) : 6 * (8 - L);
+    const bool first = to_hi ? first_hi : first_lo;
     const int ei = ep.eU[gi];
 #pragma unroll 1
     for (int c = 0; c < 128; c += 16) {
@@ -76,27 +89,48 @@ __device__ __forceinline__ void oz_epilogue(uint32_t tmem, int warp, int lane, i
         tmem_ld16(tl + 256 + c, d2r);      // U_i P_r^T
         tmem_ld16(tl + 384 + c, d2i);      // U_i P_i^T
         tmem_wait_ld();
-        const size_t gj0 = (size_t)J * 128 + c;
-        double2* yr = reinterpret_cast<double2*>(ep.yr + gi * Np + gj0);
-        double2* yi = reinterpret_cast<double2*>(ep.yi + gi * Np + gj0);
+        const size_t o = gi * Np + (size_t)J * 128 + c;
+        long long* ar = to_hi ? reinterpret_cast<long long*>(ep.yr) + o : ep.lo_r + o;
+        long long* ai = to_hi ? reinterpret_cast<long long*>(ep.yi) + o : ep.lo_i + o;
+        longlong2* vr2 = reinterpret_cast<longlong2*>(ar);
+        longlong2* vi2 = reinterpret_cast<longlong2*>(ai);
 #pragma unroll
         for (int h = 0; h < 8; h++) {
-            double vr[2], vi[2];
+            long long xr[2], xi[2];
 #pragma unroll
             for (int w = 0; w < 2; w++) {
                 const int q = 2 * h + w;
-                const double sc = pow2(ei + ep.eP[gj0 + q] - 6 * (L + 2));
-                // exact integers: Y_r = U_r P_r^T + U_i P_i^T, Y_i = U_i P_r^T - U_r P_i^T
-                vr[w] = ((double)d1r[q] + (double)d2i[q]) * sc;
-                vi[w] = ((double)d2r[q] - (double)d1i[q]) * sc;
+                const int sr = __float2int_rn(d1r[q]) + __float2int_rn(d2i[q]);
+                const int si = __float2int_rn(d2r[q]) - __float2int_rn(d1i[q]);
+                xr[w] = (long long)sr << shift;
+                xi[w] = (long long)si << shift;
             }
-            if (first) {
-                yr[h] = make_double2(vr[0], vr[1]);
-                yi[h] = make_double2(vi[0], vi[1]);
+            if (!first) {
+                const longlong2 a = vr2[h], b = vi2[h];
+                xr[0] += a.x;
+                xr[1] += a.y;
+                xi[0] += b.x;
+                xi[1] += b.y;
+            }
+            if (!last) {
+                vr2[h] = make_longlong2(xr[0], xr[1]);
+                vi2[h] = make_longlong2(xi[0], xi[1]);
             } else {
-                const double2 a = yr[h], b = yi[h];
-                yr[h] = make_double2(a.x + vr[0], a.y + vr[1]);
-                yi[h] = make_double2(b.x + vi[0], b.y + vi[1]);
+                // the last pass is of level 8 (lo): combine with hi into FP64
+                const longlong2 hr = reinterpret_cast<const longlong2*>(ep.yr + o)[h];
+                const longlong2 hi_ = reinterpret_cast<const longlong2*>(ep.yi + o)[h];
+                const long long hr_[2] = {hr.x, hr.y}, hii[2] = {hi_.x, hi_.y};
+                double yr[2], yi[2];
+#pragma unroll
+                for (int w = 0; w < 2; w++) {
+                    const int q = 2 * h + w;
+                    const int ej = ep.eP[(size_t)J * 128 + c + q];
+                    const double s_hi = pow2(ei + ej - 30), s_lo = pow2(ei + ej - 60);
+                    yr[w] = (double)hr_[w] * s_hi + (double)xr[w] * s_lo;
+                    yi[w] = (double)hii[w] * s_hi + (double)xi[w] * s_lo;
+                }
+                reinterpret_cast<double2*>(ep.yr + o)[h] = make_double2(yr[0], yr[1]);
+                reinterpret_cast<double2*>(ep.yi + o)[h] = make_double2(yi[0], yi[1]);
             }
         }
     }
@@ -229,7 +263,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             int t, u;
             oz_pair(p / chunks, t, u);
-            oz_epilogue(tmem, warp, lane, I, J, ep, t + u, p == 0);
+            // pairs run by level: levels 0-3 are the first 10 pairs, 4-8 the rest
+            oz_epilogue(tmem, warp, lane, I, J, ep, t + u, p == 0, p == 10 * chunks, p == passes - 1);
             tc_fence_before();
             asm volatile("bar.sync 1, 128;" ::: "memory");   // all four epilogue warps have read TMEM
             if (threadIdx.x == 0)

@@ -17,8 +17,10 @@ struct OzEpi {
     int group;          // mode 0 raster group (row tiles)
     const int* eU;      // row exponents of U [Np]
     const int* eP;      // row exponents of P [Np]
-    double* yr;         // FP64 planes of Y [Np][Np]
+    double* yr;         // FP64 planes of Y [Np][Np] (int64 level sums until the last pass)
     double* yi;
+    long long* lo_r;    // int64 scratch planes [Np][Np] of the low levels
+    long long* lo_i;
     unsigned* status;
     unsigned long long wait_ns;   // limit of every barrier wait (0 = 2 s)
 };

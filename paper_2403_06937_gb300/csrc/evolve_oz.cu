@@ -83,7 +83,7 @@ int padded_dim(int n) { return (1 << n) < 128 ? 128 : (1 << n); }
 
 size_t evolve_oz_bytes(int n) {
     const size_t Np = (size_t)padded_dim(n);
-    return 2 * oz_slice_bytes((int)Np) + 4 * round256(Np * Np * sizeof(double)) + 2 * round256(Np * sizeof(int)) +
+    return 2 * oz_slice_bytes((int)Np) + 6 * round256(Np * Np * sizeof(double)) + 2 * round256(Np * sizeof(int)) +
            observables_scratch_bytes(n) + 512;
 }
 
@@ -98,6 +98,8 @@ tc_status evolve_oz(const double* U, double* rho, int n, int steps, int renorm_e
     double* Ri = ar.take<double>(NN);
     double* Xr = ar.take<double>(NN);
     double* Xi = ar.take<double>(NN);
+    long long* Lr = ar.take<long long>(NN);   // low-level integer sums of the products
+    long long* Li = ar.take<long long>(NN);
     int* eU = ar.take<int>((size_t)Np);
     int* eP = ar.take<int>((size_t)Np);
     double* scratch = ar.take<double>(observables_scratch_bytes(n) / sizeof(double));
@@ -115,6 +117,8 @@ tc_status evolve_oz(const double* U, double* rho, int n, int steps, int renorm_e
     e1.eP = eP;
     e1.yr = Xr;
     e1.yi = Xi;
+    e1.lo_r = Lr;
+    e1.lo_i = Li;
     e1.status = device_status_word();
     OzEpi e2 = e1;                 // rho' = U X^H
     e2.yr = Rr;
