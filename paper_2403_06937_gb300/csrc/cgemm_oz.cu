@@ -44,15 +44,17 @@ constexpr int kKPerStage = kRowBytes / 2;     // 16 BF16 values of K
 constexpr int kKMax = 16384;                  // K per pass: 16384 * 32 * 32 = 2^24
 constexpr int kZeroExp = -100000;             // exponent of an all-zero row
 
-// pair q (by level L = t + u, then t) -> (t, u)
+// pair q -> (t, u) with t + u <= 8, t-major: (0,0), (0,1), ..., (0,8), (1,0),
+// ..., (8,0).  Consecutive passes of a tile reuse the U slice t, which the
+// CTAs of a wave (a few row tiles) keep in L2 while the P slices stream.
 __device__ __forceinline__ void oz_pair(int q, int& t, int& u) {
-    int L = 0, base = 0;
-    while (base + L + 1 <= q) {
-        base += L + 1;
-        L++;
+    int tt = 0, base = 0;
+    while (base + (kOzSlices - tt) <= q) {
+        base += kOzSlices - tt;
+        tt++;
     }
-    t = q - base;
-    u = L - t;
+    t = tt;
+    u = q - base;
 }
 
 __device__ __forceinline__ double pow2(int e) {
@@ -68,7 +70,7 @@ __device__ __forceinline__ double pow2(int e) {
 // `hi` (unit 2^(e_i + f_j - 30), kept in the FP64 output planes until the
 // last pass), levels 4-8 into `lo` (unit 2^(e_i + f_j - 60)).  Bounds:
 // hi <= chunks * 10 * 2^25 * 2^18, lo <= chunks * 35 * 2^25 * 2^24, within
-// int64 for up to 2^8 K chunks.  The last pass writes
+// int64 for up to 2^8 K chunks.  The last pass (level 8) writes
 //     Y = hi 2^(e_i + f_j - 30) + lo 2^(e_i + f_j - 60)
 // in FP64.  Integer work only, except that final combination.
 __device__ __forceinline__ void oz_epilogue(uint32_t tmem, int warp, int lane, int I, int J, const OzEpi& ep, int L,
@@ -186,6 +188,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == 4) {
         // ---------------------------------------------------------- producer
         if (lane == 0) {
+            // U slices are kept in L2 across the consecutive passes that reuse them
+            const uint64_t keep = l2_policy_evict_last();
             uint32_t it = 0;
             bool ok = true;
             for (int p = 0; p < passes && ok; p++) {
@@ -203,11 +207,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                     uint8_t* st = smem + s * kStage;
                     const uint32_t fb = saddr(&full[s]);
                     const int kx = c * Kc + kb * kKPerStage;
-                    tma_load_3d(saddr(st), &tmU, fb, kx, I * 128, t);                            // U_r slice t
-                    tma_load_3d(saddr(st + kATile), &tmU, fb, kx, I * 128, kOzSlices + t);       // U_i slice t
-                    tma_load_3d(saddr(st + 2 * kATile), &tmP, fb, kx, J * 128, u);               // P_r slice u
+                    tma_load_3d_hint(saddr(st), &tmU, fb, kx, I * 128, t, keep);                       // U_r slice t
+                    tma_load_3d_hint(saddr(st + kATile), &tmU, fb, kx, I * 128, kOzSlices + t, keep);  // U_i slice t
+                    tma_load_3d(saddr(st + 2 * kATile), &tmP, fb, kx, J * 128, u);                     // P_r slice u
                     tma_load_3d(saddr(st + 2 * kATile + 128 * kRowBytes), &tmP, fb, kx, J * 128,
-                                kOzSlices + u);                                                  // P_i slice u
+                                kOzSlices + u);                                                        // P_i slice u
                 }
             }
             if (*abort) {
@@ -263,8 +267,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             int t, u;
             oz_pair(p / chunks, t, u);
-            // pairs run by level: levels 0-3 are the first 10 pairs, 4-8 the rest
-            oz_epilogue(tmem, warp, lane, I, J, ep, t + u, p == 0, p == 10 * chunks, p == passes - 1);
+            // first pass into hi: pair (0, 0); into lo: pair (0, 4); the last pass, pair (8, 0), is into lo
+            oz_epilogue(tmem, warp, lane, I, J, ep, t + u, p == 0, p == 4 * chunks, p == passes - 1);
             tc_fence_before();
             asm volatile("bar.sync 1, 128;" ::: "memory");   // all four epilogue warps have read TMEM
             if (threadIdx.x == 0)
