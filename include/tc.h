@@ -329,15 +329,18 @@ TC_API tc_status tc_lindblad_evolve(const tc_params* params, double kappa, doubl
  * checkpoints stored every `ckpt_every` steps.
  *  rho0   : device, N*N c128 (Hermitian, read only).
  *  U      : device, N*N c128, e^{-iH dt} of the same params and dt.
+ *  precision: TC_FP64 (DMMA products) or TC_FP64_OZAKI (the per-step
+ *           products emulated at FP64 accuracy on the BF16 tensor cores;
+ *           n >= 7).
  *  O_diag : device, N doubles.
  *  grad   : host, n + 2 doubles, written when the call returns (this call
  *           synchronises `stream`).
  *  loss   : host, 1 double (may be NULL), L at the final time.
- *  work   : device, >= tc_workspace_size(n, TC_FP64, TC_OP_BACKWARD, steps,
+ *  work   : device, >= tc_workspace_size(n, precision, TC_OP_BACKWARD, steps,
  *           ckpt_every).
  *  Errors: TC_ERR_INVALID_ARG, TC_ERR_WORKSPACE, TC_ERR_CUDA, TC_ERR_NUMERIC. */
 TC_API tc_status tc_evolve_backward(const tc_params* params, double dt, int steps,
-                                    const void* rho0, const void* U, int ckpt_every,
+                                    const void* rho0, const void* U, int ckpt_every, int precision,
                                     const double* O_diag, double* grad, double* loss,
                                     void* work, size_t work_bytes, void* stream);
 

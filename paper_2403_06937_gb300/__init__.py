@@ -216,7 +216,8 @@ def evolve_host(U: torch.Tensor, rho_host: torch.Tensor, n: int, steps: int, pre
 
 
 def evolve_backward(params: Params, dt: float, steps: int, rho0: torch.Tensor, U: torch.Tensor,
-                    O_diag: torch.Tensor, ckpt_every: int = 20, stream=None, work: Optional[torch.Tensor] = None):
+                    O_diag: torch.Tensor, ckpt_every: int = 20, precision="fp64", stream=None,
+                    work: Optional[torch.Tensor] = None):
     """tc_evolve_backward: (grad, loss) of L = Tr(diag(O) rho_K) w.r.t. (g_1..g_n, omega_a, omega_c).
 
     grad is a float64 numpy-convertible CPU tensor of n + 2 values; the call blocks.
@@ -226,14 +227,15 @@ def evolve_backward(params: Params, dt: float, steps: int, rho0: torch.Tensor, U
     assert rho0.dtype == torch.complex128 and rho0.is_contiguous() and rho0.shape == (N, N)
     assert U.dtype == torch.complex128 and U.is_contiguous() and U.shape == (N, N)
     assert O_diag.dtype == torch.float64 and O_diag.is_cuda and O_diag.numel() == N
-    need = workspace_size(n, TC_FP64, TC_OP_BACKWARD, steps, ckpt_every)
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    need = workspace_size(n, prec, TC_OP_BACKWARD, steps, ckpt_every)
     if work is None or work.numel() < need:
         work = _work(need, rho0.device)
     grad = (ctypes.c_double * (n + 2))()
     loss = ctypes.c_double()
     p = params.c()
     _abi.call("tc_evolve_backward", ctypes.byref(p), float(dt), int(steps), _ptr(rho0), _ptr(U), int(ckpt_every),
-              _ptr(O_diag.contiguous()), grad, ctypes.byref(loss), _ptr(work), work.numel(),
+              prec, _ptr(O_diag.contiguous()), grad, ctypes.byref(loss), _ptr(work), work.numel(),
               ctypes.c_void_p(_stream(stream)))
     return torch.tensor(list(grad), dtype=torch.float64), float(loss.value)
 

@@ -60,7 +60,7 @@ SIGNATURES = {
     "tc_evolve": (I, [VP, VP, I, I, I, I, ctypes.POINTER(tc_params), VP, VP, SZ, VP]),
     "tc_observables": (I, [VP, I, ctypes.POINTER(tc_params), VP, VP, SZ, VP]),
     "tc_observables_noalloc": (I, [VP, I, ctypes.POINTER(tc_params), VP, VP]),
-    "tc_evolve_backward": (I, [ctypes.POINTER(tc_params), D, I, VP, VP, I, VP, DP, DP, VP, SZ, VP]),
+    "tc_evolve_backward": (I, [ctypes.POINTER(tc_params), D, I, VP, VP, I, I, VP, DP, DP, VP, SZ, VP]),
     "tc_evolve_host": (I, [VP, VP, I, I, I, I, ctypes.POINTER(tc_params), VP, VP, SZ, VP]),
     "tc_autotune": (I, [I, I, VP, SZ, VP, ctypes.POINTER(I)]),
     "tc_autotune_lookup": (I, [I, I, ctypes.POINTER(I)]),

@@ -17,9 +17,15 @@
 //     e^{A'} = sum T_k,  L(A', E) = sum F_k,   E = M / 2^s,
 // then s squarings D <- X D + D X, X <- X X (chain rule of X^2), and the
 // shift back: L(A, M) = e^{-i mu dt} L(A', M).
+//
+// precision TC_FP64_OZAKI runs the per-step products (the forward steps, the
+// adjoint steps and W += rho_k Lambda_k) as FP64-accurate products on the
+// BF16 tensor cores (cgemm_oz.cu); the few products of M and of the Frechet
+// derivative stay on the DMMA GEMM.
 #include <cmath>
 #include <vector>
 
+#include "cgemm_oz.cuh"
 #include "paths.cuh"
 
 namespace tc {
@@ -204,10 +210,48 @@ tc_status minus_i_times(int N, const double* Bs, CM X, CM Y, CM Q, cudaStream_t 
     return TC_OK;
 }
 
+// Emulated-FP64 products: slices of U and conj(U) (A operands), of the
+// current B operand and of rho_k (A operand of the W product).
+struct OzBufs {
+    OzMat U, Uc, B, A2;
+    double* yr;
+    double* yi;
+    long long* lo_r;
+    long long* lo_i;
+    int group;
+};
+
+size_t oz_backward_extra(int n) {
+    const size_t N = (size_t)1 << n;
+    return 4 * oz_mat_bytes((int)N) + 4 * round256(N * N * sizeof(double)) + 256;
+}
+
+// P <- U' P U'^dag with U' = U (or conj U for the adjoint step), emulated FP64
+tc_status step_oz(int N, OzBufs& z, bool adjoint, CM P, CM X, cudaStream_t s) {
+    const OzMat& A = adjoint ? z.Uc : z.U;
+    TC_TRY(oz_mat_load(z.B, P.r, P.i, false, false, N, (size_t)N, s));
+    TC_TRY(oz_product(0, A, z.B, OzOut{X.r, X.i, z.lo_r, z.lo_i}, z.group, s));       // X = U' P^H = U' P
+    TC_TRY(oz_mat_load(z.B, X.r, X.i, false, false, N, (size_t)N, s));
+    return oz_product(1, A, z.B, OzOut{P.r, P.i, z.lo_r, z.lo_i}, z.group, s);        // P' = U' X^H
+}
+
+// W += rho Lambda = rho Lambda^H (Lambda Hermitian), emulated FP64
+tc_status w_accumulate_oz(int N, OzBufs& z, CM rho, CM L, CM W, bool init, cudaStream_t s) {
+    TC_TRY(oz_mat_load(z.A2, rho.r, rho.i, false, false, N, (size_t)N, s));
+    TC_TRY(oz_mat_load(z.B, L.r, L.i, false, false, N, (size_t)N, s));
+    if (init) return oz_product(0, z.A2, z.B, OzOut{W.r, W.i, z.lo_r, z.lo_i}, z.group, s);
+    TC_TRY(oz_product(0, z.A2, z.B, OzOut{z.yr, z.yi, z.lo_r, z.lo_i}, z.group, s));
+    const size_t NN = (size_t)N * N;
+    axpby_kernel<<<grid_for(NN), 256, 0, s>>>(1.0, W.r, W.i, 1.0, z.yr, z.yi, W.r, W.i, NN);
+    TC_LAUNCH_CHECK();
+    return TC_OK;
+}
+
 }  // namespace
 
-size_t backward_bytes(int n, int steps, int ckpt_every) {
+size_t backward_bytes(int n, int steps, int ckpt_every, int precision) {
     if (n < 1 || n > kMaxAtoms || steps < 1 || ckpt_every < 1) return 0;
+    if (precision == TC_FP64_OZAKI) return backward_bytes(n, steps, ckpt_every, TC_FP64) + oz_backward_extra(n);
     const int nck = (steps + ckpt_every - 1) / ckpt_every;
     const int c = ckpt_every < steps ? ckpt_every : steps;
     // U, Lambda, X, W, seg0 + checkpoints + segment + Frechet (T, F, Tn, Fn, P, Q) + B + small
@@ -219,18 +263,23 @@ size_t backward_bytes(int n, int steps, int ckpt_every) {
 using namespace tc;
 
 extern "C" TC_API tc_status tc_evolve_backward(const tc_params* params, double dt, int steps, const void* rho0,
-                                               const void* U, int ckpt_every, const double* O_diag, double* grad,
-                                               double* loss, void* work, size_t work_bytes, void* stream) {
+                                               const void* U, int ckpt_every, int precision, const double* O_diag,
+                                               double* grad, double* loss, void* work, size_t work_bytes,
+                                               void* stream) {
     Model m;
     TC_TRY(make_model(params, &m));
     const int n = m.n;
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(TC_ERR_INVALID_ARG, "dt must be finite and > 0");
     if (steps < 1) return fail(TC_ERR_INVALID_ARG, "steps must be >= 1");
     if (ckpt_every < 1) return fail(TC_ERR_INVALID_ARG, "ckpt_every must be >= 1");
+    if (precision != TC_FP64 && precision != TC_FP64_OZAKI)
+        return fail(TC_ERR_INVALID_ARG, "backward: precision must be TC_FP64 or TC_FP64_OZAKI");
+    if (precision == TC_FP64_OZAKI && n < 7)
+        return fail(TC_ERR_INVALID_ARG, "backward: the emulated form needs n >= 7 (dimension a multiple of 128)");
     if (!rho0 || !U || !O_diag || !grad) return fail(TC_ERR_INVALID_ARG, "null pointer");
     if ((reinterpret_cast<uintptr_t>(rho0) | reinterpret_cast<uintptr_t>(U)) & 15u)
         return fail(TC_ERR_INVALID_ARG, "rho0 and U must be 16-byte aligned");
-    const size_t need = backward_bytes(n, steps, ckpt_every);
+    const size_t need = backward_bytes(n, steps, ckpt_every, precision);
     if (!work) return fail(TC_ERR_WORKSPACE, "work is NULL (need %zu bytes)", need);
     if (reinterpret_cast<uintptr_t>(work) & 255u) return fail(TC_ERR_WORKSPACE, "work is not 256-byte aligned");
     if (work_bytes < need) return fail(TC_ERR_WORKSPACE, "work has %zu bytes, need %zu", work_bytes, need);
@@ -262,13 +311,30 @@ extern "C" TC_API tc_status tc_evolve_backward(const tc_params* params, double d
     b.B = ar.take<double>(NN);
     b.small = ar.take<double>(2 * (size_t)N + 64);
     if (!b.small) return fail(TC_ERR_WORKSPACE, "backward: workspace too small");
+    const bool oz = precision == TC_FP64_OZAKI;
+    OzBufs z{};
+    if (oz) {
+        TC_TRY(oz_mat_init(z.U, ar, N));
+        TC_TRY(oz_mat_init(z.Uc, ar, N));
+        TC_TRY(oz_mat_init(z.B, ar, N));
+        TC_TRY(oz_mat_init(z.A2, ar, N));
+        z.yr = ar.take<double>(NN);
+        z.yi = ar.take<double>(NN);
+        z.lo_r = ar.take<long long>(NN);
+        z.lo_i = ar.take<long long>(NN);
+        if (!z.lo_i) return fail(TC_ERR_WORKSPACE, "backward: workspace too small");
+        z.group = tune_lookup(n, TC_BF16X3).tc_group;
+        TC_TRY(oz_mat_load(z.U, static_cast<const double*>(U), nullptr, true, false, N, (size_t)N, s));
+        TC_TRY(oz_mat_load(z.Uc, static_cast<const double*>(U), nullptr, true, true, N, (size_t)N, s));
+    }
+    auto fwd_step = [&](CM P) -> tc_status { return oz ? step_oz(N, z, false, P, b.X, s) : step(N, b.U, P, b.X, 0, s); };
 
     // ---------------------------------------------------------------- forward
     TC_TRY(launch_split_c128(static_cast<const double*>(U), b.U.r, b.U.i, NN, s));
     TC_TRY(launch_split_c128(static_cast<const double*>(rho0), ck[0].r, ck[0].i, NN, s));
     TC_TRY(copy_cm(ck[0], b.seg0, NN, s));   // seg0 = running rho
     for (int k = 1; k <= steps; k++) {
-        TC_TRY(step(N, b.U, b.seg0, b.X, 0, s));
+        TC_TRY(fwd_step(b.seg0));
         if (k < steps && k % ckpt_every == 0) TC_TRY(copy_cm(b.seg0, ck[k / ckpt_every], NN, s));
     }
     // loss from rho_K (in seg0)
@@ -286,13 +352,17 @@ extern "C" TC_API tc_status tc_evolve_backward(const tc_params* params, double d
         TC_TRY(copy_cm(ck[j], seg[0], NN, s));
         for (int k = k0 + 1; k < k1; k++) {
             TC_TRY(copy_cm(seg[k - 1 - k0], seg[k - k0], NN, s));
-            TC_TRY(step(N, b.U, seg[k - k0], b.X, 0, s));
+            TC_TRY(fwd_step(seg[k - k0]));
         }
         for (int k = k1 - 1; k >= k0; k--) {
-            // Lambda_k = U^dag Lambda_{k+1} U  (the step with conj(U))
-            TC_TRY(step(N, b.U, b.L, b.X, 1, s));
-            // W += rho_k Lambda_k
-            TC_TRY(gemm_c(N, seg[k - k0], 0, b.L, 0, b.W, 1.0, w_init ? 1.0 : 0.0, 0, s));
+            // Lambda_k = U^dag Lambda_{k+1} U  (the step with conj(U)); W += rho_k Lambda_k
+            if (oz) {
+                TC_TRY(step_oz(N, z, true, b.L, b.X, s));
+                TC_TRY(w_accumulate_oz(N, z, seg[k - k0], b.L, b.W, !w_init, s));
+            } else {
+                TC_TRY(step(N, b.U, b.L, b.X, 1, s));
+                TC_TRY(gemm_c(N, seg[k - k0], 0, b.L, 0, b.W, 1.0, w_init ? 1.0 : 0.0, 0, s));
+            }
             w_init = true;
         }
     }

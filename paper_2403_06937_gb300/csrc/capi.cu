@@ -356,7 +356,7 @@ TC_API size_t tc_workspace_size(int n, int precision, int ops, int steps, int ck
     if (ops & TC_OP_EXPM_MODEL) upd(expm_model_bytes(n));
     if (ops & TC_OP_LINDBLAD) upd(lindblad_bytes(n, precision));
     if (ops & TC_OP_EVOLVE_HOST) upd(evolve_bytes(n, precision) + evolve_host_extra(n, steps));
-    if (ops & TC_OP_BACKWARD) upd(backward_bytes(n, steps, ckpt_every));
+    if (ops & TC_OP_BACKWARD) upd(backward_bytes(n, steps, ckpt_every, precision));
     return need;
 }
 

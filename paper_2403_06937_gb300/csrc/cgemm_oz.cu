@@ -30,6 +30,7 @@
 
 #include "cgemm_dev.cuh"
 #include "cgemm_oz.cuh"
+#include "cgemm_tc.cuh"
 
 namespace tc {
 namespace {
@@ -294,7 +295,7 @@ constexpr int kSmem = kStages * kStage + 1024 /*align*/ + 256 /*barriers*/;
 // elements); else planar FP64 planes re, im with row stride ld.
 template <bool INTERLEAVED>
 __global__ void oz_slice_kernel(const double* __restrict__ re, const double* __restrict__ im, int N, size_t ld,
-                                int Np, __nv_bfloat16* __restrict__ slices, int* __restrict__ ex) {
+                                int Np, double im_sign, __nv_bfloat16* __restrict__ slices, int* __restrict__ ex) {
     const int warps = (int)(gridDim.x * blockDim.x) >> 5;
     const int lane = threadIdx.x & 31;
     const size_t plane = (size_t)Np * Np;
@@ -314,7 +315,7 @@ __global__ void oz_slice_kernel(const double* __restrict__ re, const double* __r
             }
         };
         double m = 0.0;
-        for (int c = lane; c < N; c += 32) {
+        for (int c = lane; c < (r < N ? N : 0); c += 32) {
             double xr, xi;
             at(c, xr, xi);
             m = fmax(m, fmax(fabs(xr), fabs(xi)));
@@ -330,6 +331,7 @@ __global__ void oz_slice_kernel(const double* __restrict__ re, const double* __r
         for (int c = lane; c < Np; c += 32) {
             double xv[2];
             at(c, xv[0], xv[1]);
+            xv[1] *= im_sign;
 #pragma unroll
             for (int part = 0; part < 2; part++) {
                 long long v = __double2ll_rn(xv[part] * sc1 * sc2);   // |v| < 2^53
@@ -389,14 +391,15 @@ tc_status launch(const CUtensorMap& tmU, const CUtensorMap& tmP, const OzEpi& ep
 
 }  // namespace
 
-tc_status oz_slice(const double* re, const double* im, bool interleaved, int N, size_t ld, int Np, void* slices,
-                   int* ex, cudaStream_t s) {
+tc_status oz_slice(const double* re, const double* im, bool interleaved, bool conj, int N, size_t ld, int Np,
+                   void* slices, int* ex, cudaStream_t s) {
     const unsigned blocks = (unsigned)(((size_t)Np * 32 + 255) / 256);
     const unsigned g = blocks < grid_for((size_t)Np * 32) ? blocks : grid_for((size_t)Np * 32);
+    const double sign = conj ? -1.0 : 1.0;
     if (interleaved)
-        oz_slice_kernel<true><<<g, 256, 0, s>>>(re, im, N, ld, Np, static_cast<__nv_bfloat16*>(slices), ex);
+        oz_slice_kernel<true><<<g, 256, 0, s>>>(re, im, N, ld, Np, sign, static_cast<__nv_bfloat16*>(slices), ex);
     else
-        oz_slice_kernel<false><<<g, 256, 0, s>>>(re, im, N, ld, Np, static_cast<__nv_bfloat16*>(slices), ex);
+        oz_slice_kernel<false><<<g, 256, 0, s>>>(re, im, N, ld, Np, sign, static_cast<__nv_bfloat16*>(slices), ex);
     TC_LAUNCH_CHECK();
     return TC_OK;
 }
@@ -418,5 +421,37 @@ tc_status cgemm_oz(int mode, const CUtensorMap& tmU, const CUtensorMap& tmP, con
 }
 
 size_t oz_slice_bytes(int Np) { return round256((size_t)2 * kOzSlices * Np * Np * sizeof(__nv_bfloat16)); }
+
+size_t oz_mat_bytes(int Np) { return oz_slice_bytes(Np) + round256((size_t)Np * sizeof(int)); }
+
+tc_status oz_mat_init(OzMat& m, Arena& ar, int Np) {
+    m.Np = Np;
+    m.slices = ar.take<uint8_t>(oz_slice_bytes(Np));
+    m.ex = ar.take<int>((size_t)Np);
+    if (!m.ex) return fail(TC_ERR_WORKSPACE, "FP64 emulation: workspace too small");
+    return make_part_map(&m.map, m.slices, Np, 2 * kOzSlices, TC_BF16X3);
+}
+
+tc_status oz_mat_load(OzMat& m, const double* re, const double* im, bool interleaved, bool conj, int N, size_t ld,
+                      cudaStream_t s) {
+    return oz_slice(re, im, interleaved, conj, N, ld, m.Np, m.slices, m.ex, s);
+}
+
+tc_status oz_product(int mode, const OzMat& A, const OzMat& B, const OzOut& out, int group, cudaStream_t s) {
+    OzEpi ep{};
+    ep.Np = A.Np;
+    ep.tiles = A.Np / 128;
+    ep.group = group;
+    ep.eU = A.ex;
+    ep.eP = B.ex;
+    ep.yr = out.yr;
+    ep.yi = out.yi;
+    ep.lo_r = out.lo_r;
+    ep.lo_i = out.lo_i;
+    ep.status = device_status_word();
+    TC_TRY(cgemm_oz(mode, A.map, B.map, ep, s));
+    if (mode == 1) TC_TRY(oz_mirror(out.yr, out.yi, A.Np, s));
+    return TC_OK;
+}
 
 }  // namespace tc

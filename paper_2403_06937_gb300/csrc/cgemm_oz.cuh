@@ -26,12 +26,34 @@ struct OzEpi {
 };
 
 // Slices [2 * kOzSlices][Np][Np] (BF16 digits: re slices, then im slices) and
-// row exponents ex[Np] of the N x N matrix (zero-padded to Np).
-tc_status oz_slice(const double* re, const double* im, bool interleaved, int N, size_t ld, int Np, void* slices,
-                   int* ex, cudaStream_t s);
+// row exponents ex[Np] of the N x N matrix (zero-padded to Np); conj negates
+// the imaginary part.
+tc_status oz_slice(const double* re, const double* im, bool interleaved, bool conj, int N, size_t ld, int Np,
+                   void* slices, int* ex, cudaStream_t s);
 size_t oz_slice_bytes(int Np);
 // Y = U P^H (mode 0: all tiles; mode 1: block-lower tiles, then oz_mirror)
 tc_status cgemm_oz(int mode, const CUtensorMap& tmU, const CUtensorMap& tmP, const OzEpi& ep, cudaStream_t s);
 tc_status oz_mirror(double* yr, double* yi, int Np, cudaStream_t s);
+
+// One operand of the emulated product: its digit slices, row exponents and
+// TMA map (row r of the operand = row r of A, or row r of B in A B^H).
+struct OzMat {
+    void* slices;
+    int* ex;
+    CUtensorMap map;
+    int Np;
+};
+struct OzOut {
+    double* yr;        // FP64 planes of the result, row stride Np
+    double* yi;
+    long long* lo_r;   // int64 scratch planes [Np][Np]
+    long long* lo_i;
+};
+size_t oz_mat_bytes(int Np);
+tc_status oz_mat_init(OzMat& m, Arena& ar, int Np);
+tc_status oz_mat_load(OzMat& m, const double* re, const double* im, bool interleaved, bool conj, int N, size_t ld,
+                      cudaStream_t s);
+// Y = A B^H at FP64 accuracy; mode 1 (Hermitian result): block-lower tiles and the mirror.
+tc_status oz_product(int mode, const OzMat& A, const OzMat& B, const OzOut& out, int group, cudaStream_t s);
 
 }  // namespace tc

@@ -83,8 +83,7 @@ int padded_dim(int n) { return (1 << n) < 128 ? 128 : (1 << n); }
 
 size_t evolve_oz_bytes(int n) {
     const size_t Np = (size_t)padded_dim(n);
-    return 2 * oz_slice_bytes((int)Np) + 6 * round256(Np * Np * sizeof(double)) + 2 * round256(Np * sizeof(int)) +
-           observables_scratch_bytes(n) + 512;
+    return 2 * oz_mat_bytes((int)Np) + 6 * round256(Np * Np * sizeof(double)) + observables_scratch_bytes(n) + 512;
 }
 
 tc_status evolve_oz(const double* U, double* rho, int n, int steps, int renorm_every, const Model* m, double* obs,
@@ -92,52 +91,33 @@ tc_status evolve_oz(const double* U, double* rho, int n, int steps, int renorm_e
     const int N = 1 << n;
     const int Np = padded_dim(n);
     const size_t NN = (size_t)Np * Np;
-    void* Us = ar.take<uint8_t>(oz_slice_bytes(Np));
-    void* Ps = ar.take<uint8_t>(oz_slice_bytes(Np));
+    OzMat Us{}, Ps{};
+    TC_TRY(oz_mat_init(Us, ar, Np));
+    TC_TRY(oz_mat_init(Ps, ar, Np));
     double* Rr = ar.take<double>(NN);
     double* Ri = ar.take<double>(NN);
     double* Xr = ar.take<double>(NN);
     double* Xi = ar.take<double>(NN);
     long long* Lr = ar.take<long long>(NN);   // low-level integer sums of the products
     long long* Li = ar.take<long long>(NN);
-    int* eU = ar.take<int>((size_t)Np);
-    int* eP = ar.take<int>((size_t)Np);
     double* scratch = ar.take<double>(observables_scratch_bytes(n) / sizeof(double));
     if (!scratch) return fail(TC_ERR_WORKSPACE, "evolve: workspace too small");
-
-    CUtensorMap tmU, tmP;
-    TC_TRY(make_part_map(&tmU, Us, Np, 2 * kOzSlices, TC_BF16X3));
-    TC_TRY(make_part_map(&tmP, Ps, Np, 2 * kOzSlices, TC_BF16X3));
-    const TuneChoice tune = tune_lookup(n, TC_BF16X3);
-    OzEpi e1{};                    // X = U rho^H
-    e1.Np = Np;
-    e1.tiles = Np / 128;
-    e1.group = tune.tc_group;
-    e1.eU = eU;
-    e1.eP = eP;
-    e1.yr = Xr;
-    e1.yi = Xi;
-    e1.lo_r = Lr;
-    e1.lo_i = Li;
-    e1.status = device_status_word();
-    OzEpi e2 = e1;                 // rho' = U X^H
-    e2.yr = Rr;
-    e2.yi = Ri;
+    const int group = tune_lookup(n, TC_BF16X3).tc_group;
+    const OzOut X{Xr, Xi, Lr, Li}, R{Rr, Ri, Lr, Li};
 
     const int stride = TC_OBS_STRIDE(n);
     const double N3 = (double)N * N * N;
     auto one_step = [&](int k, cudaStream_t cs) -> tc_status {
-        TC_TRY(oz_slice(Rr, Ri, false, N, (size_t)Np, Np, Ps, eP, cs));
+        TC_TRY(oz_mat_load(Ps, Rr, Ri, false, false, N, (size_t)Np, cs));
         {
-            ProductTimer t(8.0 * N3 * kOzPairs, cs);
-            TC_TRY(cgemm_oz(0, tmU, tmP, e1, cs));
+            ProductTimer t(8.0 * N3 * kOzPairs, cs);   // X = U rho^H
+            TC_TRY(oz_product(0, Us, Ps, X, group, cs));
         }
-        TC_TRY(oz_slice(Xr, Xi, false, N, (size_t)Np, Np, Ps, eP, cs));
+        TC_TRY(oz_mat_load(Ps, Xr, Xi, false, false, N, (size_t)Np, cs));
         {
-            ProductTimer t(4.0 * N3 * kOzPairs, cs);
-            TC_TRY(cgemm_oz(1, tmU, tmP, e2, cs));
+            ProductTimer t(4.0 * N3 * kOzPairs, cs);   // rho' = U X^H, Hermitian half + mirror
+            TC_TRY(oz_product(1, Us, Ps, R, group, cs));
         }
-        TC_TRY(oz_mirror(Rr, Ri, Np, cs));
         if (renorm_every > 0 && k % renorm_every == 0) {
             trace_pad_kernel<<<1, 1024, 0, cs>>>(Rr, N, Np, scratch);
             TC_LAUNCH_CHECK();
@@ -149,7 +129,7 @@ tc_status evolve_oz(const double* U, double* rho, int n, int steps, int renorm_e
         return TC_OK;
     };
     auto first = [&](cudaStream_t cs) -> tc_status {
-        TC_TRY(oz_slice(U, nullptr, true, N, (size_t)N, Np, Us, eU, cs));
+        TC_TRY(oz_mat_load(Us, U, nullptr, true, false, N, (size_t)N, cs));
         split_pad_kernel<<<grid_for(NN), 256, 0, cs>>>(reinterpret_cast<const double2*>(rho), N, Np, Rr, Ri);
         TC_LAUNCH_CHECK();
         if (obs) TC_TRY(launch_observables(kRhoPlanarF64, Rr, Ri, m, n, obs, scratch, cs, (size_t)Np));

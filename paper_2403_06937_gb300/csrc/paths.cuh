@@ -47,6 +47,6 @@ tc_status evolve_lowp(const double* U, double* rho, int n, int steps, int precis
 size_t lindblad_bytes(int n, int precision);
 
 // Reverse-mode gradient.
-size_t backward_bytes(int n, int steps, int ckpt_every);
+size_t backward_bytes(int n, int steps, int ckpt_every, int precision);
 
 }  // namespace tc

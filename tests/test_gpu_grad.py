@@ -30,7 +30,7 @@ def tc():
     return tc
 
 
-def _gpu_grad(tc, n, g, wa, wc, dt, steps, ckpt, atom, psi0=None, coupling=0):
+def _gpu_grad(tc, n, g, wa, wc, dt, steps, ckpt, atom, psi0=None, coupling=0, precision="fp64"):
     p = tc.Params(n, list(map(float, g)), wa, wc, coupling)
     U = tc.expm(tc.build_hamiltonian(p), n, dt)
     N = 1 << n
@@ -40,7 +40,7 @@ def _gpu_grad(tc, n, g, wa, wc, dt, steps, ckpt, atom, psi0=None, coupling=0):
         rho0 = torch.from_numpy(np.outer(psi0, psi0.conj())).cuda()
     s = np.arange(N)
     O = torch.from_numpy(((s >> (n - atom)) & 1).astype(np.float64)).cuda()
-    grad, loss = tc.evolve_backward(p, dt, steps, rho0, U, O, ckpt_every=ckpt)
+    grad, loss = tc.evolve_backward(p, dt, steps, rho0, U, O, ckpt_every=ckpt, precision=precision)
     return grad.numpy(), loss
 
 
@@ -156,3 +156,33 @@ def test_gradient_workload_n11(tc, oracle):
     scale = max(abs(v) for v in fd.values())
     for j, v in fd.items():
         assert abs(grad[j] - v) <= 1e-6 * max(abs(v), scale), (j, grad[j], v)
+
+
+@pytest.mark.parametrize("n,steps,ckpt", [(7, 12, 5), (9, 10, 4)])
+def test_emulated_fp64_products_match_oracle_tangent(tc, oracle, n, steps, ckpt):
+    """The per-step products on the BF16 tensor cores (exact digit slices): the same 1e-9 bound
+    against the oracle tangent as the DMMA products."""
+    g = W.draw_couplings(n, 70 + n) * 8
+    wa, wc, dt = 1.03, 1.0, 0.3
+    grad, loss = _gpu_grad(tc, n, g, wa, wc, dt, steps, ckpt, atom=2, precision="ozaki")
+    O = oracle.atom_population_operator(n, 2)
+    ref = oracle.grad_forward(n, g, wa, wc, dt, steps, W.all_excited_state(n), O)
+    assert np.max(np.abs(grad - ref)) <= 1e-9 * np.max(np.abs(ref))
+    g64, l64 = _gpu_grad(tc, n, g, wa, wc, dt, steps, ckpt, atom=2)
+    assert abs(loss - l64) < 1e-13
+
+
+def test_emulated_fp64_gradient_workload_n11(tc, oracle):
+    """The n = 11 gradient workload with the emulated products, against the oracle tangent."""
+    cfg = W.config_n11_grad()
+    grad, loss = _gpu_grad(tc, cfg.n, cfg.g, cfg.omega_a, cfg.omega_c, cfg.dt, cfg.steps, cfg.ckpt_every,
+                           atom=cfg.loss_atom, precision="ozaki")
+    n = cfg.n
+    O = oracle.atom_population_operator(n, cfg.loss_atom)
+    ref = oracle.grad_forward(n, cfg.g, cfg.omega_a, cfg.omega_c, cfg.dt, cfg.steps, W.all_excited_state(n), O)
+    assert np.max(np.abs(grad - ref)) <= 1e-7 * np.max(np.abs(ref))
+
+
+def test_emulated_backward_rejects_small_n(tc):
+    with pytest.raises(tc.TCError):
+        _gpu_grad(tc, 5, W.draw_couplings(5, 1), 1.0, 1.0, 0.1, 3, 2, atom=1, precision="ozaki")
