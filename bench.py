@@ -465,7 +465,8 @@ def run_batch(a):
     line = {"metric": "batched evolution: aggregate system-steps/s (64 systems, n=6..12)", "value": value,
             "unit": "system-steps/s", "n_gpus": 1, "steps": steps, "warmup": 1, "ms_per_step": 1e3 * tb / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp64": "f64", "bf16x3": "bf16", "tf32": "tf32", "tf32x3": "tf32"}[prec], "data": "synthetic",
+            "dtype": {"fp64": "f64", "bf16x3": "bf16", "tf32": "tf32", "tf32x3": "tf32", "ozaki": "bf16"}[prec],
+            "data": "synthetic",
             "config": {"workload": "64 systems, n ~ U{6..12} seed 2, own g_i ~ U[0.005,0.015], dt=0.05, %d steps"
                        % steps, "precision": prec, "ns": [c.n for c in cfgs]},
             "credited_tflops": credited / tb / 1e12,
@@ -559,14 +560,15 @@ def run_open(a):
     o = obs.cpu().numpy()
     credited = sum(12.0 * d ** 3 for d in lay.dims)
     peaks, peak_src = _measured_peaks()
-    peak = peaks["bf16_tflops_sustained"] if prec == "bf16x3" else (
+    peak = peaks["bf16_tflops_sustained"] if prec in ("bf16x3", "ozaki") else (
         peaks["bf16_tflops_sustained"] / 2 if prec in ("tf32", "tf32x3") else _fp64_peak_live(torch))
     achieved = kflops / (kms * 1e-3) / 1e12 if kms > 0 else 0.0
     value = a.steps / (ms * 1e-3)
     line = {"metric": "open-system split steps/s (Eq. 5 with photon leakage)", "value": value, "unit": "steps/s",
             "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms / a.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp64": "f64", "bf16x3": "bf16", "tf32": "tf32", "tf32x3": "tf32"}[prec], "data": "synthetic",
+            "dtype": {"fp64": "f64", "bf16x3": "bf16", "tf32": "tf32", "tf32x3": "tf32", "ozaki": "bf16"}[prec],
+            "data": "synthetic",
             "config": {"workload": cfg.description, "precision": prec, "blocks": lay.dims,
                        "state_elements": lay.total, "setup_s": t_setup,
                        "l2": "inputs larger than L2 (packed state %d MiB in complex128)" % (16 * lay.total >> 20)},

@@ -75,8 +75,8 @@ typedef enum tc_status {
  *              products with t + u <= 8 accumulate exactly in FP32 (sums
  *              stay below 2^24 for K <= 16384) and are scaled and summed in
  *              FP64.  About 2^-48 of the row and column scales per product;
- *              rho stored in FP64.  Single systems only (tc_evolve,
- *              tc_evolve_host).
+ *              rho stored in FP64.  tc_evolve, tc_evolve_host,
+ *              tc_lindblad_evolve and tc_evolve_backward (not the batch).
  * In the BF16/TF32 forms U is computed in FP64 and rho is stored in FP32
  * between steps. */
 typedef enum tc_precision {
@@ -306,7 +306,7 @@ TC_API tc_status tc_lindblad_propagators(const tc_params* params, double dt, voi
  * tensor cores (split forms, as tc_evolve: one persistent launch over the
  * tiles of every block per product, rho stored FP32 between steps).
  *  U, rho      : device packed complex128; rho in/out (Hermitian blocks).
- *  precision   : TC_FP64, TC_BF16X3, TC_TF32, TC_TF32X3.
+ *  precision   : TC_FP64, TC_BF16X3, TC_TF32, TC_TF32X3, TC_FP64_OZAKI.
  *  renorm_every: 0 = never; else after every renorm_every-th step all
  *                blocks are divided by the total trace (taken in FP64).
  *  obs         : device f64[(steps+1) * TC_OBS_STRIDE(n)] or NULL; the row

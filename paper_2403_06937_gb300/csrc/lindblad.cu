@@ -25,7 +25,9 @@
 // the tensor-core forms, one persistent launch over the tiles of every block
 // per product (the batch GEMM, blocks zero-padded to multiples of 128, U_k in
 // increment form, rho_k in FP32 planes plus operand parts), with D_tau then
-// reading and writing the FP32 planes and rebuilding the parts.
+// reading and writing the FP32 planes and rebuilding the parts.  The
+// FP64-emulated form (exact digit slices on the BF16 tensor cores) steps the
+// blocks one after another on FP64 planes padded to multiples of 128.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -33,6 +35,7 @@
 #include <vector>
 
 #include "cgemm_batch.cuh"
+#include "cgemm_oz.cuh"
 #include "cgemm_tc.cuh"
 #include "graph.cuh"
 #include "lowp.cuh"
@@ -634,14 +637,137 @@ tc_status evolve_lowp_blocks(const Layout& L, const Model& m, int precision, dou
     return fail(TC_ERR_INVALID_ARG, "unknown precision %d", precision);
 }
 
+// ---------------------------------------------------------------- FP64 emulated on BF16
+// packed interleaved blocks <-> FP64 planes padded to Np_k (grid y = block)
+__global__ void blocks_split_pad_kernel(BlockSet bs, BlockSet pk, const double2* __restrict__ src,
+                                        double* __restrict__ re, double* __restrict__ im) {
+    const int k = blockIdx.y;
+    const size_t d = (size_t)bs.d[k], ld = (size_t)bs.ld[k];
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < ld * ld; e += (size_t)gridDim.x * blockDim.x) {
+        const size_t i = e / ld, j = e % ld;
+        double2 v = make_double2(0.0, 0.0);
+        if (i < d && j < d) v = src[pk.off[k] + i * d + j];
+        re[bs.off[k] + e] = v.x;
+        im[bs.off[k] + e] = v.y;
+    }
+}
+
+__global__ void blocks_join_pad_kernel(BlockSet bs, BlockSet pk, const double* __restrict__ re,
+                                       const double* __restrict__ im, double2* __restrict__ dst) {
+    const int k = blockIdx.y;
+    const size_t d = (size_t)bs.d[k], ld = (size_t)bs.ld[k];
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < d * d; e += (size_t)gridDim.x * blockDim.x) {
+        const size_t i = e / d, j = e % d;
+        dst[pk.off[k] + e] = make_double2(re[bs.off[k] + i * ld + j], im[bs.off[k] + i * ld + j]);
+    }
+}
+
+size_t evolve_oz_bytes_blocks(int n) {
+    const Layout& L = layout_of(n);
+    const size_t PT = padded_total(L);
+    const int NpMax = padded(L.N);
+    size_t b = tables_bytes(n) + 2 * round256(PT * sizeof(double));
+    for (int k = 0; k <= n; k++) b += oz_mat_bytes(padded(L.dims[k]));   // U_k slices
+    b += oz_mat_bytes(NpMax);                                             // B operand slices
+    b += 4 * round256((size_t)NpMax * NpMax * sizeof(double));            // X planes, int64 scratch
+    return b + obs_scratch_bytes(L) + 256;
+}
+
+tc_status evolve_oz_blocks(const Layout& L, const Model& m, double kappa, double dt, const double* U, double* rho,
+                           int steps, int renorm_every, double* obs, Arena& ar, cudaStream_t s) {
+    const int n = L.n;
+    const size_t PT = padded_total(L);
+    const int NpMax = padded(L.N);
+    const size_t NN = (size_t)NpMax * NpMax;
+    Tables t{};
+    TC_TRY(take_tables(L, ar, &t));
+    double* Rr = ar.take<double>(PT);
+    double* Ri = ar.take<double>(PT);
+    std::vector<OzMat> Uk(n + 1);
+    for (int k = 0; k <= n; k++) TC_TRY(oz_mat_init(Uk[k], ar, padded(L.dims[k])));
+    OzMat Bmax{};
+    TC_TRY(oz_mat_init(Bmax, ar, NpMax));
+    double* Xr = ar.take<double>(NN);
+    double* Xi = ar.take<double>(NN);
+    long long* Lr = ar.take<long long>(NN);
+    long long* Li = ar.take<long long>(NN);
+    double* scratch = ar.take<double>(obs_scratch_bytes(L) / sizeof(double));
+    if (!scratch) return fail(TC_ERR_WORKSPACE, "lindblad evolve: workspace too small");
+    // the B operand slices seen at each block's padded size (one map per block)
+    std::vector<OzMat> Bk(n + 1);
+    for (int k = 0; k <= n; k++) {
+        Bk[k] = Bmax;
+        Bk[k].Np = padded(L.dims[k]);
+        TC_TRY(make_part_map(&Bk[k].map, Bmax.slices, Bk[k].Np, 2 * kOzSlices, TC_BF16X3));
+    }
+    const BlockSet bs = block_set(L, true);
+    const BlockSet pk = block_set(L, false);
+    const PartsSet none{};
+    const int stride = TC_OBS_STRIDE(n);
+    const bool damp = kappa > 0.0;
+    const int group = tune_lookup(n, TC_BF16X3).tc_group;
+
+    auto products = [&](cudaStream_t cs) -> tc_status {
+        for (int k = 0; k <= n; k++) {
+            const int d = L.dims[k], Np = bs.ld[k];
+            double* rr = Rr + bs.off[k];
+            double* ri = Ri + bs.off[k];
+            const double d3 = (double)d * d * d;
+            TC_TRY(oz_mat_load(Bk[k], rr, ri, false, false, d, (size_t)Np, cs));
+            {
+                ProductTimer pt(8.0 * d3 * kOzPairs, cs);   // X_k = U_k rho_k
+                TC_TRY(oz_product(0, Uk[k], Bk[k], OzOut{Xr, Xi, Lr, Li}, group, cs));
+            }
+            TC_TRY(oz_mat_load(Bk[k], Xr, Xi, false, false, d, (size_t)Np, cs));
+            {
+                ProductTimer pt(4.0 * d3 * kOzPairs, cs);   // rho_k = U_k X_k^H, Hermitian
+                TC_TRY(oz_product(1, Uk[k], Bk[k], OzOut{rr, ri, Lr, Li}, group, cs));
+            }
+        }
+        return TC_OK;
+    };
+    auto one_step = [&](int k, cudaStream_t cs) -> tc_status {
+        if (damp) TC_TRY((launch_damping<double, 0, 0>(L, bs, kappa, 0.5 * dt, t, Rr, Ri, none, cs)));
+        TC_TRY(products(cs));
+        if (damp) TC_TRY((launch_damping<double, 0, 0>(L, bs, kappa, 0.5 * dt, t, Rr, Ri, none, cs)));
+        if (renorm_every > 0 && k % renorm_every == 0)
+            TC_TRY((launch_block_renorm<double, 0, 0>(L, bs, Rr, Ri, none, scratch, cs)));
+        if (obs) TC_TRY(launch_block_observables<double>(L, bs, m, t, Rr, Ri, obs + (size_t)k * stride, scratch, cs));
+        return TC_OK;
+    };
+    auto first = [&](cudaStream_t cs) -> tc_status {
+        TC_TRY(launch_layout(L, t, cs));
+        for (int k = 0; k <= n; k++)
+            TC_TRY(oz_mat_load(Uk[k], U + 2 * L.off[k], nullptr, true, false, L.dims[k], (size_t)L.dims[k], cs));
+        dim3 g(256, (unsigned)(n + 1));
+        blocks_split_pad_kernel<<<g, 256, 0, cs>>>(bs, pk, reinterpret_cast<const double2*>(rho), Rr, Ri);
+        TC_LAUNCH_CHECK();
+        if (obs) TC_TRY(launch_block_observables<double>(L, bs, m, t, Rr, Ri, obs, scratch, cs));
+        if (steps >= 1) TC_TRY(one_step(1, cs));
+        return TC_OK;
+    };
+    auto rest = [&](cudaStream_t cs) -> tc_status {
+        for (int k = 2; k <= steps; k++) TC_TRY(one_step(k, cs));
+        return TC_OK;
+    };
+    auto tail = [&](cudaStream_t cs) -> tc_status {
+        dim3 g(256, (unsigned)(n + 1));
+        blocks_join_pad_kernel<<<g, 256, 0, cs>>>(bs, pk, Rr, Ri, reinterpret_cast<double2*>(rho));
+        TC_LAUNCH_CHECK();
+        return TC_OK;
+    };
+    return run_captured(s, first, rest, tail, steps > 2 && !timing_enabled());
+}
+
 size_t evolve_bytes(int n, int precision) {
+    if (precision == TC_FP64_OZAKI) return evolve_oz_bytes_blocks(n);
     return precision == TC_FP64 ? evolve_f64_bytes(n) : evolve_lowp_bytes_blocks(n, precision);
 }
 
 }  // namespace
 
 size_t lindblad_bytes(int n, int precision) {
-    if (precision < TC_FP64 || precision > TC_TF32X3) return 0;
+    if (precision < TC_FP64 || precision > TC_FP64_OZAKI) return 0;
     return std::max(propagators_bytes(n), evolve_bytes(n, precision));
 }
 
@@ -698,7 +824,8 @@ extern "C" TC_API tc_status tc_lindblad_evolve(const tc_params* params, double k
     if (!(kappa >= 0.0) || !std::isfinite(kappa)) return fail(TC_ERR_INVALID_ARG, "kappa must be finite and >= 0");
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(TC_ERR_INVALID_ARG, "dt must be finite and > 0");
     if (steps < 0 || renorm_every < 0) return fail(TC_ERR_INVALID_ARG, "steps / renorm_every < 0");
-    if (precision < TC_FP64 || precision > TC_TF32X3) return fail(TC_ERR_INVALID_ARG, "unknown precision %d", precision);
+    if (precision < TC_FP64 || precision > TC_FP64_OZAKI)
+        return fail(TC_ERR_INVALID_ARG, "unknown precision %d", precision);
     TC_TRY(check_work(work, work_bytes, evolve_bytes(m.n, precision)));
     TC_TRY(check_device());
     const Layout& L = layout_of(m.n);
@@ -707,5 +834,7 @@ extern "C" TC_API tc_status tc_lindblad_evolve(const tc_params* params, double k
     double* Rd = static_cast<double*>(rho);
     if (precision == TC_FP64)
         return evolve_f64(L, m, kappa, dt, Ud, Rd, steps, renorm_every, obs, ar, as_stream(stream));
+    if (precision == TC_FP64_OZAKI)
+        return evolve_oz_blocks(L, m, kappa, dt, Ud, Rd, steps, renorm_every, obs, ar, as_stream(stream));
     return evolve_lowp_blocks(L, m, precision, kappa, dt, Ud, Rd, steps, renorm_every, obs, ar, as_stream(stream));
 }

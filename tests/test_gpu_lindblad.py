@@ -302,3 +302,39 @@ def test_errors(tc):
                                 ctypes.c_void_p(rho.data_ptr()), 3, 0, 0, None, ctypes.c_void_p(w.data_ptr()), 1024,
                                 None)
     assert st == 1
+
+
+# ---------------------------------------------------------------- FP64 emulated on the BF16 tensor cores
+def test_emulated_fp64_matches_oracle_n6(tc, L):
+    """Block products from exact digit slices: the FP64 form's 1e-12 against the oracle (each
+    product is within K 2^-48 max|U| max|rho|, K = 128 here, far below that)."""
+    n, dt, steps, kappa = 6, 0.1, 20, 0.3
+    g = W.draw_couplings(n, 72) * 20
+    p = _params(tc, n, g, 1.002, 1.0)
+    lay = tc.lindblad_layout(n)
+    rho0 = _random_block_rho(L, n, 73)
+    U = tc.lindblad_propagators(p, dt)
+    rho = torch.from_numpy(_pack(L, lay, rho0)).cuda()
+    out, obs = tc.lindblad_evolve(p, kappa, dt, U, rho, steps, "ozaki")
+    ref, rows = L.propagate(n, g, 1.002, 1.0, kappa, dt, steps, rho0)
+    got = _unpack(L, lay, out.cpu().numpy())
+    assert np.max(np.abs(got - ref)) < 1e-12
+    assert np.max(np.abs(obs.cpu().numpy()[:, :2 * n + 3] - rows[:, :2 * n + 3])) < 1e-11
+
+
+def test_emulated_fp64_matches_fp64_path_n9(tc):
+    """n = 9: blocks up to 512 (four tiles, ragged 382 / 466 / 502 / 511) against the DMMA blocks."""
+    n, dt, steps, kappa = 9, 0.05, 10, 0.4
+    g = W.draw_couplings(n, 74) * 20
+    p = _params(tc, n, g, 1.002, 1.0)
+    lay = tc.lindblad_layout(n)
+    U = tc.lindblad_propagators(p, dt)
+    rho = torch.zeros(lay.total, dtype=torch.complex128, device="cuda")
+    j = lay.basis.index((1 << n) - 1)
+    lay.blocks(rho)[n][j, j] = 1.0
+    a, oa = tc.lindblad_evolve(p, kappa, dt, U, rho, steps, "fp64")
+    b, ob = tc.lindblad_evolve(p, kappa, dt, U, rho, steps, "ozaki")
+    assert torch.max(torch.abs(a - b)).item() < 1e-12
+    assert torch.max(torch.abs(oa - ob)[:, :2 * n + 3]).item() < 1e-11
+    for blk in lay.blocks(b):
+        assert torch.max(torch.abs(blk - blk.conj().T)).item() == 0.0
