@@ -76,7 +76,8 @@ typedef enum tc_status {
  *              stay below 2^24 for K <= 16384) and are scaled and summed in
  *              FP64.  About 2^-48 of the row and column scales per product;
  *              rho stored in FP64.  tc_evolve, tc_evolve_host,
- *              tc_lindblad_evolve and tc_evolve_backward (not the batch).
+ *              tc_lindblad_evolve, tc_evolve_backward and tc_batch_evolve
+ *              (there the systems run one after another).
  * In the BF16/TF32 forms U is computed in FP64 and rho is stored in FP32
  * between steps. */
 typedef enum tc_precision {

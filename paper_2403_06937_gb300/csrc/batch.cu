@@ -38,6 +38,15 @@ struct F64Sys {
 }  // namespace
 
 size_t batch_bytes(int count, const int* n, int precision) {
+    if (precision == TC_FP64_OZAKI) {
+        // the systems run one after another through one workspace
+        size_t most = 0;
+        for (int b = 0; b < count; b++) {
+            if (n[b] < 1 || n[b] > kMaxAtoms) return 0;
+            most = std::max(most, evolve_oz_bytes(n[b]));
+        }
+        return most + 256;
+    }
     size_t total = 256 + round256(sizeof(BatchSys) * (size_t)count) + 64;
     for (int b = 0; b < count; b++) {
         if (n[b] < 1 || n[b] > kMaxAtoms) return 0;
@@ -55,7 +64,7 @@ extern "C" {
 
 TC_API size_t tc_batch_workspace_size(int count, const int* n, int precision) {
     if (count < 1 || !n) return 0;
-    if (precision < TC_FP64 || precision > TC_TF32X3) return 0;
+    if (precision < TC_FP64 || precision > TC_FP64_OZAKI) return 0;
     return batch_bytes(count, n, precision);
 }
 
@@ -64,7 +73,8 @@ TC_API tc_status tc_batch_evolve(int count, const int* n, const void* const* U, 
                                  void* work, size_t work_bytes, void* stream) {
     if (count < 1 || !n || !U || !rho) return fail(TC_ERR_INVALID_ARG, "count, n, U or rho missing");
     if (steps < 0 || renorm_every < 0) return fail(TC_ERR_INVALID_ARG, "steps / renorm_every < 0");
-    if (precision < TC_FP64 || precision > TC_TF32X3) return fail(TC_ERR_INVALID_ARG, "unknown precision %d", precision);
+    if (precision < TC_FP64 || precision > TC_FP64_OZAKI)
+        return fail(TC_ERR_INVALID_ARG, "unknown precision %d", precision);
     std::vector<Model> models(count);
     for (int b = 0; b < count; b++) {
         if (n[b] < 1 || n[b] > kMaxAtoms) return fail(TC_ERR_INVALID_ARG, "system %d: n = %d outside 1..16", b, n[b]);
@@ -82,6 +92,16 @@ TC_API tc_status tc_batch_evolve(int count, const int* n, const void* const* U, 
     if (work_bytes < need) return fail(TC_ERR_WORKSPACE, "work has %zu bytes, need %zu", work_bytes, need);
     TC_TRY(check_device());
     cudaStream_t us = as_stream(stream);
+    if (precision == TC_FP64_OZAKI) {
+        // FP64 emulated on the BF16 tensor cores: each system's step loop in turn
+        // (one graph per system), all through the same workspace
+        for (int b = 0; b < count; b++) {
+            Arena ar{static_cast<char*>(work), work_bytes, 0};
+            TC_TRY(evolve_oz(static_cast<const double*>(U[b]), static_cast<double*>(rho[b]), n[b], steps,
+                             renorm_every, params ? &models[b] : nullptr, obs ? obs[b] : nullptr, ar, us));
+        }
+        return TC_OK;
+    }
 
     // systems in decreasing size: the longest tiles first in the persistent schedule
     std::vector<int> order(count);

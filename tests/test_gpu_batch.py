@@ -36,7 +36,7 @@ def _systems(tc, ns, seed, dt=0.05):
     return out
 
 
-@pytest.mark.parametrize("precision", ["bf16x3", "tf32x3", "tf32", "fp64"])
+@pytest.mark.parametrize("precision", ["bf16x3", "tf32x3", "tf32", "fp64", "ozaki"])
 def test_batch_equals_standalone_runs(tc, precision):
     ns = [3, 9, 6, 7, 8, 9, 5, 7]
     sy = _systems(tc, ns, 1)
