@@ -155,3 +155,22 @@ def test_n15_one_step_two_k_chunks(tc, oracle):
     assert np.max(np.abs(got - psi[ii] * psi[jj].conj())) < tol
     del rho, rho0, U
     torch.cuda.empty_cache()
+
+
+def test_host_buffers_and_renormalisation(tc):
+    """tc_evolve_host with the emulated form (rho in pinned host memory) equals the device call;
+    renormalisation divides by the FP64 trace."""
+    n = 7
+    p = _params(tc, n, W.draw_couplings(n, 8) * 5, 1.01, 1.0)
+    U = tc.expm_model(p, 0.1)
+    rho0, _, _ = W.random_mixed_state(n, 2, 12)
+    r_dev, o_dev = tc.evolve(U, torch.from_numpy(rho0).cuda(), n, 6, "ozaki", params=p)
+    r_host = torch.from_numpy(rho0.copy()).pin_memory()
+    o_host = torch.empty((7, 2 * n + 5), dtype=torch.float64).pin_memory()
+    tc.evolve_host(U, r_host, n, 6, "ozaki", params=p, obs_host=o_host)
+    assert torch.equal(r_host, r_dev.cpu())
+    assert torch.equal(o_host, o_dev.cpu())
+    half = torch.from_numpy(rho0 * 0.5).cuda()
+    rr, oo = tc.evolve(U, half, n, 4, "ozaki", renorm_every=2, params=p)
+    tr = oo[:, 2 * n + 2].cpu().numpy()
+    assert abs(tr[0] - 0.5) < 1e-15 and np.max(np.abs(tr[2:] - 1.0)) < 1e-14
