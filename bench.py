@@ -385,14 +385,18 @@ def run_ours(a, cfg):
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
+        calls = []
         t0 = time.perf_counter()
         for _ in range(a.steps):
+            tc0 = time.perf_counter()
             tc.evolve_host(U, rho_h, n, 1, prec, params=params, obs_host=obs_h, work=hw)
+            calls.append(1e3 * (time.perf_counter() - tc0))
         torch.cuda.synchronize()
         te = max_over_ranks(time.perf_counter() - t0, world)
         line["e2e"] = {"value": world * a.steps / te, "unit": "steps/s", "h2d_bytes_per_step": 16 * N * N,
                        "d2h_bytes_per_step": 16 * N * N + 2 * (2 * n + 5) * 8,
-                       "api": "tc_evolve_host (C ABI, pinned host rho, one step per call)"}
+                       "api": "tc_evolve_host (C ABI, pinned host rho, one step per call)",
+                       "call_ms": [round(c, 1) for c in calls]}
         del rho_h, hw
 
     if not a.no_compare:
