@@ -34,6 +34,9 @@ size_t oz_slice_bytes(int Np);
 // Y = U P^H (mode 0: all tiles; mode 1: block-lower tiles, then oz_mirror)
 tc_status cgemm_oz(int mode, const CUtensorMap& tmU, const CUtensorMap& tmP, const OzEpi& ep, cudaStream_t s);
 tc_status oz_mirror(double* yr, double* yi, int Np, cudaStream_t s);
+// CTA pairs sharing the U panels by TMA multicast (even tile counts)
+void oz_set_cluster(int on);
+bool oz_cluster_enabled();
 
 // One operand of the emulated product: its digit slices, row exponents and
 // TMA map (row r of the operand = row r of A, or row r of B in A B^H).
