@@ -466,7 +466,6 @@ std::atomic<int> g_oz_cluster{-1};
 
 }  // namespace
 
-void oz_set_cluster(int on) { g_oz_cluster.store(on ? 1 : 0); }
 bool oz_cluster_enabled() {
     int v = g_oz_cluster.load();
     if (v < 0) {

@@ -34,8 +34,8 @@ size_t oz_slice_bytes(int Np);
 // Y = U P^H (mode 0: all tiles; mode 1: block-lower tiles, then oz_mirror)
 tc_status cgemm_oz(int mode, const CUtensorMap& tmU, const CUtensorMap& tmP, const OzEpi& ep, cudaStream_t s);
 tc_status oz_mirror(double* yr, double* yi, int Np, cudaStream_t s);
-// CTA pairs sharing the U panels by TMA multicast (even tile counts)
-void oz_set_cluster(int on);
+// CTA pairs sharing the U panels by TMA multicast (even tile counts; on
+// unless TC_OZ_CLUSTER=0 in the environment)
 bool oz_cluster_enabled();
 
 // One operand of the emulated product: its digit slices, row exponents and
