@@ -92,6 +92,25 @@ __device__ __forceinline__ void tile_of(int mode, int T, int G, int b, int& I, i
     I = J = 0;   // not reached for b < T (T + 1) / 2
 }
 
+// CTA pairs (clusters of 2): pair q covers tiles (I, 2j) and (I, 2j + 1), rank
+// r taking J = 2j + r; mode 0 all rows of T (even) tiles, mode 1 the pairs
+// that hold a block-lower tile of row I (j <= I / 2; the tile (I, I + 1) of
+// an even row I is computed too and overwritten by the mirror).
+__device__ __forceinline__ void pair_tile(int mode, int T, int q, int rank, int& I, int& J) {
+    if (mode == 0) {
+        I = q / (T / 2);
+        J = 2 * (q % (T / 2)) + rank;
+        return;
+    }
+    int row = 0, base = 0;
+    while (base + row / 2 + 1 <= q) {
+        base += row / 2 + 1;
+        row++;
+    }
+    I = row;
+    J = 2 * (q - base) + rank;
+}
+
 // -------------------------------------------------------------- splitting
 __device__ __forceinline__ float tf32_rna(float x) {
     uint32_t r;

@@ -142,25 +142,6 @@ __device__ __forceinline__ void oz_epilogue(uint32_t tmem, int warp, int lane, i
     }
 }
 
-// CTA pairs (clusters of 2): pair q covers tiles (I, 2j) and (I, 2j + 1), rank
-// r taking J = 2j + r; mode 0 all rows of T (even) tiles, mode 1 the pairs
-// that hold a block-lower tile of row I (j <= I / 2; the tile (I, I + 1) of
-// an even row I is computed too and overwritten by the mirror).
-__device__ __forceinline__ void pair_tile(int mode, int T, int q, int rank, int& I, int& J) {
-    if (mode == 0) {
-        I = q / (T / 2);
-        J = 2 * (q % (T / 2)) + rank;
-        return;
-    }
-    int row = 0, base = 0;
-    while (base + row / 2 + 1 <= q) {
-        base += row / 2 + 1;
-        row++;
-    }
-    I = row;
-    J = 2 * (q - base) + rank;
-}
-
 // CL = 2: clusters of two CTAs with the same row tile I: rank 0 loads the
 // U_r slice and rank 1 the U_i slice of every stage into both CTAs (TMA
 // multicast), so each U panel crosses L2 once per pair; each CTA's MMA
