@@ -5,13 +5,18 @@
  *
  * The library computes, on one GPU:
  *   H  -- the dense Hamiltonian of Eq. 4 on the basis of Eq. 2;
- *   U  -- e^{-iH dt} by a scaled Taylor polynomial (Eqs. 6-8, 10), dense FP64;
- *   rho <- U rho U^dag step after step (Eqs. 6 and 12), on FP64 DMMA or on
- *          tcgen05 tensor cores in split-BF16 / TF32 arithmetic;
+ *   U  -- e^{-iH dt} by a scaled Taylor polynomial (Eqs. 6-8, 10): dense FP64,
+ *          or from the model with H applied as a stencil (no dense H);
+ *   rho <- U rho U^dag step after step (Eqs. 6 and 12), on FP64 DMMA, on
+ *          tcgen05 tensor cores in split-BF16 / TF32 arithmetic, or at FP64
+ *          accuracy from exact integer digit slices on the BF16 tensor cores;
  *   observables read from rho by reduction (populations, the photon-number
  *          probabilities of Eq. 13, trace, purity, energy);
  *   the gradient of a diagonal observable at the final time with respect to
- *          the couplings and frequencies (reverse mode through Eq. 6).
+ *          the couplings and frequencies (reverse mode through Eq. 6);
+ *   the open system of Eq. 5 with photon leakage (excitation blocks, exact
+ *          damping channel, symmetric split step);
+ *   many independent systems of uneven size in one call.
  *
  * Conventions shared by every call
  * --------------------------------
@@ -108,9 +113,9 @@ typedef struct tc_params {
     int coupling;       /* tc_coupling */
 } tc_params;
 
-/* Taylor plan of tc_expm.  The paper's Eq. 10 is {10, 0, 0}. */
+/* Taylor plan of tc_expm and tc_expm_model.  The paper's Eq. 10 is {10, 0, 0}. */
 typedef struct tc_expm_opts {
-    int taylor_degree;  /* 0 = smallest degree meeting FP64 accuracy; else 1..30 */
+    int taylor_degree;  /* 0 = smallest degree meeting FP64 accuracy; else 1..30 (tc_expm_model: 1..64) */
     int squarings;      /* -1 = chosen with the degree; else 0..40 */
     int shift;          /* 1 = subtract the mean diagonal before the series */
 } tc_expm_opts;
