@@ -257,6 +257,16 @@ def _compulsory_bytes(prec, N):
     return (3 * planes + 8 + 8) * N * N
 
 
+def oz_pairs(N):
+    """Digit-slice pairs per complex product of the FP64-emulated form: the
+    library takes 8-bit digits for inner dimension K <= 1024, 7-bit for
+    K <= 4096, else 6-bit (TC_OZ_BITS=6 forces 6-bit)."""
+    K = max(N, 128)
+    if os.environ.get("TC_OZ_BITS") == "6" or K > 4096:
+        return 45
+    return 28 if K <= 1024 else 36
+
+
 def _time_form(tc, torch, U, n, params, prec, steps, warmup, renorm, stream, with_clocks=None):
     """W untimed steps, then K steps of one tc_evolve call timed with CUDA events."""
     N = 1 << n
@@ -362,7 +372,7 @@ def run_ours(a, cfg):
         "vs_baseline": None, "dtype": {"fp64": "f64", "bf16x3": "bf16", "tf32": "tf32", "tf32x3": "tf32", "ozaki": "bf16"}[prec],
         "data": "synthetic",
         "config": {"workload": cfg.description, "precision": prec, "dim": N,
-                   "products_per_complex_product": {"fp64": 1, "bf16x3": 6, "tf32": 1, "tf32x3": 3, "ozaki": 45}[prec],
+                   "products_per_complex_product": {"fp64": 1, "bf16x3": 6, "tf32": 1, "tf32x3": 3, "ozaki": oz_pairs(N)}[prec],
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (U and rho are %d MiB each in complex128)" % (16 * N * N >> 20),
                    "setup_s": t_setup},
@@ -416,6 +426,8 @@ def run_ours(a, cfg):
             others[p2] = {"value": v2, "unit": "steps/s", "steps": k2, "warmup": w2,
                           "credited_tflops": credited * v2 / 1e12, "achieved_tflops": ach, "peak": pk,
                           "frac": ach / pk if pk else None, "error": r2["drift"]}
+            if p2 == "ozaki":
+                others[p2]["digit_pairs"] = oz_pairs(1 << n)
         line["other_forms"] = others
         if "value" in others.get("fp64", {}):
             line["speedup_vs_fp64"] = (value / world) / others["fp64"]["value"]

@@ -75,12 +75,15 @@ typedef enum tc_status {
  *  TC_TF32   : one TF32 product, FP32 accumulate (tcgen05 kind::tf32).
  *  TC_TF32X3 : big/small TF32 split, three products (kind::tf32).
  *  TC_FP64_OZAKI : FP64-accurate products on the BF16 tensor cores: every
- *              operand row scaled by a power of two and written as nine
- *              balanced base-64 integer digits (exact in BF16); the 45 digit
- *              products with t + u <= 8 accumulate exactly in FP32 (sums
- *              stay below 2^24 for K <= 16384) and are scaled and summed in
- *              FP64.  About 2^-48 of the row and column scales per product;
- *              rho stored in FP64.  tc_evolve, tc_evolve_host,
+ *              operand row scaled by a power of two and written as S
+ *              balanced base-2^b integer digits (exact in BF16): b = 6,
+ *              S = 9 in general; b = 7, S = 8 for inner dimensions
+ *              K <= 4096; b = 8, S = 7 for K <= 1024 (TC_OZ_BITS=6 in the
+ *              environment keeps b = 6).  The S(S+1)/2 digit products with
+ *              t + u < S (45 / 36 / 28) accumulate exactly in FP32 (sums
+ *              stay below 2^24) and are scaled and summed in FP64.  Within
+ *              2^-48 of the row and column scales per product term (worst
+ *              case); rho stored in FP64.  tc_evolve, tc_evolve_host,
  *              tc_lindblad_evolve, tc_evolve_backward and tc_batch_evolve
  *              (there the systems run one after another).
  * In the BF16/TF32 forms U is computed in FP64 and rho is stored in FP32

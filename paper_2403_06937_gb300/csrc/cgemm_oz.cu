@@ -3,20 +3,23 @@
 // rho <- U rho U^dag (Sec. III.A, Eqs. 6, 12) at FP64 accuracy.
 //
 // Slicing.  Every row r of an operand (both planes together) gets an
-// exponent e_r with max |x| < 2^(e_r - 1); then x 2^(54 - e_r) is rounded to
-// a 54-bit integer and written in balanced base-64 digits,
-//     x = 2^e_r sum_{t=0..8} d_t 2^(-6(t+1)),   d_t integers, |d_t| <= 32,
+// exponent e_r with max |x| < 2^(e_r - 1); with S digits of b bits
+// (oz_digits: b = 6, 7 or 8 as K allows, bS = 54 or 56), x 2^(bS - e_r) is
+// rounded to an integer below 2^(bS - 1) and written in balanced base-2^b
+// digits,
+//     x = 2^e_r sum_{t=0..S-1} d_t 2^(-b(t+1)),   d_t integers, |d_t| <= 2^(b-1),
 // each digit stored as an exact BF16 value (slice t).
 //
 // Products.  For slices t of U and u of P, sum_k d_t(U) d_u(P) is a sum of
-// integers of size <= 32^2 = 2^10; over K <= 16384 terms it stays within
+// integers of size <= 2^(2b-2); over K <= 2^(26-2b) terms it stays within
 // 2^24, so the FP32 accumulation of the tensor cores is exact (no rounding,
 // hence no truncation).  One pass of the K loop per slice pair (t, u) with
-// t + u <= 8 (45 pairs; the first dropped level is ~2^-48 of the row and
-// column scales) accumulates that pair in TMEM; the epilogue accumulates the
-// exact integer results in int64 with the level weights as shifts and the
-// last pass writes Y = sum 2^(e_i + f_j - 6(t + u + 2)) (integer) in FP64.
-// K above 16384 is cut into chunks of 16384, one pass each.
+// t + u <= S - 1 (S(S+1)/2 pairs; the first dropped level is below 2^-52 of
+// the row and column scales) accumulates that pair in TMEM; the epilogue
+// accumulates the exact integer results in int64 with the level weights as
+// shifts and the last pass writes Y = sum 2^(e_i + f_j - b(t + u + 2))
+// (integer) in FP64.  With 6-bit digits, K above 16384 is cut into chunks of
+// 16384, one pass each.
 //
 // Tile and roles as the split-BF16 kernel (cgemm_tc.cu): one CTA per 128 x 128
 // complex tile, A = slice t of U_r and U_i (M = 128), B = slice u of
@@ -45,16 +48,16 @@ constexpr int kThreads = 192;
 constexpr int kStages = 12;
 constexpr int kStage = 2 * kATile + kBTile;   // 16 KB
 constexpr int kKPerStage = kRowBytes / 2;     // 16 BF16 values of K
-constexpr int kKMax = 16384;                  // K per pass: 16384 * 32 * 32 = 2^24
 constexpr int kZeroExp = -100000;             // exponent of an all-zero row
 
-// pair q -> (t, u) with t + u <= 8, t-major: (0,0), (0,1), ..., (0,8), (1,0),
-// ..., (8,0).  Consecutive passes of a tile reuse the U slice t, which the
-// CTAs of a wave (a few row tiles) keep in L2 while the P slices stream.
-__device__ __forceinline__ void oz_pair(int q, int& t, int& u) {
+// pair q -> (t, u) with t + u <= S - 1, t-major: (0,0), (0,1), ..., (0,S-1),
+// (1,0), ..., (S-1,0).  Consecutive passes of a tile reuse the U slice t,
+// which the CTAs of a wave (a few row tiles) keep in L2 while the P slices
+// stream.
+__device__ __forceinline__ void oz_pair(int q, int S, int& t, int& u) {
     int tt = 0, base = 0;
-    while (base + (kOzSlices - tt) <= q) {
-        base += kOzSlices - tt;
+    while (base + (S - tt) <= q) {
+        base += S - tt;
         tt++;
     }
     t = tt;
@@ -71,11 +74,14 @@ __device__ __forceinline__ double pow2(int e) {
 // exact integers below 2^24; Y_r = U_r P_r^T + U_i P_i^T and
 // Y_i = U_i P_r^T - U_r P_i^T are formed exactly in int32 and accumulated
 // exactly in int64, with the level's weight as a shift: levels 0-3 into
-// `hi` (unit 2^(e_i + f_j - 30), kept in the FP64 output planes until the
-// last pass), levels 4-8 into `lo` (unit 2^(e_i + f_j - 60)).  Bounds:
-// hi <= chunks * 10 * 2^25 * 2^18, lo <= chunks * 35 * 2^25 * 2^24, within
-// int64 for up to 2^8 K chunks.  The last pass (level 8) writes
-//     Y = hi 2^(e_i + f_j - 30) + lo 2^(e_i + f_j - 60)
+// `hi` (shift b(3 - L), unit 2^(e_i + f_j - 5b), kept in the FP64 output
+// planes until the last pass), levels 4..S-1 into `lo` (shift b(S - 1 - L),
+// unit 2^(e_i + f_j - b(S + 1))).  Bounds (a level holds at most L + 1 pair
+// sums of magnitude 2^25 per K chunk): b = 6, hi <= chunks 2^25 2^18 1.2 and
+// lo <= chunks 5 2^25 2^24 1.1, within int64 for up to 2^8 K chunks; b = 7
+// and 8 (one chunk), hi <= 2^25 2^24 1.1, lo <= 5 2^25 2^21 1.1.  The last
+// pass (level S - 1) writes
+//     Y = hi 2^(e_i + f_j - 5b) + lo 2^(e_i + f_j - b(S + 1))
 // in FP64.  Integer work only, except that final combination.
 __device__ __forceinline__ void oz_epilogue(uint32_t tmem, int warp, int lane, int I, int J, const OzEpi& ep, int L,
                                             bool first_hi, bool first_lo, bool last) {
@@ -83,8 +89,10 @@ __device__ __forceinline__ void oz_epilogue(uint32_t tmem, int warp, int lane, i
     const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
     const size_t Np = (size_t)ep.Np;
     const size_t gi = (size_t)I * 128 + row;
+    const int b = ep.bits;
     const bool to_hi = L <= 3;
-    const int shift = to_hi ? 6 * (3 - L) : 6 * (8 - L);
+    const int shift = to_hi ? b * (3 - L) : b * (ep.slices - 1 - L);
+    const int e_hi = 5 * b, e_lo = b * (ep.slices + 1);
     const bool first = to_hi ? first_hi : first_lo;
     const int ei = ep.eU[gi];
 #pragma unroll 1
@@ -122,7 +130,7 @@ __device__ __forceinline__ void oz_epilogue(uint32_t tmem, int warp, int lane, i
                 vr2[h] = make_longlong2(xr[0], xr[1]);
                 vi2[h] = make_longlong2(xi[0], xi[1]);
             } else {
-                // the last pass is of level 8 (lo): combine with hi into FP64
+                // the last pass is of level S - 1 (lo): combine with hi into FP64
                 const longlong2 hr = reinterpret_cast<const longlong2*>(ep.yr + o)[h];
                 const longlong2 hi_ = reinterpret_cast<const longlong2*>(ep.yi + o)[h];
                 const long long hr_[2] = {hr.x, hr.y}, hii[2] = {hi_.x, hi_.y};
@@ -131,7 +139,7 @@ __device__ __forceinline__ void oz_epilogue(uint32_t tmem, int warp, int lane, i
                 for (int w = 0; w < 2; w++) {
                     const int q = 2 * h + w;
                     const int ej = ep.eP[(size_t)J * 128 + c + q];
-                    const double s_hi = pow2(ei + ej - 30), s_lo = pow2(ei + ej - 60);
+                    const double s_hi = pow2(ei + ej - e_hi), s_lo = pow2(ei + ej - e_lo);
                     yr[w] = (double)hr_[w] * s_hi + (double)xr[w] * s_lo;
                     yi[w] = (double)hii[w] * s_hi + (double)xi[w] * s_lo;
                 }
@@ -193,10 +201,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (CL == 2) cluster_sync();   // the peer's barriers exist before anything is multicast to them
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    const int Kc = ep.Np < kKMax ? ep.Np : kKMax;
+    const int S = ep.slices;
+    const int kmax = 1 << (26 - 2 * ep.bits);
+    const int Kc = ep.Np < kmax ? ep.Np : kmax;
     const int chunks = ep.Np / Kc;
     const int KBc = Kc / kKPerStage;
-    const int passes = kOzPairs * chunks;
+    const int passes = S * (S + 1) / 2 * chunks;
 
     if (warp == 4) {
         // ---------------------------------------------------------- producer
@@ -207,7 +217,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             bool ok = true;
             for (int p = 0; p < passes && ok; p++) {
                 int t, u;
-                oz_pair(p / chunks, t, u);
+                oz_pair(p / chunks, S, t, u);
                 const int c = p % chunks;
                 for (int kb = 0; kb < KBc; kb++, it++) {
                     const int s = it % kStages;
@@ -223,14 +233,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (CL == 2) {
                         // U_r slice t from rank 0, U_i slice t from rank 1, into both CTAs
                         tma_load_3d_multicast(saddr(st + rank * kATile), &tmU, fb, kx, I * 128,
-                                              (int)rank * kOzSlices + t, (uint16_t)0x3);
+                                              (int)rank * S + t, (uint16_t)0x3);
                     } else {
                         tma_load_3d_hint(saddr(st), &tmU, fb, kx, I * 128, t, keep);                       // U_r
-                        tma_load_3d_hint(saddr(st + kATile), &tmU, fb, kx, I * 128, kOzSlices + t, keep);  // U_i
+                        tma_load_3d_hint(saddr(st + kATile), &tmU, fb, kx, I * 128, S + t, keep);          // U_i
                     }
                     tma_load_3d(saddr(st + 2 * kATile), &tmP, fb, kx, J * 128, u);                     // P_r slice u
                     tma_load_3d(saddr(st + 2 * kATile + 128 * kRowBytes), &tmP, fb, kx, J * 128,
-                                kOzSlices + u);                                                        // P_i slice u
+                                S + u);                                                                // P_i slice u
                 }
             }
             if (*abort) {
@@ -294,8 +304,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 break;
             }
             int t, u;
-            oz_pair(p / chunks, t, u);
-            // first pass into hi: pair (0, 0); into lo: pair (0, 4); the last pass, pair (8, 0), is into lo
+            oz_pair(p / chunks, S, t, u);
+            // first pass into hi: pair (0, 0); into lo: pair (0, 4); the last pass, pair (S - 1, 0), is into lo
             oz_epilogue(tmem, warp, lane, I, J, ep, t + u, p == 0, p == 4 * chunks, p == passes - 1);
             tc_fence_before();
             asm volatile("bar.sync 1, 128;" ::: "memory");   // all four epilogue warps have read TMEM
@@ -317,13 +327,14 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 constexpr int kSmem = kStages * kStage + 1024 /*align*/ + 256 /*barriers*/;
 
-// One warp per row r < Np: the row exponent over both planes, then the nine
-// balanced base-64 digits of every entry (zero beyond the valid N x N block).
+// One warp per row r < Np: the row exponent over both planes, then the S
+// balanced base-2^b digits of every entry (zero beyond the valid N x N block).
 // INTERLEAVED: re/im interleaved complex128 with row stride ld (complex
 // elements); else planar FP64 planes re, im with row stride ld.
 template <bool INTERLEAVED>
 __global__ void oz_slice_kernel(const double* __restrict__ re, const double* __restrict__ im, int N, size_t ld,
-                                int Np, double im_sign, __nv_bfloat16* __restrict__ slices, int* __restrict__ ex) {
+                                int Np, double im_sign, int bits, int S, __nv_bfloat16* __restrict__ slices,
+                                int* __restrict__ ex) {
     const int warps = (int)(gridDim.x * blockDim.x) >> 5;
     const int lane = threadIdx.x & 31;
     const size_t plane = (size_t)Np * Np;
@@ -351,9 +362,10 @@ __global__ void oz_slice_kernel(const double* __restrict__ re, const double* __r
         for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
         const int e = m > 0.0 ? ilogb(m) + 2 : kZeroExp;   // max |x| < 2^(e - 1)
         if (lane == 0) ex[r] = e;
-        // x 2^(54 - e) as two exact power-of-two factors (54 - e exceeds the
+        // x 2^(bS - e) as two exact power-of-two factors (bS - e exceeds the
         // FP64 exponent range for rows below 2^-969)
-        const int sh = 54 - e;
+        const int sh = bits * S - e;
+        const long long half = 1ll << (bits - 1), mask = (1ll << bits) - 1;
         const double sc1 = m > 0.0 ? pow2(sh < 1000 ? sh : 1000) : 0.0;
         const double sc2 = m > 0.0 ? pow2(sh < 1000 ? 0 : sh - 1000) : 0.0;
         for (int c = lane; c < Np; c += 32) {
@@ -362,15 +374,14 @@ __global__ void oz_slice_kernel(const double* __restrict__ re, const double* __r
             xv[1] *= im_sign;
 #pragma unroll
             for (int part = 0; part < 2; part++) {
-                long long v = __double2ll_rn(xv[part] * sc1 * sc2);   // |v| < 2^53
-                __nv_bfloat16* dst = slices + (size_t)part * kOzSlices * plane + (size_t)r * Np + c;
-#pragma unroll
-                for (int t = kOzSlices - 1; t >= 1; t--) {
-                    const long long d = ((v + 32) & 63) - 32;   // balanced digit in [-32, 31]
-                    v = (v - d) >> 6;
+                long long v = __double2ll_rn(xv[part] * sc1 * sc2);   // |v| < 2^(bS - 1)
+                __nv_bfloat16* dst = slices + (size_t)part * S * plane + (size_t)r * Np + c;
+                for (int t = S - 1; t >= 1; t--) {
+                    const long long d = ((v + half) & mask) - half;   // balanced digit in [-2^(b-1), 2^(b-1))
+                    v = (v - d) >> bits;
                     dst[(size_t)t * plane] = __float2bfloat16_rn((float)d);
                 }
-                dst[0] = __float2bfloat16_rn((float)v);   // |v| <= 32
+                dst[0] = __float2bfloat16_rn((float)v);   // |v| <= 2^(b-1)
             }
         }
     }
@@ -444,6 +455,9 @@ tc_status launch(const CUtensorMap& tmU, const CUtensorMap& tmP, const OzEpi& ep
 // -1: not chosen yet (TC_OZ_CLUSTER=0|1 in the environment, else on: the
 // pairs give the same bits and 15 % more speed at n = 14)
 std::atomic<int> g_oz_cluster{-1};
+// -1: not chosen yet (TC_OZ_BITS=6 in the environment: 6-bit digits at every
+// size; else the widest digits K allows)
+std::atomic<int> g_oz_narrow{-1};
 
 }  // namespace
 
@@ -457,15 +471,28 @@ bool oz_cluster_enabled() {
     return v != 0;
 }
 
+OzDigits oz_digits(int Np) {
+    int narrow = g_oz_narrow.load();
+    if (narrow < 0) {
+        const char* e = std::getenv("TC_OZ_BITS");
+        narrow = e && std::atoi(e) == 6 ? 1 : 0;
+        g_oz_narrow.store(narrow);
+    }
+    if (!narrow && Np <= 1024) return OzDigits{8, 7, 28, 1024};
+    if (!narrow && Np <= 4096) return OzDigits{7, 8, 36, 4096};
+    return OzDigits{6, 9, 45, 16384};
+}
+
 tc_status oz_slice(const double* re, const double* im, bool interleaved, bool conj, int N, size_t ld, int Np,
-                   void* slices, int* ex, cudaStream_t s) {
+                   const OzDigits& dg, void* slices, int* ex, cudaStream_t s) {
     const unsigned blocks = (unsigned)(((size_t)Np * 32 + 255) / 256);
     const unsigned g = blocks < grid_for((size_t)Np * 32) ? blocks : grid_for((size_t)Np * 32);
     const double sign = conj ? -1.0 : 1.0;
+    auto* out = static_cast<__nv_bfloat16*>(slices);
     if (interleaved)
-        oz_slice_kernel<true><<<g, 256, 0, s>>>(re, im, N, ld, Np, sign, static_cast<__nv_bfloat16*>(slices), ex);
+        oz_slice_kernel<true><<<g, 256, 0, s>>>(re, im, N, ld, Np, sign, dg.bits, dg.slices, out, ex);
     else
-        oz_slice_kernel<false><<<g, 256, 0, s>>>(re, im, N, ld, Np, sign, static_cast<__nv_bfloat16*>(slices), ex);
+        oz_slice_kernel<false><<<g, 256, 0, s>>>(re, im, N, ld, Np, sign, dg.bits, dg.slices, out, ex);
     TC_LAUNCH_CHECK();
     return TC_OK;
 }
@@ -479,8 +506,11 @@ tc_status oz_mirror(double* yr, double* yi, int Np, cudaStream_t s) {
 tc_status cgemm_oz(int mode, const CUtensorMap& tmU, const CUtensorMap& tmP, const OzEpi& ep, cudaStream_t s) {
     if (ep.Np < 128 || ep.Np % 128 != 0 || ep.tiles * 128 != ep.Np)
         return fail(TC_ERR_INVALID_ARG, "cgemm_oz: padded dimension must be a multiple of 128");
-    if (ep.Np > kKMax && ep.Np % kKMax != 0)
-        return fail(TC_ERR_INVALID_ARG, "cgemm_oz: dimension above %d must be a multiple of it", kKMax);
+    const OzDigits dg = oz_digits(ep.Np);
+    if (ep.bits != dg.bits || ep.slices != dg.slices)
+        return fail(TC_ERR_INVALID_ARG, "cgemm_oz: digit width does not match the dimension");
+    if (ep.Np > dg.kmax && ep.Np % dg.kmax != 0)
+        return fail(TC_ERR_INVALID_ARG, "cgemm_oz: dimension above %d must be a multiple of it", dg.kmax);
     // CTA pairs sharing the U panels when the tile count is even
     const bool pairs = ep.tiles % 2 == 0 && oz_cluster_enabled();
     if (mode == 0) return pairs ? launch<0, 2>(tmU, tmP, ep, s) : launch<0, 1>(tmU, tmP, ep, s);
@@ -488,24 +518,38 @@ tc_status cgemm_oz(int mode, const CUtensorMap& tmU, const CUtensorMap& tmP, con
     return fail(TC_ERR_INVALID_ARG, "cgemm_oz: mode");
 }
 
-size_t oz_slice_bytes(int Np) { return round256((size_t)2 * kOzSlices * Np * Np * sizeof(__nv_bfloat16)); }
+size_t oz_slice_bytes(int Np) {
+    return round256((size_t)2 * oz_digits(Np).slices * Np * Np * sizeof(__nv_bfloat16));
+}
 
 size_t oz_mat_bytes(int Np) { return oz_slice_bytes(Np) + round256((size_t)Np * sizeof(int)); }
 
 tc_status oz_mat_init(OzMat& m, Arena& ar, int Np) {
     m.Np = Np;
+    m.dg = oz_digits(Np);
     m.slices = ar.take<uint8_t>(oz_slice_bytes(Np));
     m.ex = ar.take<int>((size_t)Np);
     if (!m.ex) return fail(TC_ERR_WORKSPACE, "FP64 emulation: workspace too small");
-    return make_part_map(&m.map, m.slices, Np, 2 * kOzSlices, TC_BF16X3);
+    return make_part_map(&m.map, m.slices, Np, 2 * m.dg.slices, TC_BF16X3);
+}
+
+tc_status oz_mat_view(OzMat& view, const OzMat& base, int Np) {
+    if (Np > base.Np || oz_slice_bytes(Np) > oz_slice_bytes(base.Np))
+        return fail(TC_ERR_INVALID_ARG, "FP64 emulation: operand view larger than its buffers");
+    view = base;
+    view.Np = Np;
+    view.dg = oz_digits(Np);
+    return make_part_map(&view.map, base.slices, Np, 2 * view.dg.slices, TC_BF16X3);
 }
 
 tc_status oz_mat_load(OzMat& m, const double* re, const double* im, bool interleaved, bool conj, int N, size_t ld,
                       cudaStream_t s) {
-    return oz_slice(re, im, interleaved, conj, N, ld, m.Np, m.slices, m.ex, s);
+    return oz_slice(re, im, interleaved, conj, N, ld, m.Np, m.dg, m.slices, m.ex, s);
 }
 
 tc_status oz_product(int mode, const OzMat& A, const OzMat& B, const OzOut& out, int group, cudaStream_t s) {
+    if (A.Np != B.Np || A.dg.bits != B.dg.bits)
+        return fail(TC_ERR_INVALID_ARG, "FP64 emulation: operands of different sizes");
     OzEpi ep{};
     ep.Np = A.Np;
     ep.tiles = A.Np / 128;
@@ -516,6 +560,8 @@ tc_status oz_product(int mode, const OzMat& A, const OzMat& B, const OzOut& out,
     ep.yi = out.yi;
     ep.lo_r = out.lo_r;
     ep.lo_i = out.lo_i;
+    ep.bits = A.dg.bits;
+    ep.slices = A.dg.slices;
     ep.status = device_status_word();
     TC_TRY(cgemm_oz(mode, A.map, B.map, ep, s));
     if (mode == 1) TC_TRY(oz_mirror(out.yr, out.yi, A.Np, s));

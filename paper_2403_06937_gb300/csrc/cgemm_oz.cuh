@@ -8,8 +8,21 @@
 
 namespace tc {
 
-constexpr int kOzSlices = 9;                                   // base-64 digits per entry (54 bits)
-constexpr int kOzPairs = kOzSlices * (kOzSlices + 1) / 2;      // slice pairs with t + u <= 8
+// Digit width of the slices for the inner dimension K of a product (the
+// padded size Np).  One pass sums K products of two digits of magnitude at
+// most 2^(bits - 1); K 2^(2 bits - 2) <= 2^24 keeps that FP32 sum exact, so
+// the smaller K is, the wider the digits and the fewer the slice pairs:
+//   K <= 1024:  8-bit digits, 7 slices (56 bits), 28 pairs
+//   K <= 4096:  7-bit digits, 8 slices (56 bits), 36 pairs
+//   otherwise:  6-bit digits, 9 slices (54 bits), 45 pairs; K in chunks of 16384
+// TC_OZ_BITS=6 in the environment keeps the 6-bit digits at every size.
+struct OzDigits {
+    int bits;     // digit width
+    int slices;   // digits per entry
+    int pairs;    // slice pairs (t, u) with t + u < slices
+    int kmax;     // K per exact pass, 2^(26 - 2 bits)
+};
+OzDigits oz_digits(int Np);
 
 struct OzEpi {
     int Np;             // padded dimension, a multiple of 128
@@ -21,15 +34,17 @@ struct OzEpi {
     double* yi;
     long long* lo_r;    // int64 scratch planes [Np][Np] of the low levels
     long long* lo_i;
+    int bits;           // digit width and slices per entry (oz_digits(Np))
+    int slices;
     unsigned* status;
     unsigned long long wait_ns;   // limit of every barrier wait (0 = 2 s)
 };
 
-// Slices [2 * kOzSlices][Np][Np] (BF16 digits: re slices, then im slices) and
-// row exponents ex[Np] of the N x N matrix (zero-padded to Np); conj negates
-// the imaginary part.
+// Slices [2 * S][Np][Np] (BF16 digits: re slices, then im slices; S digits of
+// `bits` bits, oz_digits(Np)) and row exponents ex[Np] of the N x N matrix
+// (zero-padded to Np); conj negates the imaginary part.
 tc_status oz_slice(const double* re, const double* im, bool interleaved, bool conj, int N, size_t ld, int Np,
-                   void* slices, int* ex, cudaStream_t s);
+                   const OzDigits& dg, void* slices, int* ex, cudaStream_t s);
 size_t oz_slice_bytes(int Np);
 // Y = U P^H (mode 0: all tiles; mode 1: block-lower tiles, then oz_mirror)
 tc_status cgemm_oz(int mode, const CUtensorMap& tmU, const CUtensorMap& tmP, const OzEpi& ep, cudaStream_t s);
@@ -45,6 +60,7 @@ struct OzMat {
     int* ex;
     CUtensorMap map;
     int Np;
+    OzDigits dg;   // oz_digits(Np)
 };
 struct OzOut {
     double* yr;        // FP64 planes of the result, row stride Np
@@ -54,6 +70,8 @@ struct OzOut {
 };
 size_t oz_mat_bytes(int Np);
 tc_status oz_mat_init(OzMat& m, Arena& ar, int Np);
+// `view` = `base`'s buffers seen as an operand of the smaller padded size Np
+tc_status oz_mat_view(OzMat& view, const OzMat& base, int Np);
 tc_status oz_mat_load(OzMat& m, const double* re, const double* im, bool interleaved, bool conj, int N, size_t ld,
                       cudaStream_t s);
 // Y = A B^H at FP64 accuracy; mode 1 (Hermitian result): block-lower tiles and the mirror.

@@ -110,12 +110,12 @@ tc_status evolve_oz(const double* U, double* rho, int n, int steps, int renorm_e
     auto one_step = [&](int k, cudaStream_t cs) -> tc_status {
         TC_TRY(oz_mat_load(Ps, Rr, Ri, false, false, N, (size_t)Np, cs));
         {
-            ProductTimer t(8.0 * N3 * kOzPairs, cs);   // X = U rho^H
+            ProductTimer t(8.0 * N3 * Us.dg.pairs, cs);   // X = U rho^H
             TC_TRY(oz_product(0, Us, Ps, X, group, cs));
         }
         TC_TRY(oz_mat_load(Ps, Xr, Xi, false, false, N, (size_t)Np, cs));
         {
-            ProductTimer t(4.0 * N3 * kOzPairs, cs);   // rho' = U X^H, Hermitian half + mirror
+            ProductTimer t(4.0 * N3 * Us.dg.pairs, cs);   // rho' = U X^H, Hermitian half + mirror
             TC_TRY(oz_product(1, Us, Ps, R, group, cs));
         }
         if (renorm_every > 0 && k % renorm_every == 0) {

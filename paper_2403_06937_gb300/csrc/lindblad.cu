@@ -695,11 +695,7 @@ tc_status evolve_oz_blocks(const Layout& L, const Model& m, double kappa, double
     if (!scratch) return fail(TC_ERR_WORKSPACE, "lindblad evolve: workspace too small");
     // the B operand slices seen at each block's padded size (one map per block)
     std::vector<OzMat> Bk(n + 1);
-    for (int k = 0; k <= n; k++) {
-        Bk[k] = Bmax;
-        Bk[k].Np = padded(L.dims[k]);
-        TC_TRY(make_part_map(&Bk[k].map, Bmax.slices, Bk[k].Np, 2 * kOzSlices, TC_BF16X3));
-    }
+    for (int k = 0; k <= n; k++) TC_TRY(oz_mat_view(Bk[k], Bmax, padded(L.dims[k])));
     const BlockSet bs = block_set(L, true);
     const BlockSet pk = block_set(L, false);
     const PartsSet none{};
@@ -715,12 +711,12 @@ tc_status evolve_oz_blocks(const Layout& L, const Model& m, double kappa, double
             const double d3 = (double)d * d * d;
             TC_TRY(oz_mat_load(Bk[k], rr, ri, false, false, d, (size_t)Np, cs));
             {
-                ProductTimer pt(8.0 * d3 * kOzPairs, cs);   // X_k = U_k rho_k
+                ProductTimer pt(8.0 * d3 * Uk[k].dg.pairs, cs);   // X_k = U_k rho_k
                 TC_TRY(oz_product(0, Uk[k], Bk[k], OzOut{Xr, Xi, Lr, Li}, group, cs));
             }
             TC_TRY(oz_mat_load(Bk[k], Xr, Xi, false, false, d, (size_t)Np, cs));
             {
-                ProductTimer pt(4.0 * d3 * kOzPairs, cs);   // rho_k = U_k X_k^H, Hermitian
+                ProductTimer pt(4.0 * d3 * Uk[k].dg.pairs, cs);   // rho_k = U_k X_k^H, Hermitian
                 TC_TRY(oz_product(1, Uk[k], Bk[k], OzOut{rr, ri, Lr, Li}, group, cs));
             }
         }

@@ -8,7 +8,16 @@ contribute at most 8 * 2^10 * 2^-66 2^(e_i + f_j) per term; with
 2^e <= 4 max|row| each of the K terms of a product is within
 2^-48 max|A_i| max|B_j|, so one product is within K 2^-48 max|U| max|P|,
 two products per step.  (The FP64 DMMA reference adds its own K 2^-53.)
+That is the bound of the 6-bit digits (K > 4096); the 7- and 8-bit digits of
+the smaller sizes (56 bits, dropped pairs below 2^-51.2 of the scales) meet
+it with room to spare.  It is a worst case, loose enough that a dropped top
+slice level would pass it: test_single_product_tight checks the typical size
+of the error instead.
 """
+import os
+import subprocess
+import sys
+
 import numpy as np
 import pytest
 import torch
@@ -174,3 +183,92 @@ def test_host_buffers_and_renormalisation(tc):
     rr, oo = tc.evolve(U, half, n, 4, "ozaki", renorm_every=2, params=p)
     tr = oo[:, 2 * n + 2].cpu().numpy()
     assert abs(tr[0] - 0.5) < 1e-15 and np.max(np.abs(tr[2:] - 1.0)) < 1e-14
+
+
+def _uuh(tc, n, precision, seed=3):
+    """One step from rho0 = I is the single product U U^H (the first product,
+    U I, only rounds U to its slice grid): U a random complex symmetric matrix
+    (the form every e^{-iH dt} of a real symmetric H has, which the FP64 path
+    relies on), max |U| = 1."""
+    N = 1 << n
+    rng = np.random.default_rng(seed + n)
+    A = rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N))
+    U = (A + A.T) / 2
+    U /= np.max(np.abs(U))
+    Ud = torch.from_numpy(U).cuda()
+    p = _params(tc, n, W.draw_couplings(n, 2), 1.0, 1.0)
+    eye = torch.eye(N, dtype=torch.complex128, device="cuda")
+    out, _ = tc.evolve(Ud, eye, n, 1, precision, params=p)
+    tc.sync_status()
+    return U, out
+
+
+def _tight(K, ref):
+    """Off the diagonal 16 sqrt(K) 2^-53 of the operand scales (max |U| = 1)
+    plus 16 units of 2^-53 |entry|; on it (a coherent sum of K positive
+    terms, which an FP64 reference summing in sequence rounds K times at the
+    size of the sum) 16 sqrt(K) 2^-53 |entry| in addition."""
+    base = 16 * np.sqrt(K) * 2.0 ** -53
+    tol = base + 16 * 2.0 ** -53 * np.abs(ref)
+    i = np.arange(ref.shape[0])
+    tol[i, i] += base * np.abs(ref[i, i])
+    return tol
+
+
+def _ratio(got, ref, K):
+    return float(np.max(np.abs(got - ref) / _tight(K, ref)))
+
+
+@pytest.mark.parametrize("n", [7, 10, 11, 12, 13])
+def test_single_product_tight(tc, n):
+    """U U^H against numpy (blocked FP64 sums; up to n = 12) within _tight.
+    A CPU emulation of the exact slice arithmetic puts a correct product at
+    0.04-0.2 of that bound (7- and 8-bit digits at the low end, 6-bit at the
+    high end) and numpy's at about 0.2; leaving out the top slice level
+    (t + u = S - 1) would put it at 5-16 times the bound: this catches that
+    where the worst-case bound above cannot.  Against the FP64 DMMA path,
+    whose K-term sums run in sequence (an error near K 2^-53 of the operand
+    scales, measured 0.27 K 2^-53 at n = 13), the bound adds K 2^-53."""
+    K = max(1 << n, 128)
+    U, oz = _uuh(tc, n, "ozaki")
+    got = oz.cpu().numpy()
+    if n <= 12:
+        r = _ratio(got, U @ U.conj().T, K)
+        print("n=%d: error / bound %.3f against numpy" % (n, r))
+        assert r < 1.0
+    _, ref = _uuh(tc, n, "fp64")
+    ref = ref.cpu().numpy()
+    d = np.max(np.abs(got - ref) / (_tight(K, ref) + K * 2.0 ** -53))
+    print("n=%d: error / bound %.3f against the FP64 path" % (n, d))
+    assert d < 1.0
+    assert torch.equal(oz, oz.conj().T)
+    del oz
+    torch.cuda.empty_cache()
+
+
+def test_six_bit_digits_at_every_size(tc, tmp_path):
+    """TC_OZ_BITS=6 keeps the 6-bit digits (9 slices, 45 pairs) at the sizes
+    that default to 8- and 7-bit ones (n = 10, 12): the same tight bound
+    against numpy holds, and the low bits differ from the default form's, so
+    the setting took effect."""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    for n in (10, 12):
+        path = str(tmp_path / ("six_%d.npy" % n))
+        script = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, %r)
+sys.path.insert(0, %r)
+import paper_2403_06937_gb300 as tc
+from test_gpu_ozaki import _uuh
+_, out = _uuh(tc, %d, 'ozaki')
+np.save(%r, out.cpu().numpy())
+""" % (root, os.path.join(root, "tests"), n, path)
+        subprocess.run([sys.executable, "-c", script], env=dict(os.environ, TC_OZ_BITS="6"), check=True)
+        six = np.load(path)
+        U, wide = _uuh(tc, n, "ozaki")
+        wide = wide.cpu().numpy()
+        ref = U @ U.conj().T
+        r6, rw = _ratio(six, ref, 1 << n), _ratio(wide, ref, 1 << n)
+        print("n=%d: error / bound %.3f (6-bit digits), %.3f (default)" % (n, r6, rw))
+        assert r6 < 1.0 and rw < 1.0
+        assert not np.array_equal(six, wide)
