@@ -102,49 +102,81 @@ __device__ __forceinline__ void oz_epilogue(uint32_t tmem, int warp, int lane, i
         tmem_ld16(tl + 128 + c, d1i);      // U_r P_i^T
         tmem_ld16(tl + 256 + c, d2r);      // U_i P_r^T
         tmem_ld16(tl + 384 + c, d2i);      // U_i P_i^T
-        tmem_wait_ld();
         const size_t o = gi * Np + (size_t)J * 128 + c;
         long long* ar = to_hi ? reinterpret_cast<long long*>(ep.yr) + o : ep.lo_r + o;
         long long* ai = to_hi ? reinterpret_cast<long long*>(ep.yi) + o : ep.lo_i + o;
         longlong2* vr2 = reinterpret_cast<longlong2*>(ar);
         longlong2* vi2 = reinterpret_cast<longlong2*>(ai);
-#pragma unroll
-        for (int h = 0; h < 8; h++) {
-            long long xr[2], xi[2];
-#pragma unroll
-            for (int w = 0; w < 2; w++) {
-                const int q = 2 * h + w;
-                const int sr = __float2int_rn(d1r[q]) + __float2int_rn(d2i[q]);
-                const int si = __float2int_rn(d2r[q]) - __float2int_rn(d1i[q]);
-                xr[w] = (long long)sr << shift;
-                xi[w] = (long long)si << shift;
-            }
+        // The exact pass sums as int64 pairs, two columns per entry of x.
+        auto sums = [&](int h, longlong2& xr, longlong2& xi) {
+            const int q = 2 * h;
+            xr.x = (long long)(__float2int_rn(d1r[q]) + __float2int_rn(d2i[q])) << shift;
+            xr.y = (long long)(__float2int_rn(d1r[q + 1]) + __float2int_rn(d2i[q + 1])) << shift;
+            xi.x = (long long)(__float2int_rn(d2r[q]) - __float2int_rn(d1i[q])) << shift;
+            xi.y = (long long)(__float2int_rn(d2r[q + 1]) - __float2int_rn(d1i[q + 1])) << shift;
+        };
+        // Every load of a batch is issued before its first store (the planes
+        // are separate buffers, which the compiler cannot see), so a chunk
+        // waits for one memory round trip, not one per pair of columns.
+        if (!last) {
+            longlong2 pr[8], pi[8];
             if (!first) {
-                const longlong2 a = vr2[h], b = vi2[h];
-                xr[0] += a.x;
-                xr[1] += a.y;
-                xi[0] += b.x;
-                xi[1] += b.y;
-            }
-            if (!last) {
-                vr2[h] = make_longlong2(xr[0], xr[1]);
-                vi2[h] = make_longlong2(xi[0], xi[1]);
-            } else {
-                // the last pass is of level S - 1 (lo): combine with hi into FP64
-                const longlong2 hr = reinterpret_cast<const longlong2*>(ep.yr + o)[h];
-                const longlong2 hi_ = reinterpret_cast<const longlong2*>(ep.yi + o)[h];
-                const long long hr_[2] = {hr.x, hr.y}, hii[2] = {hi_.x, hi_.y};
-                double yr[2], yi[2];
 #pragma unroll
-                for (int w = 0; w < 2; w++) {
-                    const int q = 2 * h + w;
-                    const int ej = ep.eP[(size_t)J * 128 + c + q];
-                    const double s_hi = pow2(ei + ej - e_hi), s_lo = pow2(ei + ej - e_lo);
-                    yr[w] = (double)hr_[w] * s_hi + (double)xr[w] * s_lo;
-                    yi[w] = (double)hii[w] * s_hi + (double)xi[w] * s_lo;
+                for (int h = 0; h < 8; h++) {
+                    pr[h] = vr2[h];
+                    pi[h] = vi2[h];
                 }
-                reinterpret_cast<double2*>(ep.yr + o)[h] = make_double2(yr[0], yr[1]);
-                reinterpret_cast<double2*>(ep.yi + o)[h] = make_double2(yi[0], yi[1]);
+            }
+            tmem_wait_ld();
+#pragma unroll
+            for (int h = 0; h < 8; h++) {
+                longlong2 xr, xi;
+                sums(h, xr, xi);
+                if (!first) {
+                    xr.x += pr[h].x;
+                    xr.y += pr[h].y;
+                    xi.x += pi[h].x;
+                    xi.y += pi[h].y;
+                }
+                vr2[h] = xr;
+                vi2[h] = xi;
+            }
+        } else {
+            // the last pass is of level S - 1 (lo): combine with hi into FP64,
+            // eight columns per batch
+            tmem_wait_ld();
+            const longlong2* hr2 = reinterpret_cast<const longlong2*>(ep.yr + o);
+            const longlong2* hi2 = reinterpret_cast<const longlong2*>(ep.yi + o);
+#pragma unroll
+            for (int g = 0; g < 8; g += 4) {
+                longlong2 pr[4], pi[4], hr[4], hi[4];
+                int ej[8];
+#pragma unroll
+                for (int h = 0; h < 4; h++) {
+                    pr[h] = first ? make_longlong2(0, 0) : vr2[g + h];
+                    pi[h] = first ? make_longlong2(0, 0) : vi2[g + h];
+                    hr[h] = hr2[g + h];
+                    hi[h] = hi2[g + h];
+                    ej[2 * h] = ep.eP[(size_t)J * 128 + c + 2 * (g + h)];
+                    ej[2 * h + 1] = ep.eP[(size_t)J * 128 + c + 2 * (g + h) + 1];
+                }
+#pragma unroll
+                for (int h = 0; h < 4; h++) {
+                    longlong2 xr, xi;
+                    sums(g + h, xr, xi);
+                    const long long lr[2] = {xr.x + pr[h].x, xr.y + pr[h].y};
+                    const long long li[2] = {xi.x + pi[h].x, xi.y + pi[h].y};
+                    const long long hr_[2] = {hr[h].x, hr[h].y}, hii[2] = {hi[h].x, hi[h].y};
+                    double yr[2], yi[2];
+#pragma unroll
+                    for (int w = 0; w < 2; w++) {
+                        const double s_hi = pow2(ei + ej[2 * h + w] - e_hi), s_lo = pow2(ei + ej[2 * h + w] - e_lo);
+                        yr[w] = (double)hr_[w] * s_hi + (double)lr[w] * s_lo;
+                        yi[w] = (double)hii[w] * s_hi + (double)li[w] * s_lo;
+                    }
+                    reinterpret_cast<double2*>(ep.yr + o)[g + h] = make_double2(yr[0], yr[1]);
+                    reinterpret_cast<double2*>(ep.yi + o)[g + h] = make_double2(yi[0], yi[1]);
+                }
             }
         }
     }
