@@ -182,10 +182,32 @@ __device__ __forceinline__ void oz_epilogue(uint32_t tmem, int warp, int lane, i
     }
 }
 
+// CTA pairs sharing the P panel: pair q covers tiles (2i, J) and
+// (2i + 1, J), rank r taking I = 2i + r; mode 0 all T columns of each row
+// pair (T even), mode 1 the columns J <= 2i + 1 (the tile (2i, 2i + 1) lies
+// above the diagonal: computed, then overwritten by the mirror).
+__device__ __forceinline__ void pair_tile_rows(int mode, int T, int q, int rank, int& I, int& J) {
+    if (mode == 0) {
+        I = 2 * (q / T) + rank;
+        J = q % T;
+        return;
+    }
+    int i = 0, base = 0;
+    while (base + 2 * i + 2 <= q) {
+        base += 2 * i + 2;
+        i++;
+    }
+    I = 2 * i + rank;
+    J = q - base;
+}
+
 // CL = 2: clusters of two CTAs with the same row tile I: rank 0 loads the
 // U_r slice and rank 1 the U_i slice of every stage into both CTAs (TMA
-// multicast), so each U panel crosses L2 once per pair; each CTA's MMA
-// completion releases the stage in both CTAs (empty barriers count 2).
+// multicast), so each U panel crosses L2 once per pair.  CL = 3: clusters of
+// two CTAs with the same column tile J: rank 0 loads the P_r slice and rank 1
+// the P_i slice into both, and each CTA loads its own U panel (kept in L2).
+// In both, each CTA's MMA completion releases the stage in both CTAs (empty
+// barriers count 2).
 template <int MODE, int CL>
 __global__ void __launch_bounds__(kThreads, 1)
     cgemm_oz_kernel(const __grid_constant__ CUtensorMap tmU, const __grid_constant__ CUtensorMap tmP, OzEpi ep) {
@@ -204,16 +226,19 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t lim = ep.wait_ns ? ep.wait_ns : kWaitLimitNs;
     int I, J;
-    const uint32_t rank = CL == 2 ? cluster_ctarank() : 0u;
+    constexpr bool kPair = CL >= 2;
+    const uint32_t rank = kPair ? cluster_ctarank() : 0u;
     if (CL == 2)
         pair_tile(MODE, ep.tiles, (int)(blockIdx.x >> 1), (int)rank, I, J);
+    else if (CL == 3)
+        pair_tile_rows(MODE, ep.tiles, (int)(blockIdx.x >> 1), (int)rank, I, J);
     else
         tile_of(MODE, ep.tiles, ep.group, blockIdx.x, I, J);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; s++) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], CL);
+            mbar_init(&empty[s], kPair ? 2 : 1);
         }
         mbar_init(accum, 1);
         mbar_init(tmem_empty, 1);
@@ -230,7 +255,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         prefetch_tmap(&tmP);
     }
     __syncthreads();
-    if (CL == 2) cluster_sync();   // the peer's barriers exist before anything is multicast to them
+    if (kPair) cluster_sync();   // the peer's barriers exist before anything is multicast to them
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     const int S = ep.slices;
@@ -270,17 +295,23 @@ __global__ void __launch_bounds__(kThreads, 1)
                         tma_load_3d_hint(saddr(st), &tmU, fb, kx, I * 128, t, keep);                       // U_r
                         tma_load_3d_hint(saddr(st + kATile), &tmU, fb, kx, I * 128, S + t, keep);          // U_i
                     }
-                    tma_load_3d(saddr(st + 2 * kATile), &tmP, fb, kx, J * 128, u);                     // P_r slice u
-                    tma_load_3d(saddr(st + 2 * kATile + 128 * kRowBytes), &tmP, fb, kx, J * 128,
-                                S + u);                                                                // P_i slice u
+                    if (CL == 3) {
+                        // P_r slice u from rank 0, P_i slice u from rank 1, into both CTAs
+                        tma_load_3d_multicast(saddr(st + 2 * kATile + rank * 128 * kRowBytes), &tmP, fb, kx,
+                                              J * 128, (int)rank * S + u, (uint16_t)0x3);
+                    } else {
+                        tma_load_3d(saddr(st + 2 * kATile), &tmP, fb, kx, J * 128, u);                 // P_r slice u
+                        tma_load_3d(saddr(st + 2 * kATile + 128 * kRowBytes), &tmP, fb, kx, J * 128,
+                                    S + u);                                                            // P_i slice u
+                    }
                 }
             }
             if (*abort) {
                 // let the copies already issued land before the CTA goes away
                 for (uint32_t k = it > (uint32_t)kStages ? it - kStages : 0u; k < it; k++)
                     (void)mbar_wait_bounded(&full[k % kStages], (k / kStages) & 1u, nullptr,
-                                            CL == 2 ? 10000000ull : lim, 0);
-            } else if (CL == 2) {
+                                            kPair ? 10000000ull : lim, 0);
+            } else if (kPair) {
                 // the last use of every stage released by both CTAs' MMAs: no arrival of
                 // the peer is still on its way to this CTA's barriers when it leaves
                 for (uint32_t k = it > (uint32_t)kStages ? it - kStages : 0u; k < it; k++)
@@ -307,7 +338,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const uint64_t bd = desc_kmajor_sw32(saddr(st + 2 * kATile));
                     umma<0>(tmem, desc_kmajor_sw32(saddr(st)), bd, kIdesc, kb > 0 ? 1u : 0u);
                     umma<0>(tmem + 256, desc_kmajor_sw32(saddr(st + kATile)), bd, kIdesc, kb > 0 ? 1u : 0u);
-                    if (CL == 2)
+                    if (kPair)
                         umma_commit_multicast(saddr(&empty[s]), (uint16_t)0x3);
                     else
                         umma_commit(saddr(&empty[s]));
@@ -350,7 +381,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncwarp();
     tc_fence_before();
     __syncthreads();
-    if (CL == 2) cluster_sync();   // neither CTA leaves while the other may still write to it
+    if (kPair) cluster_sync();   // neither CTA leaves while the other may still write to it
     if (warp == 0) {
         tc_fence_after();
         tmem_dealloc(tmem, 512);
@@ -460,12 +491,15 @@ tc_status launch(const CUtensorMap& tmU, const CUtensorMap& tmP, const OzEpi& ep
         TC_LAUNCH_CHECK();
         return TC_OK;
     }
-    // pairs of CTAs: mode 0 T * T / 2, mode 1 sum over rows of (I / 2 + 1)
+    // pairs of CTAs: mode 0 T * T / 2; mode 1 sharing U: sum over rows of
+    // (I / 2 + 1), sharing P: sum over row pairs i of (2 i + 2)
     unsigned pairs = 0;
     if (MODE == 0) {
         pairs = (unsigned)(T * (T / 2));
-    } else {
+    } else if (CL == 2) {
         for (int I = 0; I < T; I++) pairs += (unsigned)(I / 2 + 1);
+    } else {
+        for (int i = 0; i < T / 2; i++) pairs += (unsigned)(2 * i + 2);
     }
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(2 * pairs);
@@ -484,23 +518,28 @@ tc_status launch(const CUtensorMap& tmU, const CUtensorMap& tmP, const OzEpi& ep
     return TC_OK;
 }
 
-// -1: not chosen yet (TC_OZ_CLUSTER=0|1 in the environment, else on: the
-// pairs give the same bits and 15 % more speed at n = 14)
-std::atomic<int> g_oz_cluster{-1};
+// -2: not read yet; -1: by size; else TC_OZ_CLUSTER from the environment
+// (0 single CTAs, 1 pairs sharing U, 2 pairs sharing P).  All give the same
+// bits.  By size: pairs sharing P from 128 tiles a side (n = 14: half the
+// DRAM reads of pairs sharing U, 2 % faster), pairs sharing U below (n = 12:
+// 1.4 % faster than sharing P; both 15 % faster than single CTAs at n = 14).
+std::atomic<int> g_oz_cluster{-2};
 // -1: not chosen yet (TC_OZ_BITS=6 in the environment: 6-bit digits at every
 // size; else the widest digits K allows)
 std::atomic<int> g_oz_narrow{-1};
 
 }  // namespace
 
-bool oz_cluster_enabled() {
+int oz_cluster_mode(int tiles) {
     int v = g_oz_cluster.load();
-    if (v < 0) {
+    if (v == -2) {
         const char* e = std::getenv("TC_OZ_CLUSTER");
-        v = e ? (std::atoi(e) != 0 ? 1 : 0) : 1;
+        v = e ? std::atoi(e) : -1;
+        v = v < -1 || v > 2 ? -1 : v;
         g_oz_cluster.store(v);
     }
-    return v != 0;
+    if (tiles % 2 != 0) return 0;
+    return v >= 0 ? v : (tiles >= 128 ? 2 : 1);
 }
 
 OzDigits oz_digits(int Np) {
@@ -543,10 +582,14 @@ tc_status cgemm_oz(int mode, const CUtensorMap& tmU, const CUtensorMap& tmP, con
         return fail(TC_ERR_INVALID_ARG, "cgemm_oz: digit width does not match the dimension");
     if (ep.Np > dg.kmax && ep.Np % dg.kmax != 0)
         return fail(TC_ERR_INVALID_ARG, "cgemm_oz: dimension above %d must be a multiple of it", dg.kmax);
-    // CTA pairs sharing the U panels when the tile count is even
-    const bool pairs = ep.tiles % 2 == 0 && oz_cluster_enabled();
-    if (mode == 0) return pairs ? launch<0, 2>(tmU, tmP, ep, s) : launch<0, 1>(tmU, tmP, ep, s);
-    if (mode == 1) return pairs ? launch<1, 2>(tmU, tmP, ep, s) : launch<1, 1>(tmU, tmP, ep, s);
+    // CTA pairs sharing the U (or P) panels when the tile count is even
+    const int cl = oz_cluster_mode(ep.tiles);
+    if (mode == 0)
+        return cl == 2 ? launch<0, 3>(tmU, tmP, ep, s) : cl == 1 ? launch<0, 2>(tmU, tmP, ep, s)
+                                                                 : launch<0, 1>(tmU, tmP, ep, s);
+    if (mode == 1)
+        return cl == 2 ? launch<1, 3>(tmU, tmP, ep, s) : cl == 1 ? launch<1, 2>(tmU, tmP, ep, s)
+                                                                 : launch<1, 1>(tmU, tmP, ep, s);
     return fail(TC_ERR_INVALID_ARG, "cgemm_oz: mode");
 }
 
