@@ -127,8 +127,8 @@ class Clocks:
         os.unlink(self.path)
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
-                "samples": len(sm), "power_w_max": float(max(power)) if power else None}
+        return {"sm_mhz": float(np.median(sm)), "sm_mhz_min": float(min(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm), "power_w_max": float(max(power)) if power else None}
 
 
 # ------------------------------------------------------------------ peaks
@@ -396,6 +396,8 @@ def run_ours(a, cfg):
             torch.distributed.barrier()
         torch.cuda.synchronize()
         calls = []
+        eclk = Clocks(local)
+        eclk.start()
         t0 = time.perf_counter()
         for _ in range(a.steps):
             tc0 = time.perf_counter()
@@ -403,10 +405,11 @@ def run_ours(a, cfg):
             calls.append(1e3 * (time.perf_counter() - tc0))
         torch.cuda.synchronize()
         te = max_over_ranks(time.perf_counter() - t0, world)
+        eck = eclk.stop()
         line["e2e"] = {"value": world * a.steps / te, "unit": "steps/s", "h2d_bytes_per_step": 16 * N * N,
                        "d2h_bytes_per_step": 16 * N * N + 2 * (2 * n + 5) * 8,
                        "api": "tc_evolve_host (C ABI, pinned host rho, one step per call)",
-                       "call_ms": [round(c, 1) for c in calls]}
+                       "call_ms": [round(c, 1) for c in calls], "clocks": eck}
         del rho_h, hw
 
     if not a.no_compare:
