@@ -358,6 +358,12 @@ TC_API tc_status tc_evolve_backward(const tc_params* params, double dt, int step
  * copies rho and the observable rows back, and synchronises `stream` before
  * returning (the results are in host memory on return).  Page-locked host
  * buffers give the full copy bandwidth; pageable ones work but copy slower.
+ * In the tensor-core forms with N >= 2048 the copies overlap the products:
+ * rho moves in and out in 2 or 4 row blocks on an internal copy stream,
+ * the first product of step 1 runs by column blocks as their rows arrive,
+ * and the second product of the last step runs bottom-up by row blocks,
+ * each finished block converted and copied out while the rows above are
+ * computed; the results are the same bits as tc_evolve's.
  *  U        : device, N*N c128 (as tc_evolve), 16-byte aligned.
  *  rho_host : host, N*N c128, in/out.
  *  obs_host : host, (steps + 1) * TC_OBS_STRIDE(n) doubles, or NULL.

@@ -457,15 +457,18 @@ TC_API tc_status tc_evolve_host(const void* U, void* rho_host, int n, int steps,
     Arena ar{static_cast<char*>(work), work_bytes, 0};
     double* rho_dev = ar.take<double>(2 * N * N);
     double* obs_dev = ar.take<double>((size_t)(steps + 1) * (2 * n + 5));
-    TC_CUDA(cudaMemcpyAsync(rho_dev, rho_host, 16 * N * N, cudaMemcpyHostToDevice, s));
     double* od = obs_host ? obs_dev : nullptr;
     const double* Ud = static_cast<const double*>(U);
-    tc_status st = precision == TC_FP64         ? evolve_f64(Ud, rho_dev, n, steps, renorm_every, mp, od, ar, s)
-                   : precision == TC_FP64_OZAKI ? evolve_oz(Ud, rho_dev, n, steps, renorm_every, mp, od, ar, s)
-                                                : evolve_lowp(Ud, rho_dev, n, steps, precision, renorm_every, mp,
-                                                              od, ar, s);
-    if (st != TC_OK) return st;
-    TC_CUDA(cudaMemcpyAsync(rho_host, rho_dev, 16 * N * N, cudaMemcpyDeviceToHost, s));
+    if (precision == TC_FP64 || precision == TC_FP64_OZAKI) {
+        TC_CUDA(cudaMemcpyAsync(rho_dev, rho_host, 16 * N * N, cudaMemcpyHostToDevice, s));
+        TC_TRY(precision == TC_FP64 ? evolve_f64(Ud, rho_dev, n, steps, renorm_every, mp, od, ar, s)
+                                    : evolve_oz(Ud, rho_dev, n, steps, renorm_every, mp, od, ar, s));
+        TC_CUDA(cudaMemcpyAsync(rho_host, rho_dev, 16 * N * N, cudaMemcpyDeviceToHost, s));
+    } else {
+        // copies overlapped with the first and last products (row blocks on a copy stream)
+        TC_TRY(evolve_lowp_host(Ud, static_cast<double*>(rho_host), rho_dev, n, steps, precision, renorm_every, mp,
+                                od, ar, s));
+    }
     if (obs_host)
         TC_CUDA(cudaMemcpyAsync(obs_host, obs_dev, (size_t)(steps + 1) * (2 * n + 5) * sizeof(double),
                                 cudaMemcpyDeviceToHost, s));

@@ -52,24 +52,27 @@ __device__ __forceinline__ void tri_decode(int b, int& i, int& j) {
 
 // Tile b of the launch -> (I, J).  Both orders keep the CTAs that run at the
 // same time on few operand panels, so the panels are re-read from L2:
-//  mode 0 (all T x T tiles): groups of G row tiles, column by column;
-//  mode 1 (block-lower tiles): G x G super-blocks of the lower triangle, row
+//  mode 0 (T x T tiles, or the columns [lo, hi)): groups of G row tiles,
+//  column by column;
+//  mode 1 (block-lower tiles, or those of the rows [lo, hi); lo a multiple of
+//  G, hi a multiple of G or T): G x G super-blocks of the lower triangle, row
 //  by row; inside a super-block the tiles go column by column (the diagonal
 //  super-blocks hold only their lower half).
-__device__ __forceinline__ void tile_of(int mode, int T, int G, int b, int& I, int& J) {
+__device__ __forceinline__ void tile_of_range(int mode, int T, int G, int lo, int hi, int b, int& I, int& J) {
     if (G < 1) G = 1;
     if (mode == 0) {
-        int per_group = G * T;
+        const int C = hi - lo;
+        int per_group = G * C;
         int g = b / per_group;
         int first = g * G;
         int rows = min(G, T - first);
         int in = b % per_group;
         I = first + in % rows;
-        J = in / rows;
+        J = lo + in / rows;
         return;
     }
-    const int SB = (T + G - 1) / G;
-    for (int bi = 0; bi < SB; bi++) {
+    const int SB0 = lo / G, SB1 = (hi + G - 1) / G;
+    for (int bi = SB0; bi < SB1; bi++) {
         const int rows = min(G, T - bi * G);
         for (int bj = 0; bj <= bi; bj++) {
             const int cols = min(G, T - bj * G);
@@ -89,7 +92,11 @@ __device__ __forceinline__ void tile_of(int mode, int T, int G, int b, int& I, i
             b -= cnt;
         }
     }
-    I = J = 0;   // not reached for b < T (T + 1) / 2
+    I = J = 0;   // not reached for b below the launch's tile count
+}
+
+__device__ __forceinline__ void tile_of(int mode, int T, int G, int b, int& I, int& J) {
+    tile_of_range(mode, T, G, 0, T, b, I, J);
 }
 
 // CTA pairs (clusters of 2): pair q covers tiles (I, 2j) and (I, 2j + 1), rank

@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t lim = ep.wait_ns ? ep.wait_ns : kWaitLimitNs;
     int I, J;
-    tile_of(MODE, ep.tiles, ep.group, blockIdx.x, I, J);
+    tile_of_range(MODE, ep.tiles, ep.group, ep.lo, ep.hi > 0 ? ep.hi : ep.tiles, blockIdx.x, I, J);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; s++) {
@@ -190,7 +190,9 @@ tc_status launch(const CUtensorMap& tmU, const CUtensorMap& tmP, const CgemmEpi&
         attr_set[dev] = true;
     }
     const int T = ep.tiles;
-    const unsigned grid = MODE == 0 ? (unsigned)(T * T) : (unsigned)(T * (T + 1) / 2);
+    const int lo = ep.hi > 0 ? ep.lo : 0, hi = ep.hi > 0 ? ep.hi : T;
+    const unsigned grid =
+        MODE == 0 ? (unsigned)(T * (hi - lo)) : (unsigned)((hi * (hi + 1) - lo * (lo + 1)) / 2);
     k<<<grid, kThreads, smem, s>>>(tmU, tmP, ep);
     TC_LAUNCH_CHECK();
     return TC_OK;
@@ -221,6 +223,14 @@ tc_status cgemm_tc(int precision, int mode, const CUtensorMap& tmU, const CUtens
     if (ep.Np < 128 || ep.Np % 128 != 0 || ep.tiles * 128 != ep.Np)
         return fail(TC_ERR_INVALID_ARG, "cgemm_tc: padded dimension must be a multiple of 128");
     if (mode != 0 && mode != 1) return fail(TC_ERR_INVALID_ARG, "cgemm_tc: mode");
+    if (ep.hi > 0) {
+        const int G = ep.group < 1 ? 1 : ep.group;
+        if (ep.lo < 0 || ep.lo >= ep.hi || ep.hi > ep.tiles)
+            return fail(TC_ERR_INVALID_ARG, "cgemm_tc: tile range [%d, %d) outside [0, %d)", ep.lo, ep.hi, ep.tiles);
+        if (mode == 1 && (ep.lo % G != 0 || (ep.hi % G != 0 && ep.hi != ep.tiles)))
+            return fail(TC_ERR_INVALID_ARG, "cgemm_tc: row range [%d, %d) not aligned to the group %d", ep.lo,
+                        ep.hi, G);
+    }
     if (stages == 0) stages = cgemm_default_stages(precision);
     const bool alt = stages == cgemm_alt_stages(precision);
     if (!alt && stages != cgemm_default_stages(precision))

@@ -27,6 +27,9 @@ struct CgemmEpi {
     unsigned* status;
     unsigned long long wait_ns;   // limit of every barrier wait (0 = 2 s)
     int withhold;                 // fault injection: the producer never fills the first stage
+    int lo, hi;                   // hi > 0: only the tile columns [lo, hi) (mode 0) or the
+                                  // block-lower tiles of the tile rows [lo, hi) (mode 1; lo a
+                                  // multiple of group, hi a multiple of group or tiles)
 };
 
 // stages: TMA ring depth (0 = the largest that fits); the built depths are

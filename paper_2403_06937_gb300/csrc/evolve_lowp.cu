@@ -103,10 +103,14 @@ __global__ void prep_u_kernel(const double2* U, int N, int Np, const double* pha
     }
 }
 
+// rows [r0, r1) of the padded plane
 template <int KIND, int S>
-__global__ void prep_rho_kernel(const double2* rho, int N, int Np, float* Rr, float* Ri, void* parts) {
+__global__ void prep_rho_kernel(const double2* rho, int N, int Np, int r0, int r1, float* Rr, float* Ri,
+                                void* parts) {
     const size_t plane = (size_t)Np * Np;
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < plane; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t first = (size_t)r0 * Np, count = (size_t)(r1 - r0) * Np;
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += (size_t)gridDim.x * blockDim.x) {
+        const size_t e = first + k;
         const size_t i = e / Np, j = e % Np;
         double2 v = make_double2(0.0, 0.0);
         if (i < (size_t)N && j < (size_t)N) v = rho[i * N + j];
@@ -152,9 +156,11 @@ __global__ void trace_f32_kernel(const float* Rr, int N, int Np, double* out) {
     if (threadIdx.x == 0) out[0] = s[0];
 }
 
-__global__ void finish_kernel(const float* Rr, const float* Ri, int N, int Np, double2* rho) {
-    const size_t count = (size_t)N * N;
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x) {
+// rows [r0, r1) of the N x N result
+__global__ void finish_kernel(const float* Rr, const float* Ri, int N, int Np, int r0, int r1, double2* rho) {
+    const size_t first = (size_t)r0 * N, count = (size_t)(r1 - r0) * N;
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += (size_t)gridDim.x * blockDim.x) {
+        const size_t e = first + k;
         const size_t i = e / N, j = e % N;
         rho[e] = make_double2((double)Rr[i * Np + j], (double)Ri[i * Np + j]);
     }
@@ -167,7 +173,7 @@ size_t plane_bytes(int Np, size_t E) { return round256((size_t)Np * Np * E); }
 namespace {
 
 template <int KIND, int S>
-tc_status run_prep(const double* U, const double* rho, LowpBufs& b, cudaStream_t s) {
+tc_status run_prep_u(const double* U, LowpBufs& b, cudaStream_t s) {
     const size_t plane = (size_t)b.Np * b.Np;
     double* phase = b.scratch;   // consumed by prep_u before any other use of scratch
     unit_phase_kernel<<<1, 1024, 0, s>>>(reinterpret_cast<const double2*>(U), b.N, phase);
@@ -175,10 +181,21 @@ tc_status run_prep(const double* U, const double* rho, LowpBufs& b, cudaStream_t
     prep_u_kernel<KIND, S><<<grid_for(plane), 256, 0, s>>>(reinterpret_cast<const double2*>(U), b.N, b.Np, phase,
                                                             b.Uparts);
     TC_LAUNCH_CHECK();
-    prep_rho_kernel<KIND, S><<<grid_for(plane), 256, 0, s>>>(reinterpret_cast<const double2*>(rho), b.N, b.Np, b.Rr,
-                                                               b.Ri, b.Rparts);
+    return TC_OK;
+}
+
+template <int KIND, int S>
+tc_status run_prep_rho(const double* rho, LowpBufs& b, int r0, int r1, cudaStream_t s) {
+    prep_rho_kernel<KIND, S><<<grid_for((size_t)(r1 - r0) * b.Np), 256, 0, s>>>(
+        reinterpret_cast<const double2*>(rho), b.N, b.Np, r0, r1, b.Rr, b.Ri, b.Rparts);
     TC_LAUNCH_CHECK();
     return TC_OK;
+}
+
+template <int KIND, int S>
+tc_status run_prep(const double* U, const double* rho, LowpBufs& b, cudaStream_t s) {
+    TC_TRY((run_prep_u<KIND, S>(U, b, s)));
+    return run_prep_rho<KIND, S>(rho, b, 0, b.Np, s);
 }
 
 template <int KIND, int S>
@@ -211,8 +228,30 @@ tc_status lowp_renorm(int precision, LowpBufs& b, cudaStream_t s) {
     return fail(TC_ERR_INVALID_ARG, "precision");
 }
 
-tc_status lowp_finish(const LowpBufs& b, double* rho, cudaStream_t s) {
-    finish_kernel<<<grid_for((size_t)b.N * b.N), 256, 0, s>>>(b.Rr, b.Ri, b.N, b.Np, reinterpret_cast<double2*>(rho));
+tc_status lowp_prep_u(int precision, const double* U, LowpBufs& b, cudaStream_t s) {
+    switch (precision) {
+        case TC_BF16X3: return run_prep_u<0, 3>(U, b, s);
+        case TC_TF32: return run_prep_u<1, 1>(U, b, s);
+        case TC_TF32X3: return run_prep_u<1, 2>(U, b, s);
+    }
+    return fail(TC_ERR_INVALID_ARG, "precision");
+}
+
+tc_status lowp_prep_rho(int precision, const double* rho, LowpBufs& b, int r0, int r1, cudaStream_t s) {
+    if (r0 < 0 || r0 >= r1 || r1 > b.Np) return fail(TC_ERR_INVALID_ARG, "prep: row range");
+    switch (precision) {
+        case TC_BF16X3: return run_prep_rho<0, 3>(rho, b, r0, r1, s);
+        case TC_TF32: return run_prep_rho<1, 1>(rho, b, r0, r1, s);
+        case TC_TF32X3: return run_prep_rho<1, 2>(rho, b, r0, r1, s);
+    }
+    return fail(TC_ERR_INVALID_ARG, "precision");
+}
+
+tc_status lowp_finish(const LowpBufs& b, double* rho, cudaStream_t s, int r0, int r1) {
+    if (r1 < 0) r1 = b.N;
+    if (r0 < 0 || r0 >= r1 || r1 > b.N) return fail(TC_ERR_INVALID_ARG, "finish: row range");
+    finish_kernel<<<grid_for((size_t)(r1 - r0) * b.N), 256, 0, s>>>(b.Rr, b.Ri, b.N, b.Np, r0, r1,
+                                                                    reinterpret_cast<double2*>(rho));
     TC_LAUNCH_CHECK();
     return TC_OK;
 }
@@ -250,35 +289,53 @@ size_t evolve_lowp_bytes(int n, int precision) {
     return lowp_system_bytes(n, precision);
 }
 
+namespace {
+
+// Tensor maps and epilogues of the two products of a step on the buffers b.
+struct StepPlan {
+    CUtensorMap tmU, tmR, tmX;
+    CgemmEpi e1;   // X = rho^H + V rho^H
+    CgemmEpi e2;   // rho' = X^H + V X^H
+    TuneChoice tune;
+};
+
+tc_status plan_step(int n, int precision, const LowpBufs& b, StepPlan& p) {
+    TC_TRY(make_part_map(&p.tmU, b.Uparts, b.Np, 2 * b.S, precision));
+    TC_TRY(make_part_map(&p.tmR, b.Rparts, b.Np, 2 * b.S, precision));
+    TC_TRY(make_part_map(&p.tmX, b.Xparts, b.Np, 2 * b.S, precision));
+    p.tune = tune_lookup(n, precision);
+    p.e1 = CgemmEpi{};
+    p.e1.Np = b.Np;
+    p.e1.tiles = b.Np / 128;
+    p.e1.group = p.tune.tc_group;
+    p.e1.pr = b.Rr;
+    p.e1.pi = b.Ri;
+    p.e1.parts = b.Xparts;
+    p.e1.yr = b.Xr;
+    p.e1.yi = b.Xi;
+    p.e1.status = device_status_word();
+    p.e2 = p.e1;
+    p.e2.pr = b.Xr;
+    p.e2.pi = b.Xi;
+    p.e2.parts = b.Rparts;
+    p.e2.yr = b.Rr;
+    p.e2.yi = b.Ri;
+    return TC_OK;
+}
+
+}  // namespace
+
 tc_status evolve_lowp(const double* U, double* rho, int n, int steps, int precision, int renorm_every,
                       const Model* m, double* obs, Arena& ar, cudaStream_t s) {
     LowpBufs b{};
     TC_TRY(lowp_carve(n, precision, ar, b));
     const size_t pl = (size_t)b.Np * b.Np;
     if (plane_bytes(b.Np, b.E) != pl * b.E) return fail(TC_ERR_INVALID_ARG, "evolve: plane size");
-
-    CUtensorMap tmU, tmR, tmX;
-    TC_TRY(make_part_map(&tmU, b.Uparts, b.Np, 2 * b.S, precision));
-    TC_TRY(make_part_map(&tmR, b.Rparts, b.Np, 2 * b.S, precision));
-    TC_TRY(make_part_map(&tmX, b.Xparts, b.Np, 2 * b.S, precision));
-
-    const TuneChoice tune = tune_lookup(n, precision);
-    CgemmEpi e1{};                 // X = rho^H + V rho^H
-    e1.Np = b.Np;
-    e1.tiles = b.Np / 128;
-    e1.group = tune.tc_group;
-    e1.pr = b.Rr;
-    e1.pi = b.Ri;
-    e1.parts = b.Xparts;
-    e1.yr = b.Xr;
-    e1.yi = b.Xi;
-    e1.status = device_status_word();
-    CgemmEpi e2 = e1;              // rho' = X^H + V X^H
-    e2.pr = b.Xr;
-    e2.pi = b.Xi;
-    e2.parts = b.Rparts;
-    e2.yr = b.Rr;
-    e2.yi = b.Ri;
+    StepPlan sp{};
+    TC_TRY(plan_step(n, precision, b, sp));
+    const CUtensorMap &tmU = sp.tmU, &tmR = sp.tmR, &tmX = sp.tmX;
+    const CgemmEpi &e1 = sp.e1, &e2 = sp.e2;
+    const TuneChoice& tune = sp.tune;
 
     const int stride = TC_OBS_STRIDE(n);
     const double N3 = (double)b.N * b.N * b.N;
@@ -311,6 +368,122 @@ tc_status evolve_lowp(const double* U, double* rho, int n, int steps, int precis
     };
     auto tail = [&](cudaStream_t cs) -> tc_status { return lowp_finish(b, rho, cs); };
     return run_captured(s, first, rest, tail, steps > 2 && !timing_enabled());
+}
+
+int lowp_host_chunks(int n, int precision) {
+    const int N = 1 << n;
+    if (N < 2048) return 1;
+    const int T = N / 128;
+    int G = tune_lookup(n, precision).tc_group;
+    G = G < 1 ? 1 : G;
+    return T % (4 * G) == 0 ? 4 : T % (2 * G) == 0 ? 2 : 1;
+}
+
+namespace {
+
+// Streams and events of one pipelined call, released when it goes out of scope
+// (the device finishes the queued work first).
+struct CopyLane {
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev[12] = {};
+    int used = 0;
+    ~CopyLane() {
+        for (int i = 0; i < used; i++) cudaEventDestroy(ev[i]);
+        if (cs) cudaStreamDestroy(cs);
+    }
+    tc_status init(int events) {
+        if (events > 12) return fail(TC_ERR_INVALID_ARG, "copy lane: too many events");
+        TC_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        for (; used < events; used++) TC_CUDA(cudaEventCreateWithFlags(&ev[used], cudaEventDisableTiming));
+        return TC_OK;
+    }
+};
+
+}  // namespace
+
+tc_status evolve_lowp_host(const double* U, double* rho_host, double* rho_dev, int n, int steps, int precision,
+                           int renorm_every, const Model* m, double* obs, Arena& ar, cudaStream_t s) {
+    const size_t N = (size_t)1 << n;
+    const size_t bytes = 16 * N * N;
+    const int C = steps >= 1 ? lowp_host_chunks(n, precision) : 1;
+    if (C == 1) {
+        TC_CUDA(cudaMemcpyAsync(rho_dev, rho_host, bytes, cudaMemcpyHostToDevice, s));
+        TC_TRY(evolve_lowp(U, rho_dev, n, steps, precision, renorm_every, m, obs, ar, s));
+        TC_CUDA(cudaMemcpyAsync(rho_host, rho_dev, bytes, cudaMemcpyDeviceToHost, s));
+        return TC_OK;
+    }
+    LowpBufs b{};
+    TC_TRY(lowp_carve(n, precision, ar, b));
+    if (b.Np != (int)N) return fail(TC_ERR_INVALID_ARG, "evolve: pipelined copies need N >= 128");
+    StepPlan sp{};
+    TC_TRY(plan_step(n, precision, b, sp));
+    const int T = b.Np / 128;
+    const size_t R = N / C;                  // rows per chunk
+    const size_t chunk = 16 * R * N;         // bytes per chunk
+    const int stride = TC_OBS_STRIDE(n);
+    CopyLane lane;
+    TC_TRY(lane.init(2 * C + 2));
+    cudaEvent_t* h2d = lane.ev;              // [C]
+    cudaEvent_t* fin = lane.ev + C;          // [C]
+    cudaEvent_t start = lane.ev[2 * C], done = lane.ev[2 * C + 1];
+    auto dev_rows = [&](size_t c) { return reinterpret_cast<char*>(rho_dev) + c * chunk; };
+    auto host_rows = [&](size_t c) { return reinterpret_cast<char*>(rho_host) + c * chunk; };
+
+    // rho in by row blocks on the copy stream (after earlier work on s that may use the staging)
+    TC_CUDA(cudaEventRecord(start, s));
+    TC_CUDA(cudaStreamWaitEvent(lane.cs, start, 0));
+    for (int c = 0; c < C; c++) {
+        TC_CUDA(cudaMemcpyAsync(dev_rows(c), host_rows(c), chunk, cudaMemcpyHostToDevice, lane.cs));
+        TC_CUDA(cudaEventRecord(h2d[c], lane.cs));
+    }
+    TC_TRY(lowp_prep_u(precision, U, b, s));
+    // step 1, first product by column blocks: X[:, J] needs only the rows J of rho
+    for (int c = 0; c < C; c++) {
+        TC_CUDA(cudaStreamWaitEvent(s, h2d[c], 0));
+        TC_TRY(lowp_prep_rho(precision, rho_dev, b, (int)(c * R), (int)((c + 1) * R), s));
+        CgemmEpi e = sp.e1;
+        e.lo = c * T / C;
+        e.hi = (c + 1) * T / C;
+        TC_TRY(cgemm_tc(precision, 0, sp.tmU, sp.tmR, e, s, sp.tune.tc_stages));
+    }
+    if (obs) TC_TRY(launch_observables(kRhoPlanarF32, b.Rr, b.Ri, m, n, obs, b.scratch, s, (size_t)b.Np));
+    for (int k = 1; k <= steps; k++) {
+        if (k > 1) TC_TRY(cgemm_tc(precision, 0, sp.tmU, sp.tmR, sp.e1, s, sp.tune.tc_stages));
+        const bool renorm = renorm_every > 0 && k % renorm_every == 0;
+        if (k < steps || renorm) {
+            TC_TRY(cgemm_tc(precision, 1, sp.tmU, sp.tmX, sp.e2, s, sp.tune.tc_stages));
+            if (renorm) TC_TRY(lowp_renorm(precision, b, s));
+            if (obs) TC_TRY(launch_observables(kRhoPlanarF32, b.Rr, b.Ri, m, n, obs + (size_t)k * stride, b.scratch,
+                                               s, (size_t)b.Np));
+            if (k < steps) continue;
+            // last step renormalised: rho' is whole only now; convert and copy out by row blocks
+            for (int c = 0; c < C; c++) {
+                TC_TRY(lowp_finish(b, rho_dev, s, (int)(c * R), (int)((c + 1) * R)));
+                TC_CUDA(cudaEventRecord(fin[c], s));
+                TC_CUDA(cudaStreamWaitEvent(lane.cs, fin[c], 0));
+                TC_CUDA(cudaMemcpyAsync(host_rows(c), dev_rows(c), chunk, cudaMemcpyDeviceToHost, lane.cs));
+            }
+            break;
+        }
+        // last step, second product bottom-up by row blocks: once the tile rows >= lo are done
+        // (each tile writes itself and its mirror), the rows >= lo * 128 of rho' are final
+        for (int c = C - 1; c >= 0; c--) {
+            CgemmEpi e = sp.e2;
+            e.lo = c * T / C;
+            e.hi = (c + 1) * T / C;
+            TC_TRY(cgemm_tc(precision, 1, sp.tmU, sp.tmX, e, s, sp.tune.tc_stages));
+            TC_TRY(lowp_finish(b, rho_dev, s, (int)(c * R), (int)((c + 1) * R)));
+            TC_CUDA(cudaEventRecord(fin[c], s));
+            TC_CUDA(cudaStreamWaitEvent(lane.cs, fin[c], 0));
+            TC_CUDA(cudaMemcpyAsync(host_rows(c), dev_rows(c), chunk, cudaMemcpyDeviceToHost, lane.cs));
+        }
+        if (obs)
+            TC_TRY(launch_observables(kRhoPlanarF32, b.Rr, b.Ri, m, n, obs + (size_t)k * stride, b.scratch, s,
+                                      (size_t)b.Np));
+    }
+    TC_CUDA(cudaEventRecord(done, lane.cs));
+    TC_CUDA(cudaStreamWaitEvent(s, done, 0));
+    return TC_OK;
 }
 
 }  // namespace tc

@@ -42,6 +42,15 @@ tc_status evolve_oz(const double* U, double* rho, int n, int steps, int renorm_e
 size_t evolve_lowp_bytes(int n, int precision);
 tc_status evolve_lowp(const double* U, double* rho, int n, int steps, int precision, int renorm_every,
                       const Model* m, double* obs, Arena& ar, cudaStream_t s);
+// tc_evolve_host for the tensor-core forms: rho_host copied in by row blocks
+// (the first product starts on the column blocks whose rows have arrived) and
+// out by row blocks (the last second product runs bottom-up, each finished
+// block converted and copied while the rows above are computed), on a copy
+// stream of its own; rho_dev is the N x N complex128 staging.  Sizes without
+// 4 (or 2) group-aligned blocks, or N < 2048, copy whole around the loop.
+tc_status evolve_lowp_host(const double* U, double* rho_host, double* rho_dev, int n, int steps, int precision,
+                           int renorm_every, const Model* m, double* obs, Arena& ar, cudaStream_t s);
+int lowp_host_chunks(int n, int precision);
 
 // Open-system form (packed excitation blocks).
 size_t lindblad_bytes(int n, int precision);
