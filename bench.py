@@ -44,7 +44,7 @@ METRIC = "evolution steps/s and complex-GEMM TFLOP/s at n=14 (FP64 vs split-BF16
 # current kernel build.  Keyed by (precision, n).  Source: profiles/
 # cgemm_tc_bf16x3.md (n = 14: X = U rho 227.5 / 243.7 GB, rho' half 111.1 /
 # 108.2 GB per launch).
-NCU_TRAFFIC = {("bf16x3", 14): 172.6e9}
+NCU_TRAFFIC = {("bf16x3", 14): 169.7e9}
 
 
 def _args():
