@@ -182,25 +182,6 @@ __device__ __forceinline__ void oz_epilogue(uint32_t tmem, int warp, int lane, i
     }
 }
 
-// CTA pairs sharing the P panel: pair q covers tiles (2i, J) and
-// (2i + 1, J), rank r taking I = 2i + r; mode 0 all T columns of each row
-// pair (T even), mode 1 the columns J <= 2i + 1 (the tile (2i, 2i + 1) lies
-// above the diagonal: computed, then overwritten by the mirror).
-__device__ __forceinline__ void pair_tile_rows(int mode, int T, int q, int rank, int& I, int& J) {
-    if (mode == 0) {
-        I = 2 * (q / T) + rank;
-        J = q % T;
-        return;
-    }
-    int i = 0, base = 0;
-    while (base + 2 * i + 2 <= q) {
-        base += 2 * i + 2;
-        i++;
-    }
-    I = 2 * i + rank;
-    J = q - base;
-}
-
 // CL = 2: clusters of two CTAs with the same row tile I: rank 0 loads the
 // U_r slice and rank 1 the U_i slice of every stage into both CTAs (TMA
 // multicast), so each U panel crosses L2 once per pair.  CL = 3: clusters of

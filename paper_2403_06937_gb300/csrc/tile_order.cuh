@@ -1,0 +1,116 @@
+// tile_order.cuh -- the order in which the CTAs of a tensor-core GEMM launch
+// visit the 128 x 128 output tiles (single CTAs, and CTA pairs sharing an
+// operand panel).  Plain C++ with host and device linkage, so that the host
+// tests can check the orders' coverage against the launch sizes.
+#pragma once
+
+#include <math.h>
+
+#ifdef __CUDACC__
+#define TC_HD __host__ __device__
+#else
+#define TC_HD
+#endif
+
+namespace tc {
+namespace cg {
+
+TC_HD inline int tile_min(int a, int b) { return a < b ? a : b; }
+
+TC_HD inline void tri_decode(int b, int& i, int& j) {
+    int r = (int)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
+    while ((r + 1) * (r + 2) / 2 <= b) ++r;
+    while (r * (r + 1) / 2 > b) --r;
+    i = r;
+    j = b - r * (r + 1) / 2;
+}
+
+// Tile b of the launch -> (I, J).  Both orders keep the CTAs that run at the
+// same time on few operand panels, so the panels are re-read from L2:
+//  mode 0 (T x T tiles, or the columns [lo, hi)): groups of G row tiles,
+//  column by column;
+//  mode 1 (block-lower tiles, or those of the rows [lo, hi); lo a multiple of
+//  G, hi a multiple of G or T): G x G super-blocks of the lower triangle, row
+//  by row; inside a super-block the tiles go column by column (the diagonal
+//  super-blocks hold only their lower half).
+TC_HD inline void tile_of_range(int mode, int T, int G, int lo, int hi, int b, int& I, int& J) {
+    if (G < 1) G = 1;
+    if (mode == 0) {
+        const int C = hi - lo;
+        int per_group = G * C;
+        int g = b / per_group;
+        int first = g * G;
+        int rows = tile_min(G, T - first);
+        int in = b % per_group;
+        I = first + in % rows;
+        J = lo + in / rows;
+        return;
+    }
+    const int SB0 = lo / G, SB1 = (hi + G - 1) / G;
+    for (int bi = SB0; bi < SB1; bi++) {
+        const int rows = tile_min(G, T - bi * G);
+        for (int bj = 0; bj <= bi; bj++) {
+            const int cols = tile_min(G, T - bj * G);
+            const int cnt = (bi == bj) ? rows * (rows + 1) / 2 : rows * cols;
+            if (b < cnt) {
+                if (bi == bj) {
+                    int ti, tj;
+                    tri_decode(b, ti, tj);
+                    I = bi * G + ti;
+                    J = bj * G + tj;
+                } else {
+                    I = bi * G + b % rows;
+                    J = bj * G + b / rows;
+                }
+                return;
+            }
+            b -= cnt;
+        }
+    }
+    I = J = 0;   // not reached for b below the launch's tile count
+}
+
+TC_HD inline void tile_of(int mode, int T, int G, int b, int& I, int& J) {
+    tile_of_range(mode, T, G, 0, T, b, I, J);
+}
+
+// CTA pairs (clusters of 2): pair q covers tiles (I, 2j) and (I, 2j + 1), rank
+// r taking J = 2j + r; mode 0 all rows of T (even) tiles, mode 1 the pairs
+// that hold a block-lower tile of row I (j <= I / 2; the tile (I, I + 1) of
+// an even row I is computed too and overwritten by the mirror).
+TC_HD inline void pair_tile(int mode, int T, int q, int rank, int& I, int& J) {
+    if (mode == 0) {
+        I = q / (T / 2);
+        J = 2 * (q % (T / 2)) + rank;
+        return;
+    }
+    int row = 0, base = 0;
+    while (base + row / 2 + 1 <= q) {
+        base += row / 2 + 1;
+        row++;
+    }
+    I = row;
+    J = 2 * (q - base) + rank;
+}
+
+// CTA pairs sharing the P panel: pair q covers tiles (2i, J) and
+// (2i + 1, J), rank r taking I = 2i + r; mode 0 all T columns of each row
+// pair (T even), mode 1 the columns J <= 2i + 1 (the tile (2i, 2i + 1) lies
+// above the diagonal: computed, then overwritten by the mirror).
+TC_HD inline void pair_tile_rows(int mode, int T, int q, int rank, int& I, int& J) {
+    if (mode == 0) {
+        I = 2 * (q / T) + rank;
+        J = q % T;
+        return;
+    }
+    int i = 0, base = 0;
+    while (base + 2 * i + 2 <= q) {
+        base += 2 * i + 2;
+        i++;
+    }
+    I = 2 * i + rank;
+    J = q - base;
+}
+
+}  // namespace cg
+}  // namespace tc
