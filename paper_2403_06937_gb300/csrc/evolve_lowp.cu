@@ -401,8 +401,32 @@ struct CopyLane {
 
 }  // namespace
 
+namespace {
+
+tc_status evolve_lowp_host_blocks(const double* U, double* rho_host, double* rho_dev, int n, int steps,
+                                  int precision, int renorm_every, const Model* m, double* obs, Arena& ar,
+                                  cudaStream_t s, CopyLane& lane);
+
+}  // namespace
+
 tc_status evolve_lowp_host(const double* U, double* rho_host, double* rho_dev, int n, int steps, int precision,
                            int renorm_every, const Model* m, double* obs, Arena& ar, cudaStream_t s) {
+    CopyLane lane;
+    const tc_status st = evolve_lowp_host_blocks(U, rho_host, rho_dev, n, steps, precision, renorm_every, m, obs, ar,
+                                                 s, lane);
+    if (st != TC_OK) {
+        // copies already queued must not touch the caller's buffers after the call returns
+        if (lane.cs) cudaStreamSynchronize(lane.cs);
+        cudaStreamSynchronize(s);
+    }
+    return st;
+}
+
+namespace {
+
+tc_status evolve_lowp_host_blocks(const double* U, double* rho_host, double* rho_dev, int n, int steps,
+                                  int precision, int renorm_every, const Model* m, double* obs, Arena& ar,
+                                  cudaStream_t s, CopyLane& lane) {
     const size_t N = (size_t)1 << n;
     const size_t bytes = 16 * N * N;
     const int C = steps >= 1 ? lowp_host_chunks(n, precision) : 1;
@@ -421,7 +445,6 @@ tc_status evolve_lowp_host(const double* U, double* rho_host, double* rho_dev, i
     const size_t R = N / C;                  // rows per chunk
     const size_t chunk = 16 * R * N;         // bytes per chunk
     const int stride = TC_OBS_STRIDE(n);
-    CopyLane lane;
     TC_TRY(lane.init(2 * C + 2));
     cudaEvent_t* h2d = lane.ev;              // [C]
     cudaEvent_t* fin = lane.ev + C;          // [C]
@@ -486,4 +509,5 @@ tc_status evolve_lowp_host(const double* U, double* rho_host, double* rho_dev, i
     return TC_OK;
 }
 
+}  // namespace
 }  // namespace tc
