@@ -43,15 +43,14 @@ def test_tuning_changes_speed_not_results(tc, precision):
     assert torch.equal(before, after) and torch.equal(ob, oa)
 
 
-def test_both_fp64_tiles_agree(tc, oracle):
+def test_both_fp64_tiles_agree(tc, oracle, tmp_path):
     """The 32 and 64 DMMA tiles (forced through the cache) give the same step."""
     n = 8
     g = W.draw_couplings(n, 5) * 4
     rho0, wts, states = W.random_mixed_state(n, 2, 1)
     res = []
     for tile in (32, 64):
-        path = os.path.join(ROOT, "gpurun_out", "tune_tile_%d.jsonl" % tile) if os.path.isdir(
-            os.path.join(ROOT, "gpurun_out")) else "/tmp/tune_tile_%d.jsonl" % tile
+        path = str(tmp_path / ("tune_tile_%d.jsonl" % tile))
         arch = 103
         with open(path, "w") as f:
             f.write('{"arch": %d, "n": %d, "precision": 0, "f64_tile": %d, "tc_group": 8, "tc_stages": 0}\n'
