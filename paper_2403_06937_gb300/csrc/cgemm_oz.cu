@@ -27,6 +27,9 @@
 // one K step of one pair (16 KB), 12 stages.  Warp 4 issues TMA, warp 5 the
 // MMAs, warps 0-3 the epilogue; the MMA issuer starts a pass only after the
 // epilogue has read the previous one out of TMEM.  Every wait is bounded.
+// With an even tile count, CTAs run as clusters of two that share the U panel
+// (same row tile) or the P panel (same column tile) by TMA multicast; the
+// arrangement is chosen per size (oz_cluster_mode) and never changes a bit.
 //   mode 0: all tiles (X = U rho).
 //   mode 1: block-lower tiles (rho' = U X^H); oz_mirror fills the upper half.
 #include <cuda_bf16.h>
