@@ -14,6 +14,9 @@
 // FP64, and the observable row from the FP32 planes.
 // Dimensions below 128 (n < 7) are zero-padded to one 128 x 128 tile: the
 // padded rows and columns of U and rho are zero and stay zero.
+// evolve_lowp_host is the same loop with rho in host memory: its copies run
+// by row blocks on a second stream, overlapped with the first product of the
+// first step and the second product of the last.
 #include <cuda_bf16.h>
 
 #include "cgemm_tc.cuh"
