@@ -222,7 +222,8 @@ def _ratio(got, ref, K):
 @pytest.mark.parametrize("n", [7, 10, 11, 12, 13])
 def test_single_product_tight(tc, n):
     """U U^H against numpy (blocked FP64 sums; up to n = 12) within _tight.
-    A CPU emulation of the exact slice arithmetic puts a correct product at
+    A CPU emulation of the exact slice arithmetic (test_ozaki_digit_scheme.py)
+    puts a correct product at
     0.04-0.2 of that bound (7- and 8-bit digits at the low end, 6-bit at the
     high end) and numpy's at about 0.2; leaving out the top slice level
     (t + u = S - 1) would put it at 5-16 times the bound: this catches that
