@@ -336,3 +336,27 @@ def test_gradient_identities(oracle):
     gr = oracle.grad_forward(n, g, 1.0, 1.0, dt, steps, psi0, O)
     # at resonance populations are even in the detuning
     assert abs(gr[n]) < 1e-12 and abs(gr[n + 1]) < 1e-12
+
+
+def test_fig3_claims_hold_under_the_qubit_photon_reading(oracle):
+    """The qualitative claims of Sec. IV (Figs. 3-4) -- P(0) falls from 1, the
+    P(m) peak in the order m = 1..n, the curves are symmetric about n/2 --
+    are exact for equal couplings at resonance under the Eq. 1 (qubit-photon)
+    reading, where the atoms are independent: with s = sin^2(g t),
+    P(m)(t) = C(n, m) s^m (1 - s)^(n - m), which peaks at s = m / n, and
+    P(m)(t) = P(n - m)(pi / (2 g) - t).  n = 8 from the all-excited state (the
+    Fig. 3 workload), over a quarter Rabi period on a grid that hits its end."""
+    n, g = 8, 0.01
+    K = 300
+    T = math.pi / (2 * g)
+    dt = T / K
+    _, obs = oracle.propagate(n, [g] * n, 1.0, 1.0, dt, K, W.all_excited_state(n),
+                              coupling=oracle.COUPLING_QUBIT_PHOTON)
+    P = obs[:, n + 1:2 * n + 2]            # P(m), m = 0..n, at t = k dt
+    assert abs(P[0, 0] - 1.0) < 1e-14 and np.all(np.diff(P[:, 0]) < 1e-15)   # falls from 1 to ~0
+    peaks = [int(np.argmax(P[:, m])) for m in range(1, n + 1)]
+    assert all(a < b for a, b in zip(peaks, peaks[1:]))
+    for m, k in zip(range(1, n + 1), peaks):
+        assert abs(k - math.asin(math.sqrt(m / n)) / g / dt) <= 1.0
+    for m in range(n + 1):
+        np.testing.assert_allclose(P[:, m], P[::-1, n - m], atol=1e-12)
