@@ -27,9 +27,6 @@
 // one K step of one pair (16 KB), 12 stages.  Warp 4 issues TMA, warp 5 the
 // MMAs, warps 0-3 the epilogue; the MMA issuer starts a pass only after the
 // epilogue has read the previous one out of TMEM.  Every wait is bounded.
-// With an even tile count, CTAs run as clusters of two that share the U panel
-// (same row tile) or the P panel (same column tile) by TMA multicast; the
-// arrangement is chosen per size (oz_cluster_mode) and never changes a bit.
 //   mode 0: all tiles (X = U rho).
 //   mode 1: block-lower tiles (rho' = U X^H); oz_mirror fills the upper half.
 #include <cuda_bf16.h>
@@ -185,14 +182,7 @@ __device__ __forceinline__ void oz_epilogue(uint32_t tmem, int warp, int lane, i
     }
 }
 
-// CL = 2: clusters of two CTAs with the same row tile I: rank 0 loads the
-// U_r slice and rank 1 the U_i slice of every stage into both CTAs (TMA
-// multicast), so each U panel crosses L2 once per pair.  CL = 3: clusters of
-// two CTAs with the same column tile J: rank 0 loads the P_r slice and rank 1
-// the P_i slice into both, and each CTA loads its own U panel (kept in L2).
-// In both, each CTA's MMA completion releases the stage in both CTAs (empty
-// barriers count 2).
-template <int MODE, int CL>
+template <int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
     cgemm_oz_kernel(const __grid_constant__ CUtensorMap tmU, const __grid_constant__ CUtensorMap tmP, OzEpi ep) {
     constexpr uint32_t kIdesc = make_idesc(1u, 128u, 256u);   // BF16 x BF16 -> FP32, M 128, N 256
@@ -210,19 +200,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t lim = ep.wait_ns ? ep.wait_ns : kWaitLimitNs;
     int I, J;
-    constexpr bool kPair = CL >= 2;
-    const uint32_t rank = kPair ? cluster_ctarank() : 0u;
-    if (CL == 2)
-        pair_tile(MODE, ep.tiles, (int)(blockIdx.x >> 1), (int)rank, I, J);
-    else if (CL == 3)
-        pair_tile_rows(MODE, ep.tiles, (int)(blockIdx.x >> 1), (int)rank, I, J);
-    else
-        tile_of(MODE, ep.tiles, ep.group, blockIdx.x, I, J);
+    tile_of(MODE, ep.tiles, ep.group, blockIdx.x, I, J);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; s++) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], kPair ? 2 : 1);
+            mbar_init(&empty[s], 1);
         }
         mbar_init(accum, 1);
         mbar_init(tmem_empty, 1);
@@ -239,7 +222,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         prefetch_tmap(&tmP);
     }
     __syncthreads();
-    if (kPair) cluster_sync();   // the peer's barriers exist before anything is multicast to them
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     const int S = ep.slices;
@@ -271,35 +253,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                     uint8_t* st = smem + s * kStage;
                     const uint32_t fb = saddr(&full[s]);
                     const int kx = c * Kc + kb * kKPerStage;
-                    if (CL == 2) {
-                        // U_r slice t from rank 0, U_i slice t from rank 1, into both CTAs
-                        tma_load_3d_multicast(saddr(st + rank * kATile), &tmU, fb, kx, I * 128,
-                                              (int)rank * S + t, (uint16_t)0x3);
-                    } else {
-                        tma_load_3d_hint(saddr(st), &tmU, fb, kx, I * 128, t, keep);                       // U_r
-                        tma_load_3d_hint(saddr(st + kATile), &tmU, fb, kx, I * 128, S + t, keep);          // U_i
-                    }
-                    if (CL == 3) {
-                        // P_r slice u from rank 0, P_i slice u from rank 1, into both CTAs
-                        tma_load_3d_multicast(saddr(st + 2 * kATile + rank * 128 * kRowBytes), &tmP, fb, kx,
-                                              J * 128, (int)rank * S + u, (uint16_t)0x3);
-                    } else {
-                        tma_load_3d(saddr(st + 2 * kATile), &tmP, fb, kx, J * 128, u);                 // P_r slice u
-                        tma_load_3d(saddr(st + 2 * kATile + 128 * kRowBytes), &tmP, fb, kx, J * 128,
-                                    S + u);                                                            // P_i slice u
-                    }
+                    tma_load_3d_hint(saddr(st), &tmU, fb, kx, I * 128, t, keep);                       // U_r
+                    tma_load_3d_hint(saddr(st + kATile), &tmU, fb, kx, I * 128, S + t, keep);          // U_i
+                    tma_load_3d(saddr(st + 2 * kATile), &tmP, fb, kx, J * 128, u);                     // P_r slice u
+                    tma_load_3d(saddr(st + 2 * kATile + 128 * kRowBytes), &tmP, fb, kx, J * 128,
+                                S + u);                                                                // P_i slice u
                 }
             }
             if (*abort) {
                 // let the copies already issued land before the CTA goes away
                 for (uint32_t k = it > (uint32_t)kStages ? it - kStages : 0u; k < it; k++)
-                    (void)mbar_wait_bounded(&full[k % kStages], (k / kStages) & 1u, nullptr,
-                                            kPair ? 10000000ull : lim, 0);
-            } else if (kPair) {
-                // the last use of every stage released by both CTAs' MMAs: no arrival of
-                // the peer is still on its way to this CTA's barriers when it leaves
-                for (uint32_t k = it > (uint32_t)kStages ? it - kStages : 0u; k < it; k++)
-                    (void)mbar_wait_bounded(&empty[k % kStages], (k / kStages) & 1u, abort, lim, 0);
+                    (void)mbar_wait_bounded(&full[k % kStages], (k / kStages) & 1u, nullptr, lim, 0);
             }
         }
     } else if (warp == 5) {
@@ -322,10 +286,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const uint64_t bd = desc_kmajor_sw32(saddr(st + 2 * kATile));
                     umma<0>(tmem, desc_kmajor_sw32(saddr(st)), bd, kIdesc, kb > 0 ? 1u : 0u);
                     umma<0>(tmem + 256, desc_kmajor_sw32(saddr(st + kATile)), bd, kIdesc, kb > 0 ? 1u : 0u);
-                    if (kPair)
-                        umma_commit_multicast(saddr(&empty[s]), (uint16_t)0x3);
-                    else
-                        umma_commit(saddr(&empty[s]));
+                    umma_commit(saddr(&empty[s]));
                 }
                 umma_commit(saddr(accum));
             }
@@ -365,7 +326,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncwarp();
     tc_fence_before();
     __syncthreads();
-    if (kPair) cluster_sync();   // neither CTA leaves while the other may still write to it
     if (warp == 0) {
         tc_fence_after();
         tmem_dealloc(tmem, 512);
@@ -457,9 +417,9 @@ unsigned grid_for(size_t work) {
     return (unsigned)(want < cap ? (want ? want : 1) : cap);
 }
 
-template <int MODE, int CL>
+template <int MODE>
 tc_status launch(const CUtensorMap& tmU, const CUtensorMap& tmP, const OzEpi& ep, cudaStream_t s) {
-    auto k = cgemm_oz_kernel<MODE, CL>;
+    auto k = cgemm_oz_kernel<MODE>;
     static bool attr_set[64] = {};
     int dev = 0;
     TC_CUDA(cudaGetDevice(&dev));
@@ -469,62 +429,17 @@ tc_status launch(const CUtensorMap& tmU, const CUtensorMap& tmP, const OzEpi& ep
         attr_set[dev] = true;
     }
     const int T = ep.tiles;
-    if (CL == 1) {
-        const unsigned grid = MODE == 0 ? (unsigned)(T * T) : (unsigned)(T * (T + 1) / 2);
-        k<<<grid, kThreads, kSmem, s>>>(tmU, tmP, ep);
-        TC_LAUNCH_CHECK();
-        return TC_OK;
-    }
-    // pairs of CTAs: mode 0 T * T / 2; mode 1 sharing U: sum over rows of
-    // (I / 2 + 1), sharing P: sum over row pairs i of (2 i + 2)
-    unsigned pairs = 0;
-    if (MODE == 0) {
-        pairs = (unsigned)(T * (T / 2));
-    } else if (CL == 2) {
-        for (int I = 0; I < T; I++) pairs += (unsigned)(I / 2 + 1);
-    } else {
-        for (int i = 0; i < T / 2; i++) pairs += (unsigned)(2 * i + 2);
-    }
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3(2 * pairs);
-    cfg.blockDim = dim3(kThreads);
-    cfg.dynamicSmemBytes = kSmem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 2;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    TC_CUDA(cudaLaunchKernelEx(&cfg, k, tmU, tmP, ep));
+    const unsigned grid = MODE == 0 ? (unsigned)(T * T) : (unsigned)(T * (T + 1) / 2);
+    k<<<grid, kThreads, kSmem, s>>>(tmU, tmP, ep);
     TC_LAUNCH_CHECK();
     return TC_OK;
 }
 
-// -2: not read yet; -1: by size; else TC_OZ_CLUSTER from the environment
-// (0 single CTAs, 1 pairs sharing U, 2 pairs sharing P).  All give the same
-// bits.  By size: pairs sharing P from 128 tiles a side (n = 14: half the
-// DRAM reads of pairs sharing U, 2 % faster), pairs sharing U below (n = 12:
-// 1.4 % faster than sharing P; both 15 % faster than single CTAs at n = 14).
-std::atomic<int> g_oz_cluster{-2};
 // -1: not chosen yet (TC_OZ_BITS=6 in the environment: 6-bit digits at every
 // size; else the widest digits K allows)
 std::atomic<int> g_oz_narrow{-1};
 
 }  // namespace
-
-int oz_cluster_mode(int tiles) {
-    int v = g_oz_cluster.load();
-    if (v == -2) {
-        const char* e = std::getenv("TC_OZ_CLUSTER");
-        v = e ? std::atoi(e) : -1;
-        v = v < -1 || v > 2 ? -1 : v;
-        g_oz_cluster.store(v);
-    }
-    if (tiles % 2 != 0) return 0;
-    return v >= 0 ? v : (tiles >= 128 ? 2 : 1);
-}
 
 OzDigits oz_digits(int Np) {
     int narrow = g_oz_narrow.load();
@@ -566,14 +481,8 @@ tc_status cgemm_oz(int mode, const CUtensorMap& tmU, const CUtensorMap& tmP, con
         return fail(TC_ERR_INVALID_ARG, "cgemm_oz: digit width does not match the dimension");
     if (ep.Np > dg.kmax && ep.Np % dg.kmax != 0)
         return fail(TC_ERR_INVALID_ARG, "cgemm_oz: dimension above %d must be a multiple of it", dg.kmax);
-    // CTA pairs sharing the U (or P) panels when the tile count is even
-    const int cl = oz_cluster_mode(ep.tiles);
-    if (mode == 0)
-        return cl == 2 ? launch<0, 3>(tmU, tmP, ep, s) : cl == 1 ? launch<0, 2>(tmU, tmP, ep, s)
-                                                                 : launch<0, 1>(tmU, tmP, ep, s);
-    if (mode == 1)
-        return cl == 2 ? launch<1, 3>(tmU, tmP, ep, s) : cl == 1 ? launch<1, 2>(tmU, tmP, ep, s)
-                                                                 : launch<1, 1>(tmU, tmP, ep, s);
+    if (mode == 0) return launch<0>(tmU, tmP, ep, s);
+    if (mode == 1) return launch<1>(tmU, tmP, ep, s);
     return fail(TC_ERR_INVALID_ARG, "cgemm_oz: mode");
 }
 

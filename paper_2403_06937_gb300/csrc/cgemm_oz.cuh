@@ -49,11 +49,6 @@ size_t oz_slice_bytes(int Np);
 // Y = U P^H (mode 0: all tiles; mode 1: block-lower tiles, then oz_mirror)
 tc_status cgemm_oz(int mode, const CUtensorMap& tmU, const CUtensorMap& tmP, const OzEpi& ep, cudaStream_t s);
 tc_status oz_mirror(double* yr, double* yi, int Np, cudaStream_t s);
-// CTA arrangement for `tiles` tiles a side (pairs need an even count):
-// 0 single CTAs, 1 pairs sharing the U panels by TMA multicast, 2 pairs
-// sharing the P panels; TC_OZ_CLUSTER in the environment, else 2 from 128
-// tiles a side and 1 below
-int oz_cluster_mode(int tiles);
 
 // One operand of the emulated product: its digit slices, row exponents and
 // TMA map (row r of the operand = row r of A, or row r of B in A B^H).

@@ -74,25 +74,6 @@ TC_HD inline void tile_of(int mode, int T, int G, int b, int& I, int& J) {
     tile_of_range(mode, T, G, 0, T, b, I, J);
 }
 
-// CTA pairs (clusters of 2): pair q covers tiles (I, 2j) and (I, 2j + 1), rank
-// r taking J = 2j + r; mode 0 all rows of T (even) tiles, mode 1 the pairs
-// that hold a block-lower tile of row I (j <= I / 2; the tile (I, I + 1) of
-// an even row I is computed too and overwritten by the mirror).
-TC_HD inline void pair_tile(int mode, int T, int q, int rank, int& I, int& J) {
-    if (mode == 0) {
-        I = q / (T / 2);
-        J = 2 * (q % (T / 2)) + rank;
-        return;
-    }
-    int row = 0, base = 0;
-    while (base + row / 2 + 1 <= q) {
-        base += row / 2 + 1;
-        row++;
-    }
-    I = row;
-    J = 2 * (q - base) + rank;
-}
-
 // CTA pairs sharing the P panel: pair q covers tiles (2i, J) and
 // (2i + 1, J), rank r taking I = 2i + r; mode 0 all T columns of each row
 // pair (T even), mode 1 the columns J <= 2i + 1 (the tile (2i, 2i + 1) lies

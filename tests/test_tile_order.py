@@ -1,7 +1,7 @@
 """The tile orders of the tensor-core GEMM launches (csrc/tile_order.cuh),
 compiled for the host with g++ and checked by tests/tile_order_check.cpp:
 every launch form (single CTAs over all or a range of tiles, CTA pairs
-sharing the U or the P panel) visits each tile it owns exactly once, inside
+sharing the P panel) visits each tile it owns exactly once, inside
 the grid, and the split launches of the host-buffer call cover the same
 tiles as the whole launch.  No GPU."""
 import os

@@ -4,7 +4,6 @@
 // the same tiles as the whole launch.
 //   single CTAs, mode 0: columns [lo, hi) of T x T; mode 1: block-lower tiles
 //     of the tile rows [lo, hi) (lo a multiple of G, hi of G or T);
-//   CTA pairs sharing U (pair_tile): both CTAs in one row tile;
 //   CTA pairs sharing P (pair_tile_rows): both CTAs in one column tile.
 // Prints one line per failure and exits 1 if there was any.
 #include <cstdio>
@@ -14,7 +13,6 @@
 
 #include "tile_order.cuh"
 
-using tc::cg::pair_tile;
 using tc::cg::pair_tile_rows;
 using tc::cg::tile_of;
 using tc::cg::tile_of_range;
@@ -69,38 +67,14 @@ static void check_single(int T, int G) {
 
 static void check_pairs(int T) {
     for (int mode = 0; mode < 2; mode++) {
-        // sharing U: mode 0 T * T / 2 pairs, mode 1 sum over rows of (I / 2 + 1)
-        long pairs = 0;
-        if (mode == 0) {
-            pairs = (long)T * (T / 2);
-        } else {
-            for (int I = 0; I < T; I++) pairs += I / 2 + 1;
-        }
-        std::set<std::pair<int, int>> seen;
-        for (long q = 0; q < pairs; q++) {
-            int I0, J0, I1, J1;
-            pair_tile(mode, T, (int)q, 0, I0, J0);
-            pair_tile(mode, T, (int)q, 1, I1, J1);
-            if (I0 != I1) fail("pair_tile: the pair spans two row tiles", T, 0, mode, I0, I1);
-            for (auto t : {std::make_pair(I0, J0), std::make_pair(I1, J1)}) {
-                if (t.first < 0 || t.first >= T || t.second < 0 || t.second >= T)
-                    fail("pair_tile out of range", T, 0, mode, t.first, t.second);
-                if (!seen.insert(t).second) fail("pair_tile visits twice", T, 0, mode, t.first, t.second);
-            }
-        }
-        for (auto t : owned(mode, T))
-            if (!seen.count(t)) fail("pair_tile misses a tile", T, 0, mode, t.first, t.second);
-        for (auto t : seen)   // extras only above the diagonal next to it (overwritten by the mirror)
-            if (mode == 1 && t.second > t.first && !(t.second == t.first + 1 && t.first % 2 == 0))
-                fail("pair_tile extra tile", T, 0, mode, t.first, t.second);
         // sharing P: mode 0 T * T / 2 pairs, mode 1 sum over row pairs i of (2 i + 2)
-        pairs = 0;
+        long pairs = 0;
         if (mode == 0) {
             pairs = (long)T * (T / 2);
         } else {
             for (int i = 0; i < T / 2; i++) pairs += 2 * i + 2;
         }
-        seen.clear();
+        std::set<std::pair<int, int>> seen;
         for (long q = 0; q < pairs; q++) {
             int I0, J0, I1, J1;
             pair_tile_rows(mode, T, (int)q, 0, I0, J0);
