@@ -72,8 +72,9 @@ def test_no_alloc_matches_workspace_version_on_consecutive_calls(lib, oracle, n)
     a0 = _with_work(lib, ta, n, params)
     b0 = _with_work(lib, tb, n, params)
     torch.cuda.synchronize()
-    np.testing.assert_allclose(a1.cpu().numpy(), a0.cpu().numpy(), rtol=0, atol=1e-12)
-    np.testing.assert_allclose(b1.cpu().numpy(), b0.cpu().numpy(), rtol=0, atol=1e-12)
+    # the same kernels and the same fixed reduction order: bitwise the same rows
+    np.testing.assert_array_equal(a1.cpu().numpy(), a0.cpu().numpy())
+    np.testing.assert_array_equal(b1.cpu().numpy(), b0.cpu().numpy())
     if n <= 9:
         np.testing.assert_allclose(a1.cpu().numpy(), oracle.observables(n, g, 1.003, 0.998, rho_a), atol=1e-12)
 
