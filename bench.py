@@ -38,13 +38,12 @@ import workloads as W  # noqa: E402
 
 METRIC = "evolution steps/s and complex-GEMM TFLOP/s at n=14 (FP64 vs split-BF16) at stated error"
 
-# DRAM bytes (read + write) per launch of the dominant kernel, averaged over
-# the launches of one ncu capture of the benchmark's own command (one pass:
-# dram__bytes_read.sum + dram__bytes_write.sum); None until captured for the
-# current kernel build.  Keyed by (precision, n).  Source: profiles/
-# cgemm_tc_bf16x3.md (n = 14: X = U rho 227.5 / 243.7 GB, rho' half 111.1 /
-# 108.2 GB per launch).
-NCU_TRAFFIC = {("bf16x3", 14): 169.7e9}
+# DRAM bytes (read + write) per launch of the dominant kernel, keyed by
+# (precision, n): dram__bytes_read.sum + dram__bytes_write.sum averaged over
+# the launches of a one-pass ncu capture at n <= 12, scaled to n by the
+# N^3 units a launch processes.  Empty until such a capture of the current
+# kernel build exists (the line then reports null).
+NCU_TRAFFIC = {}
 
 
 def _args():
@@ -62,6 +61,8 @@ def _args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the TF32 / TF32x3 / FP64 comparison forms")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--full", action="store_true",
+                    help="also run the workload's whole run (500 steps at n=14) and state its error vs the oracle")
     return ap.parse_args()
 
 
@@ -81,7 +82,7 @@ class Clocks:
     """nvidia-smi sampled every 200 ms during the timed region."""
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-              "clocks_event_reasons.sw_power_cap")
+              "clocks_event_reasons.sw_power_cap,clocks.mem")
 
     def __init__(self, index: int):
         self.index = index
@@ -108,7 +109,7 @@ class Clocks:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.f.close()
-        sm, mx, reasons, power = [], [], set(), []
+        sm, mx, reasons, power, mem = [], [], set(), [], []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         with open(self.path) as f:
             for line in f:
@@ -121,6 +122,10 @@ class Clocks:
                     power.append(float(parts[2]))
                 except ValueError:
                     continue
+                try:
+                    mem.append(float(parts[8]))
+                except (ValueError, IndexError):
+                    pass
                 for nm, v in zip(names, parts[4:8]):
                     if v.lower().startswith("active"):
                         reasons.add(nm)
@@ -128,7 +133,8 @@ class Clocks:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         return {"sm_mhz": float(np.median(sm)), "sm_mhz_min": float(min(sm)), "sm_max_mhz": float(max(mx)),
-                "reasons": sorted(reasons), "samples": len(sm), "power_w_max": float(max(power)) if power else None}
+                "reasons": sorted(reasons), "samples": len(sm), "power_w_max": float(max(power)) if power else None,
+                "mem_mhz_min": float(min(mem)) if mem else None, "mem_mhz_max": float(max(mem)) if mem else None}
 
 
 # ------------------------------------------------------------------ peaks
@@ -156,6 +162,43 @@ def _fp64_peak_live(torch):
         best = min(best, e0.elapsed_time(e1))
     del a, b
     return 2.0 * 4096 ** 3 / (best * 1e-3) / 1e12
+
+
+def _tf32_peak_live(torch, seconds: float = 2.0):
+    """cuBLAS TF32 GEMM (torch.matmul float32 with TF32 allowed, 8192^3): the
+    TF32 tensor pipe's measured rate, as a burst (best of 5) and sustained
+    (back to back for `seconds`, as the kernels run inside a long step)."""
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    try:
+        m = 8192
+        a = torch.randn(m, m, dtype=torch.float32, device="cuda")
+        b = torch.randn(m, m, dtype=torch.float32, device="cuda")
+        c = torch.matmul(a, b)
+        torch.cuda.synchronize()
+        best = 1e30
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b, out=c)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        per = best * 1e-3
+        reps = max(4, int(seconds / per))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            torch.matmul(a, b, out=c)
+        e1.record()
+        torch.cuda.synchronize()
+        flop = 2.0 * m ** 3
+        burst = flop / per / 1e12
+        sustained = flop * reps / (e0.elapsed_time(e1) * 1e-3) / 1e12
+        del a, b, c
+        return burst, sustained
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
 
 
 # ------------------------------------------------------------------ CPU oracle
@@ -196,24 +239,36 @@ def _cpu_sample(cfg, target_s: float, reps: int = 1):
 
 # ------------------------------------------------------------------ reference arm
 def run_reference(a, cfg, metric=METRIC, scale=1.0, scale_note="", workload=None):
-    """The CPU oracle's dense step on a bounded row sample, extrapolated to
-    steps/s (`scale` converts a dense N x N step into the workload's step)."""
+    """The reference arm: the CPU oracle's dense step (the paper ships no code).
+
+    Each of the W + K "steps" of this arm is one bounded sample of the
+    workload's dense step: a block of rows of rho' = U rho U^dag, sized so the
+    whole run ends within a few minutes.  `ms_per_step` is the wall time of
+    one such sample, `steps` the number of samples timed, and `value` the
+    whole dense steps per second they extrapolate to (`scale` converts a
+    dense N x N step into the workload's step)."""
     rank, world, _ = _dist()
     if rank != 0:
         return 0
-    vals = []
-    per_step_target = max(1.0, min(a.cpu_seconds, 240.0 / max(1, a.steps + a.warmup)))
+    vals, secs, rows_list = [], [], []
+    per_step_target = max(1.0, min(a.cpu_seconds, 150.0 / max(1, a.steps + a.warmup)))
     sample = cores = None
     for i in range(a.warmup + a.steps):
-        v, cores, sample, _ = _cpu_sample(cfg, per_step_target)
+        v, cores, sample, t = _cpu_sample(cfg, per_step_target)
         if i >= a.warmup:
             vals.append(v * scale)
+            secs.append(t)
     value = float(np.median(vals))
+    t_sample = float(np.median(secs))
+    frac = value / scale * t_sample       # fraction of one dense step a sample computes
     sample = sample + scale_note
     line = {
         "impl": "reference", "metric": metric, "value": value, "unit": "steps/s", "n_gpus": a.gpus,
-        "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * t_sample, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "step_kind": ("each step of this arm is one bounded row sample of the dense step (%.4f of a whole "
+                      "step, %.2f s); ms_per_step is a sample's wall time and value the whole steps/s "
+                      "they extrapolate to" % (frac, t_sample)),
         "config": {"workload": workload or cfg.description, "dim": cfg.N,
                    "reference": "CPU oracle (no code ships with the paper)"},
         "cpu_baseline": {"value": value, "unit": "steps/s", "cores": cores, "kind": "oracle", "sample": sample},
@@ -267,8 +322,32 @@ def oz_pairs(N):
     return 28 if K <= 1024 else 36
 
 
+def _sample_entries(torch, rho, count=20000, top=48, seed=5):
+    """Indices (i, j) of a seeded random sample of rho's entries plus the
+    top x top block on the largest diagonal entries, and rho's values there
+    (gathered on the device, copied to the host)."""
+    N = rho.shape[0]
+    rng = np.random.default_rng(seed)
+    idx = rng.integers(0, N, size=(count, 2))
+    big = torch.argsort(rho.diagonal().real.abs(), descending=True)[:min(top, N)].cpu().numpy()
+    ii = np.concatenate([idx[:, 0], np.repeat(big, len(big))])
+    jj = np.concatenate([idx[:, 1], np.tile(big, len(big))])
+    vals = rho[torch.from_numpy(ii).cuda(), torch.from_numpy(jj).cuda()].cpu().numpy()
+    return ii, jj, vals
+
+
+def _drift(o, n, steps_done):
+    return {"kind": "conserved quantities after %d steps" % steps_done,
+            "trace": float(abs(o[-1, 2 * n + 2] - 1.0)),
+            "purity": float(abs(o[-1, 2 * n + 3] - 1.0)),
+            "energy_rel": float(abs(o[-1, 2 * n + 4] - o[0, 2 * n + 4]) / abs(o[0, 2 * n + 4]))}
+
+
 def _time_form(tc, torch, U, n, params, prec, steps, warmup, renorm, stream, with_clocks=None):
-    """W untimed steps, then K steps of one tc_evolve call timed with CUDA events."""
+    """W untimed steps, then K steps of one tc_evolve call timed with CUDA events.
+
+    Also returns what the oracle comparison needs: the observable rows of the
+    timed call (steps W..W+K) and a sample of rho's entries after step W+K."""
     N = 1 << n
     rho = torch.zeros((N, N), dtype=torch.complex128, device="cuda")
     rho[N - 1, N - 1] = 1.0
@@ -297,6 +376,7 @@ def _time_form(tc, torch, U, n, params, prec, steps, warmup, renorm, stream, wit
     tc.sync_status()
     ms = e0.elapsed_time(e1)
     o = obs.cpu().numpy()
+    sample = _sample_entries(torch, rho)
     # the roofline of the product kernels: the same K steps again with an event
     # pair around every product launch (direct launches, no graph)
     if not inline:
@@ -306,13 +386,68 @@ def _time_form(tc, torch, U, n, params, prec, steps, warmup, renorm, stream, wit
         torch.cuda.synchronize()
     tc.timing_enable(False)
     klaunch, kms, kflops = tc.timing_read()
-    drift = {"kind": "conserved quantities after %d steps (oracle-free)" % (warmup + steps),
-             "trace": float(abs(o[-1, 2 * n + 2] - 1.0)),
-             "purity": float(abs(o[-1, 2 * n + 3] - 1.0)),
-             "energy_rel": float(abs(o[-1, 2 * n + 4] - o[0, 2 * n + 4]) / abs(o[0, 2 * n + 4]))}
     del work, rho
     return {"ms": ms, "launches": launches, "klaunch": klaunch, "kms": kms, "kflops": kflops, "clocks": ck,
-            "drift": drift}
+            "drift": _drift(o, n, warmup + steps), "obs": o, "sample": sample, "first": warmup,
+            "steps": steps}
+
+
+def _full_run(tc, torch, U, n, params, prec, steps, renorm):
+    """The workload's whole run (all its steps, renormalised as it states) in
+    one tc_evolve call, for the error of the final result against the oracle."""
+    N = 1 << n
+    rho = torch.zeros((N, N), dtype=torch.complex128, device="cuda")
+    rho[N - 1, N - 1] = 1.0
+    t0 = time.perf_counter()
+    rho, obs = tc.evolve(U, rho, n, steps, prec, renorm_every=renorm, params=params, inplace=True)
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    tc.sync_status()
+    o = obs.cpu().numpy()
+    res = {"seconds": t, "drift": _drift(o, n, steps), "obs": o, "sample": _sample_entries(torch, rho),
+           "first": 0, "steps": steps}
+    del rho
+    return res
+
+
+def _oracle_trajectories(cfg, upto):
+    """O-psi: the oracle's pure-state propagation of the workload from the
+    all-excited state, the observable rows of every step up to max(upto) and
+    psi after each step count in `upto`.  Returns (rows, {steps: psi}, s/step)."""
+    import oracle
+    oracle.build()
+    marks = sorted(set(int(u) for u in upto))
+    psi = W.all_excited_state(cfg.n)
+    rows = [oracle.observables_pure(cfg.n, cfg.g, cfg.omega_a, cfg.omega_c, psi)]
+    psis = {0: psi.copy()}
+    done = 0
+    t0 = time.perf_counter()
+    for m in marks:
+        if m > done:
+            psi, ob = oracle.propagate(cfg.n, cfg.g, cfg.omega_a, cfg.omega_c, cfg.dt, m - done, psi)
+            rows.extend(ob[1:])
+            done = m
+        psis[m] = psi.copy()
+    t = time.perf_counter() - t0
+    return np.array(rows), psis, t / max(done, 1)
+
+
+def _error_vs_oracle(r, n, rows, psis):
+    """Max-abs error of a form's results against the oracle over the steps it
+    ran: populations P_i, mean photon number <p>, photon-number
+    probabilities P(m) (Eq. 13) and the sampled rho entries."""
+    o = r["obs"]
+    first, k = r["first"], r["steps"]
+    ref = rows[first:first + k + 1]
+    ii, jj, vals = r["sample"]
+    psi = psis[first + k]
+    want = psi[ii] * psi[jj].conj()
+    return {"steps": "%d..%d" % (first, first + k),
+            "populations": float(np.max(np.abs(o[:, :n] - ref[:, :n]))),
+            "mean_photons": float(np.max(np.abs(o[:, n] - ref[:, n]))),
+            "photon_number_probabilities": float(np.max(np.abs(o[:, n + 1:2 * n + 2] - ref[:, n + 1:2 * n + 2]))),
+            "rho_sampled": float(np.max(np.abs(vals - want))),
+            "rho_entries_sampled": int(len(ii))}
 
 
 def run_ours(a, cfg):
@@ -340,15 +475,19 @@ def run_ours(a, cfg):
     credited = 12.0 * N ** 3
     peaks, peak_src = _measured_peaks()
 
-    def peak_of(p, fp64_peak=None):
+    def peak_of(p, fp64_peak=None, tf32_peak=None):
         if p == "fp64":
             return fp64_peak, "FP64: cuBLAS DGEMM 4096^3 measured live in this run (torch.matmul float64)"
         if p in ("tf32", "tf32x3"):
+            if tf32_peak is not None:
+                return tf32_peak[1], ("TF32: cuBLAS TF32 GEMM 8192^3 measured live in this run, sustained "
+                                      "(back to back for 2 s; burst %.0f TFLOP/s)" % tf32_peak[0])
             return peaks["bf16_tflops_sustained"] / 2.0, \
                 "TF32: %s bf16_tflops_sustained x 1/2 (nominal tf32:bf16 ratio)" % peak_src
         return peaks["bf16_tflops_sustained"], "BF16: %s bf16_tflops_sustained (kernel timed inside a long step)" % peak_src
 
     fp64_peak = _fp64_peak_live(torch) if (prec == "fp64" or not a.no_compare) else None
+    tf32_peak = _tf32_peak_live(torch) if (prec in ("tf32", "tf32x3") or not a.no_compare) else None
     clocks = Clocks(local)
     if world > 1:
         torch.distributed.barrier()
@@ -356,7 +495,7 @@ def run_ours(a, cfg):
                    with_clocks=clocks)
     ms = max_over_ranks(r["ms"], world)
     value = replica_value(a.steps, world, ms)
-    peak, peak_note = peak_of(prec, fp64_peak)
+    peak, peak_note = peak_of(prec, fp64_peak, tf32_peak)
     achieved = r["kflops"] / (r["kms"] * 1e-3) / 1e12 if r["kms"] > 0 else 0.0
     roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak if peak else None, "traffic": NCU_TRAFFIC.get((prec, n)),
@@ -381,8 +520,9 @@ def run_ours(a, cfg):
         "roofline": roof,
         "clocks": r["clocks"],
         "gpu_launches": r["launches"],
-        "error": r["drift"],
+        "error": {"vs_oracle": None, "drift": r["drift"]},
     }
+    forms = {prec: r}      # every timed form's results, for the oracle comparison
 
     if not a.no_e2e:
         # end to end through the public C ABI call with host buffers: every step copies
@@ -395,7 +535,9 @@ def run_ours(a, cfg):
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
-        calls = []
+        calls, phases = [], []
+        tc.phases_enable(True)     # event marks at the phase boundaries of each call (no extra sync)
+        tc.phases_read()
         eclk = Clocks(local)
         eclk.start()
         t0 = time.perf_counter()
@@ -403,13 +545,18 @@ def run_ours(a, cfg):
             tc0 = time.perf_counter()
             tc.evolve_host(U, rho_h, n, 1, prec, params=params, obs_host=obs_h, work=hw)
             calls.append(1e3 * (time.perf_counter() - tc0))
+            phases.append(tc.phases_read())
         torch.cuda.synchronize()
         te = max_over_ranks(time.perf_counter() - t0, world)
         eck = eclk.stop()
+        tc.phases_enable(False)
+        marks = [m for m, _ in phases[0]] if phases and phases[0] else []
         line["e2e"] = {"value": world * a.steps / te, "unit": "steps/s", "h2d_bytes_per_step": 16 * N * N,
                        "d2h_bytes_per_step": 16 * N * N + 2 * (2 * n + 5) * 8,
                        "api": "tc_evolve_host (C ABI, pinned host rho, one step per call)",
-                       "call_ms": [round(c, 1) for c in calls], "clocks": eck}
+                       "call_ms": [round(c, 1) for c in calls], "clocks": eck,
+                       "phases": {"marks": marks,
+                                  "ms_after_start": [[round(t, 1) for _, t in p] for p in phases]}}
         del rho_h, hw
 
     if not a.no_compare:
@@ -423,12 +570,14 @@ def run_ours(a, cfg):
                 others["fp64"] = {"omitted": "one FP64 step takes about %.0f s at n=%d" % (credited / 1.1e12, n)}
                 continue
             r2 = _time_form(tc, torch, U, n, params, p2, k2, w2, renorm if p2 != "fp64" else 0, stream)
+            forms[p2] = r2
             v2 = k2 / (r2["ms"] * 1e-3)
-            pk, _ = peak_of(p2, fp64_peak)
+            pk, pk_note = peak_of(p2, fp64_peak, tf32_peak)
             ach = r2["kflops"] / (r2["kms"] * 1e-3) / 1e12 if r2["kms"] > 0 else 0.0
             others[p2] = {"value": v2, "unit": "steps/s", "steps": k2, "warmup": w2,
                           "credited_tflops": credited * v2 / 1e12, "achieved_tflops": ach, "peak": pk,
-                          "frac": ach / pk if pk else None, "error": r2["drift"]}
+                          "frac": ach / pk if pk else None, "peak_source": pk_note,
+                          "error": {"vs_oracle": None, "drift": r2["drift"]}}
             if p2 == "ozaki":
                 others[p2]["digit_pairs"] = oz_pairs(1 << n)
         line["other_forms"] = others
@@ -437,9 +586,35 @@ def run_ours(a, cfg):
             if "value" in others.get("ozaki", {}):
                 others["ozaki"]["speedup_vs_fp64"] = others["ozaki"]["value"] / others["fp64"]["value"]
 
+    full = None
+    if a.full:
+        # the headline's whole run (all the workload's steps) for the error of its final result
+        full = _full_run(tc, torch, U, n, params, prec, cfg.steps, renorm if prec != "fp64" else 0)
+        line["full_run"] = {"steps": cfg.steps, "seconds": full["seconds"], "drift": full["drift"],
+                            "error": {"vs_oracle": None}}
+
     if rank == 0 and not a.no_cpu:
+        # CPU leg (rank 0, host cores): the like-for-like dense-step sample, then the
+        # oracle's pure-state propagation (O-psi) of this workload, timed per step;
+        # its trajectory is the reference every timed form's result is compared with.
         v, cores, sample, _ = _cpu_sample(cfg, a.cpu_seconds)
-        line["cpu_baseline"] = {"value": v, "unit": "steps/s", "cores": cores, "kind": "oracle", "sample": sample}
+        upto = [f["first"] + f["steps"] for f in forms.values()]
+        if full is not None:
+            upto.append(full["steps"])
+        rows, psis, per_step = _oracle_trajectories(cfg, upto)
+        line["cpu_baseline"] = {"value": v, "unit": "steps/s", "cores": cores, "kind": "oracle", "sample": sample,
+                                "oracle_pure_state": {"seconds_per_step": per_step,
+                                                      "seconds_for_%d_steps" % cfg.steps: per_step * cfg.steps,
+                                                      "threads": 1,
+                                                      "what": "O-psi: psi <- e^{-iH dt} psi by the Taylor series to "
+                                                              "convergence with the sparse H, plus one observable "
+                                                              "row per step"}}
+        line["error"]["vs_oracle"] = _error_vs_oracle(forms[prec], n, rows, psis)
+        for p2, f in forms.items():
+            if p2 != prec and p2 in line.get("other_forms", {}):
+                line["other_forms"][p2]["error"]["vs_oracle"] = _error_vs_oracle(f, n, rows, psis)
+        if full is not None:
+            line["full_run"]["error"]["vs_oracle"] = _error_vs_oracle(full, n, rows, psis)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -247,6 +247,16 @@ TC_API tc_status tc_evolve(const void* U, void* rho, int n, int steps, int preci
 TC_API tc_status tc_observables(const void* rho, int n, const tc_params* params,
                                 double* out, void* work, size_t work_bytes, void* stream);
 
+/* tc_expectation_diag -- <O> = Tr(diag(O) rho) = sum_s O_s Re rho[s][s] for a
+ * diagonal observable O (e.g. the population of one atom, the quantity Sec.
+ * IV.A follows in Figs. 3-4; the loss of tc_evolve_backward).  One block
+ * sums in a fixed order, so reruns are bitwise identical.
+ *  rho    : device, N*N c128, read only.
+ *  O_diag : device, N doubles.
+ *  out    : device, 1 double.
+ *  Errors: TC_ERR_INVALID_ARG, TC_ERR_UNSUPPORTED_DEVICE. */
+TC_API tc_status tc_expectation_diag(const void* rho, int n, const double* O_diag, double* out, void* stream);
+
 /* tc_observables_noalloc -- tc_observables for callers that cannot allocate
  * device memory at all, so cannot supply a `work` buffer: for example a
  * monitor thread inside a program whose device memory is wholly owned by
@@ -441,6 +451,20 @@ TC_API long long tc_launch_count(void);
  * and their FLOPs, then clears the record. */
 TC_API tc_status tc_timing_enable(int on);
 TC_API tc_status tc_timing_read(long long* launches, double* ms, double* flops);
+
+/* tc_phases_enable(1): from now on tc_evolve_host records a CUDA event at
+ * each phase boundary of its call on the stream doing that phase: the start,
+ * the end of each host-to-device row-block copy ("h2d<c>"), the operand
+ * preparation of U ("prep_u"), each column block of the first product
+ * ("x<c>"), each row block of the last second product with its conversion
+ * ("y<c>"), the end of each device-to-host row-block copy ("d2h<c>") and the
+ * end ("done").  tc_phases_read synchronises the recorded events and returns
+ * in ms[i] the time of mark i after the first mark (ms[0] = 0) and in
+ * `names` their names, one per line (both for the first `max` marks, names
+ * truncated to fit `names_bytes`); *count receives the number recorded.  The
+ * record is then cleared.  Measurement support only; no paper counterpart. */
+TC_API tc_status tc_phases_enable(int on);
+TC_API tc_status tc_phases_read(double* ms, char* names, size_t names_bytes, int max, int* count);
 
 /* ------------------------------------------------------ failure testing */
 

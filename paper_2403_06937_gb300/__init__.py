@@ -199,6 +199,16 @@ def observables(rho: torch.Tensor, n: int, params: Optional[Params] = None, stre
     return out
 
 
+def expectation_diag(rho: torch.Tensor, n: int, O_diag: torch.Tensor, stream=None) -> torch.Tensor:
+    """tc_expectation_diag: Tr(diag(O) rho) as a 0-d float64 tensor on rho's device."""
+    N = 1 << n
+    assert rho.dtype == torch.complex128 and rho.is_contiguous() and rho.shape == (N, N)
+    assert O_diag.dtype == torch.float64 and O_diag.is_contiguous() and O_diag.numel() == N
+    out = torch.empty((), dtype=torch.float64, device=rho.device)
+    _abi.call("tc_expectation_diag", _ptr(rho), n, _ptr(O_diag), _ptr(out), ctypes.c_void_p(_stream(stream)))
+    return out
+
+
 def evolve_host(U: torch.Tensor, rho_host: torch.Tensor, n: int, steps: int, precision="fp64",
                 renorm_every: int = 0, params: Optional[Params] = None, obs_host: Optional[torch.Tensor] = None,
                 stream=None, work: Optional[torch.Tensor] = None) -> None:
@@ -243,28 +253,45 @@ def evolve_backward(params: Params, dt: float, steps: int, rho0: torch.Tensor, U
 class EvolveFn(torch.autograd.Function):
     """L = Tr(diag(O) rho_K) as a differentiable function of (g, omega_a, omega_c).
 
-    forward: builds H (Eq. 4), U = e^{-iH dt} and steps rho0 K times (FP64);
-    backward: tc_evolve_backward (reverse mode with checkpoints).
+    forward: H (Eq. 4), U = e^{-iH dt} (tc_expm), K steps of rho <- U rho U^dag
+    (tc_evolve) and L (tc_expectation_diag); nothing of the reverse pass runs.
+    backward (only when a gradient is asked for): tc_evolve_backward, the
+    reverse mode with checkpoints every `ckpt_every` steps.
+    precision: "fp64" (DMMA products) or "ozaki" (the products emulated at FP64
+    accuracy on the BF16 tensor cores; n >= 7), for both passes.
     Inputs g (n,), omega_a (), omega_c () are float64 tensors; rho0 and O_diag
-    are CUDA tensors.  Returns a 0-d float64 tensor.
+    are CUDA tensors.  Returns a 0-d float64 tensor on rho0's device.
     """
 
     @staticmethod
-    def forward(ctx, g, omega_a, omega_c, rho0, O_diag, dt, steps, ckpt_every=20, coupling=TC_COUPLING_BOSONIC):
+    def forward(ctx, g, omega_a, omega_c, rho0, O_diag, dt, steps, ckpt_every=20, coupling=TC_COUPLING_BOSONIC,
+                precision="fp64"):
+        if precision not in ("fp64", "ozaki"):
+            raise ValueError("EvolveFn: precision must be 'fp64' or 'ozaki'")
         n = int(g.numel())
         params = Params(n, [float(x) for x in g.detach().cpu()], float(omega_a), float(omega_c), coupling)
         U = expm(build_hamiltonian(params, device=rho0.device), n, dt)
-        grad, loss = evolve_backward(params, dt, steps, rho0, U, O_diag, ckpt_every)
-        ctx.save_for_backward(grad)
-        ctx.n = n
-        return torch.tensor(loss, dtype=torch.float64, device=g.device)
+        rho, _ = evolve(U, rho0, n, steps, precision, params=params, observe=False)
+        O = O_diag.contiguous()
+        loss = expectation_diag(rho, n, O)
+        ctx.save_for_backward(rho0, O, U)
+        ctx.params, ctx.dt, ctx.steps, ctx.ckpt_every, ctx.precision = params, dt, steps, ckpt_every, precision
+        ctx.devices = (g.device, omega_a.device if torch.is_tensor(omega_a) else g.device,
+                       omega_c.device if torch.is_tensor(omega_c) else g.device)
+        return loss
 
     @staticmethod
     def backward(ctx, gout):
-        (grad,) = ctx.saved_tensors
-        grad = grad.to(gout.device) * gout
-        n = ctx.n
-        return grad[:n], grad[n], grad[n + 1], None, None, None, None, None, None
+        none = (None,) * 7
+        if not any(ctx.needs_input_grad[:3]):
+            return (None, None, None) + none
+        rho0, O, U = ctx.saved_tensors
+        grad, _ = evolve_backward(ctx.params, ctx.dt, ctx.steps, rho0, U, O, ctx.ckpt_every,
+                                  precision=ctx.precision)
+        n = ctx.params.n
+        scale = gout.detach().to("cpu", torch.float64)
+        dg, dwa, dwc = grad[:n] * scale, grad[n] * scale, grad[n + 1] * scale
+        return (dg.to(ctx.devices[0]), dwa.to(ctx.devices[1]), dwc.to(ctx.devices[2])) + none
 
 
 def batch_evolve(Us, rhos, steps: int, precision="bf16x3", renorm_every: int = 0, params=None,
@@ -350,14 +377,30 @@ def timing_read():
     return int(L.value), float(ms.value), float(fl.value)
 
 
+def phases_enable(on: bool = True) -> None:
+    """tc_phases_enable: record event marks at the phase boundaries of tc_evolve_host calls."""
+    _abi.call("tc_phases_enable", int(bool(on)))
+
+
+def phases_read(max_marks: int = 64):
+    """tc_phases_read: [(mark name, ms after the first mark)] recorded since the last read."""
+    ms = (ctypes.c_double * max_marks)()
+    names = ctypes.create_string_buffer(16 * max_marks + 1)
+    count = ctypes.c_int()
+    _abi.call("tc_phases_read", ms, names, len(names), int(max_marks), ctypes.byref(count))
+    got = names.value.decode().split("\n")[:min(count.value, max_marks)]
+    return [(nm, float(ms[i])) for i, nm in enumerate(got)]
+
+
 def sync_status(stream=None) -> None:
     _abi.call("tc_sync_status", ctypes.c_void_p(_stream(stream)))
 
 
 __all__ = ["Params", "TCError", "build_hamiltonian", "expm", "expm_model", "evolve", "LindbladLayout",
            "lindblad_layout", "lindblad_propagators", "lindblad_evolve", "evolve_host", "observables",
+           "expectation_diag",
            "evolve_backward", "EvolveFn", "batch_evolve", "autotune", "autotune_lookup", "autotune_set",
-           "workspace_size", "launch_count", "timing_enable", "timing_read",
+           "workspace_size", "launch_count", "timing_enable", "timing_read", "phases_enable", "phases_read",
            "device_check", "sync_status", "obs_stride", "PRECISIONS", "TC_FP64", "TC_BF16X3", "TC_TF32",
            "TC_TF32X3", "TC_COUPLING_BOSONIC", "TC_COUPLING_QUBIT_PHOTON", "TC_OP_EXPM", "TC_OP_EVOLVE",
            "TC_OP_OBSERVABLES", "TC_OP_BACKWARD"]

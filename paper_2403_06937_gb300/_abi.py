@@ -59,6 +59,7 @@ SIGNATURES = {
     "tc_lindblad_evolve": (I, [ctypes.POINTER(tc_params), D, D, VP, VP, I, I, I, VP, VP, SZ, VP]),
     "tc_evolve": (I, [VP, VP, I, I, I, I, ctypes.POINTER(tc_params), VP, VP, SZ, VP]),
     "tc_observables": (I, [VP, I, ctypes.POINTER(tc_params), VP, VP, SZ, VP]),
+    "tc_expectation_diag": (I, [VP, I, VP, VP, VP]),
     "tc_observables_noalloc": (I, [VP, I, ctypes.POINTER(tc_params), VP, VP]),
     "tc_evolve_backward": (I, [ctypes.POINTER(tc_params), D, I, VP, VP, I, I, VP, DP, DP, VP, SZ, VP]),
     "tc_evolve_host": (I, [VP, VP, I, I, I, I, ctypes.POINTER(tc_params), VP, VP, SZ, VP]),
@@ -71,6 +72,8 @@ SIGNATURES = {
     "tc_launch_count": (ctypes.c_longlong, []),
     "tc_timing_enable": (I, [I]),
     "tc_timing_read": (I, [ctypes.POINTER(ctypes.c_longlong), DP, DP]),
+    "tc_phases_enable": (I, [I]),
+    "tc_phases_read": (I, [DP, ctypes.c_char_p, SZ, I, ctypes.POINTER(I)]),
     "tc_fault_inject": (I, [I, I, D]),
     "tc_sync_status": (I, [VP]),
 }

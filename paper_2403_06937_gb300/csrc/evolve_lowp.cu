@@ -19,6 +19,8 @@
 // first step and the second product of the last.
 #include <cuda_bf16.h>
 
+#include <cstdio>
+
 #include "cgemm_tc.cuh"
 #include "graph.cuh"
 #include "lowp.cuh"
@@ -455,14 +457,22 @@ tc_status evolve_lowp_host_blocks(const double* U, double* rho_host, double* rho
     auto dev_rows = [&](size_t c) { return reinterpret_cast<char*>(rho_dev) + c * chunk; };
     auto host_rows = [&](size_t c) { return reinterpret_cast<char*>(rho_host) + c * chunk; };
 
+    char tag[16];
+    auto mark = [&](const char* what, int c, cudaStream_t on) {
+        std::snprintf(tag, sizeof(tag), c >= 0 ? "%s%d" : "%s", what, c);
+        phase_mark(tag, on);
+    };
     // rho in by row blocks on the copy stream (after earlier work on s that may use the staging)
+    mark("start", -1, s);
     TC_CUDA(cudaEventRecord(start, s));
     TC_CUDA(cudaStreamWaitEvent(lane.cs, start, 0));
     for (int c = 0; c < C; c++) {
         TC_CUDA(cudaMemcpyAsync(dev_rows(c), host_rows(c), chunk, cudaMemcpyHostToDevice, lane.cs));
         TC_CUDA(cudaEventRecord(h2d[c], lane.cs));
+        mark("h2d", c, lane.cs);
     }
     TC_TRY(lowp_prep_u(precision, U, b, s));
+    mark("prep_u", -1, s);
     // step 1, first product by column blocks: X[:, J] needs only the rows J of rho
     for (int c = 0; c < C; c++) {
         TC_CUDA(cudaStreamWaitEvent(s, h2d[c], 0));
@@ -471,6 +481,7 @@ tc_status evolve_lowp_host_blocks(const double* U, double* rho_host, double* rho
         e.lo = c * T / C;
         e.hi = (c + 1) * T / C;
         TC_TRY(cgemm_tc(precision, 0, sp.tmU, sp.tmR, e, s, sp.tune.tc_stages));
+        mark("x", c, s);
     }
     if (obs) TC_TRY(launch_observables(kRhoPlanarF32, b.Rr, b.Ri, m, n, obs, b.scratch, s, (size_t)b.Np));
     for (int k = 1; k <= steps; k++) {
@@ -485,9 +496,11 @@ tc_status evolve_lowp_host_blocks(const double* U, double* rho_host, double* rho
             // last step renormalised: rho' is whole only now; convert and copy out by row blocks
             for (int c = 0; c < C; c++) {
                 TC_TRY(lowp_finish(b, rho_dev, s, (int)(c * R), (int)((c + 1) * R)));
+                mark("y", c, s);
                 TC_CUDA(cudaEventRecord(fin[c], s));
                 TC_CUDA(cudaStreamWaitEvent(lane.cs, fin[c], 0));
                 TC_CUDA(cudaMemcpyAsync(host_rows(c), dev_rows(c), chunk, cudaMemcpyDeviceToHost, lane.cs));
+                mark("d2h", c, lane.cs);
             }
             break;
         }
@@ -499,9 +512,11 @@ tc_status evolve_lowp_host_blocks(const double* U, double* rho_host, double* rho
             e.hi = (c + 1) * T / C;
             TC_TRY(cgemm_tc(precision, 1, sp.tmU, sp.tmX, e, s, sp.tune.tc_stages));
             TC_TRY(lowp_finish(b, rho_dev, s, (int)(c * R), (int)((c + 1) * R)));
+            mark("y", c, s);
             TC_CUDA(cudaEventRecord(fin[c], s));
             TC_CUDA(cudaStreamWaitEvent(lane.cs, fin[c], 0));
             TC_CUDA(cudaMemcpyAsync(host_rows(c), dev_rows(c), chunk, cudaMemcpyDeviceToHost, lane.cs));
+            mark("d2h", c, lane.cs);
         }
         if (obs)
             TC_TRY(launch_observables(kRhoPlanarF32, b.Rr, b.Ri, m, n, obs + (size_t)k * stride, b.scratch, s,
@@ -509,6 +524,7 @@ tc_status evolve_lowp_host_blocks(const double* U, double* rho_host, double* rho
     }
     TC_CUDA(cudaEventRecord(done, lane.cs));
     TC_CUDA(cudaStreamWaitEvent(s, done, 0));
+    mark("done", -1, s);
     return TC_OK;
 }
 

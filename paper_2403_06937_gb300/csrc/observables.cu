@@ -149,6 +149,20 @@ __global__ void scale_kernel(T* re, T* im, size_t count, const double* trace, un
     }
 }
 
+// sum_s O_s Re rho[s][s] of an interleaved complex128 rho; one block, fixed order
+__global__ void expectation_diag_kernel(const double* rho, const double* O, unsigned N, double* out) {
+    __shared__ double s[1024];
+    double a = 0.0;
+    for (unsigned i = threadIdx.x; i < N; i += blockDim.x) a += O[i] * rho[2 * ((size_t)i * N + i)];
+    s[threadIdx.x] = a;
+    __syncthreads();
+    for (unsigned w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = s[0];
+}
+
 }  // namespace
 
 size_t observables_scratch_bytes(int n) {
@@ -210,6 +224,21 @@ tc_status launch_renormalise(int layout, void* re, void* im, int n, double* scra
 }
 
 }  // namespace tc
+
+extern "C" TC_API tc_status tc_expectation_diag(const void* rho, int n, const double* O_diag, double* out,
+                                                void* stream) {
+    using namespace tc;
+    if (n < 1 || n > kMaxAtoms) return fail(TC_ERR_INVALID_ARG, "n = %d outside 1..16", n);
+    if (!rho || !O_diag || !out) return fail(TC_ERR_INVALID_ARG, "rho, O_diag or out is NULL");
+    if ((reinterpret_cast<uintptr_t>(rho) | reinterpret_cast<uintptr_t>(O_diag) | reinterpret_cast<uintptr_t>(out)) &
+        7u)
+        return fail(TC_ERR_INVALID_ARG, "rho, O_diag and out must be 8-byte aligned");
+    TC_TRY(check_device());
+    expectation_diag_kernel<<<1, 1024, 0, as_stream(stream)>>>(static_cast<const double*>(rho), O_diag, 1u << n,
+                                                               out);
+    TC_LAUNCH_CHECK();
+    return TC_OK;
+}
 
 // ---------------------------------------------------------------------------
 // tc_observables_noalloc: the same two kernels with their per-block partial

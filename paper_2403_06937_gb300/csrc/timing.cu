@@ -2,6 +2,7 @@
 // launched, and optional CUDA-event pairs around the product (GEMM) kernels,
 // recorded on the stream those kernels are launched on.
 #include <atomic>
+#include <cstring>
 #include <mutex>
 #include <vector>
 
@@ -18,6 +19,12 @@ struct Pair {
 };
 std::vector<Pair> g_pairs;
 std::vector<cudaEvent_t> g_free;
+std::atomic<int> g_phases_on{0};
+struct Mark {
+    char name[16];
+    cudaEvent_t e;
+};
+std::vector<Mark> g_marks;
 
 cudaEvent_t take_event() {
     if (!g_free.empty()) {
@@ -48,6 +55,20 @@ ProductTimer::~ProductTimer() {
     cudaEventRecord(b_, s_);
     std::lock_guard<std::mutex> lk(g_mu);
     g_pairs.push_back({a_, b_, flops_});
+}
+
+void phase_mark(const char* name, cudaStream_t s) {
+    if (!g_phases_on.load()) return;
+    std::lock_guard<std::mutex> lk(g_mu);
+    Mark m{};
+    std::strncpy(m.name, name, sizeof(m.name) - 1);
+    m.e = take_event();
+    if (!m.e) return;
+    if (cudaEventRecord(m.e, s) != cudaSuccess) {
+        g_free.push_back(m.e);
+        return;
+    }
+    g_marks.push_back(m);
 }
 
 }  // namespace tc
@@ -82,6 +103,38 @@ TC_API tc_status tc_timing_read(long long* launches, double* ms, double* flops) 
     if (launches) *launches = n;
     if (ms) *ms = t;
     if (flops) *flops = f;
+    return st;
+}
+
+TC_API tc_status tc_phases_enable(int on) {
+    g_phases_on.store(on ? 1 : 0);
+    return TC_OK;
+}
+
+TC_API tc_status tc_phases_read(double* ms, char* names, size_t names_bytes, int max, int* count) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    tc_status st = TC_OK;
+    size_t used = 0;
+    if (names && names_bytes) names[0] = '\0';
+    for (size_t i = 0; i < g_marks.size(); i++) {
+        float e = 0.f;
+        if (cudaEventSynchronize(g_marks[i].e) != cudaSuccess ||
+            (i > 0 && cudaEventElapsedTime(&e, g_marks[0].e, g_marks[i].e) != cudaSuccess))
+            st = fail(TC_ERR_CUDA, "phases: event query failed");
+        if ((int)i < max) {
+            if (ms) ms[i] = e;
+            const size_t len = std::strlen(g_marks[i].name);
+            if (names && used + len + 2 <= names_bytes) {
+                std::memcpy(names + used, g_marks[i].name, len);
+                used += len;
+                names[used++] = '\n';
+                names[used] = '\0';
+            }
+        }
+    }
+    if (count) *count = (int)g_marks.size();
+    for (auto& m : g_marks) g_free.push_back(m.e);
+    g_marks.clear();
     return st;
 }
 

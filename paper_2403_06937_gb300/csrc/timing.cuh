@@ -24,4 +24,9 @@ class ProductTimer {
     cudaEvent_t a_ = nullptr, b_ = nullptr;
 };
 
+// When phase marks are enabled (tc_phases_enable), records a timing event on
+// stream `s` named `name` (copied, at most 15 characters); tc_phases_read
+// returns the marks' times relative to the first one.  A no-op otherwise.
+void phase_mark(const char* name, cudaStream_t s);
+
 }  // namespace tc

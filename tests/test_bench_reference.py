@@ -26,6 +26,9 @@ def test_reference_arm_line():
     assert d["value"] > 0 and d["unit"] == "steps/s" and d["steps"] == 2
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0
+    # each step of this arm is one bounded sample: steps x ms_per_step is the time the samples took
+    assert "step_kind" in d and 0 < d["ms_per_step"] < 60e3
+    assert d["steps"] * d["ms_per_step"] * 1e-3 < 120
 
 
 def test_reference_arm_without_oracle_form():

@@ -169,6 +169,32 @@ def test_n12_workload_sampled(tc, oracle):
     assert np.max(np.abs(obs.cpu().numpy() - oobs)) < 1e-10
 
 
+@pytest.mark.slow
+@pytest.mark.parametrize("precision", ["ozaki", "fp64"])
+def test_n12_workload_all_200_steps(tc, oracle, precision):
+    """The n = 12 FP64 workload over all its 200 steps, in both FP64 product
+    forms (DMMA and emulated on the BF16 tensor cores), against the oracle's
+    pure-state propagation: every observable row and the final rho (random
+    sample plus the block on the heaviest entries) within 1e-10 max-abs."""
+    cfg = W.config_n12()
+    p = _params(tc, cfg.n, cfg.g, cfg.omega_a, cfg.omega_c)
+    U = tc.expm(tc.build_hamiltonian(p), cfg.n, cfg.dt)
+    rho0 = torch.from_numpy(W.all_excited_rho(cfg.n)).cuda()
+    rho, obs = tc.evolve(U, rho0, cfg.n, cfg.steps, precision, params=p)
+    tc.sync_status()
+    psi, oobs = oracle.propagate(cfg.n, cfg.g, cfg.omega_a, cfg.omega_c, cfg.dt, cfg.steps,
+                                 W.all_excited_state(cfg.n))
+    e_obs = float(np.max(np.abs(obs.cpu().numpy() - oobs)))
+    rng = np.random.default_rng(12)
+    top = np.argsort(-np.abs(psi))[:64]
+    ii = np.concatenate([rng.integers(0, cfg.N, 20000), np.repeat(top, len(top))])
+    jj = np.concatenate([rng.integers(0, cfg.N, 20000), np.tile(top, len(top))])
+    got = rho[torch.from_numpy(ii).cuda(), torch.from_numpy(jj).cuda()].cpu().numpy()
+    e_rho = float(np.max(np.abs(got - psi[ii] * psi[jj].conj())))
+    print("n=12, 200 steps, %s: max|obs - oracle| %.2e, max|rho - oracle| %.2e" % (precision, e_obs, e_rho))
+    assert e_obs < 1e-10 and e_rho < 1e-10
+
+
 def test_short_workspace_is_an_error(tc):
     import ctypes
     from paper_2403_06937_gb300 import _abi

@@ -126,6 +126,60 @@ def test_autograd_function(tc):
     assert abs(wa.grad.item() - ref[n]) < 1e-14 and abs(wc.grad.item() - ref[n + 1]) < 1e-14
 
 
+def test_autograd_forward_runs_no_reverse_pass(tc, monkeypatch):
+    """The forward of EvolveFn is the evolution alone: without a gradient
+    request (no_grad, or inputs that need none) the reverse pass is never
+    called; backward calls it once."""
+    n, steps, dt = 4, 6, 0.3
+    calls = []
+    real = tc.evolve_backward
+
+    def counting(*args, **kw):
+        calls.append(1)
+        return real(*args, **kw)
+
+    monkeypatch.setattr(tc, "evolve_backward", counting)
+    rho0 = torch.from_numpy(W.all_excited_rho(n)).cuda()
+    O = torch.from_numpy(((np.arange(1 << n) >> (n - 2)) & 1).astype(np.float64)).cuda()
+    g0 = W.draw_couplings(n, 2) * 8
+    g = torch.tensor(g0, dtype=torch.float64)
+    L_plain = tc.EvolveFn.apply(g, torch.tensor(1.01, dtype=torch.float64), torch.tensor(1.0, dtype=torch.float64),
+                                rho0, O, dt, steps, 3)
+    with torch.no_grad():
+        gq = torch.tensor(g0, dtype=torch.float64, requires_grad=True)
+        L_nograd = tc.EvolveFn.apply(gq, torch.tensor(1.01, dtype=torch.float64),
+                                     torch.tensor(1.0, dtype=torch.float64), rho0, O, dt, steps, 3)
+    assert calls == [] and not L_plain.requires_grad
+    _, loss = _gpu_grad(tc, n, g0, 1.01, 1.0, dt, steps, 3, atom=2)
+    assert abs(L_plain.item() - loss) < 1e-14 and abs(L_nograd.item() - loss) < 1e-14
+    gr = torch.tensor(g0, dtype=torch.float64, requires_grad=True)
+    L = tc.EvolveFn.apply(gr, torch.tensor(1.01, dtype=torch.float64), torch.tensor(1.0, dtype=torch.float64),
+                          rho0, O, dt, steps, 3)
+    assert calls == []
+    L.backward()
+    assert calls == [1] and gr.grad is not None
+
+
+@pytest.mark.parametrize("precision", ["fp64", "ozaki"])
+def test_autograd_function_matches_oracle_tangent(tc, oracle, precision):
+    """EvolveFn in both product forms (FP64 DMMA and FP64 emulated on the BF16
+    tensor cores, which needs n >= 7) against the oracle's forward-mode tangent."""
+    n, steps, dt = 7, 20, 0.2
+    g0 = W.draw_couplings(n, 12) * 6
+    g = torch.tensor(g0, dtype=torch.float64, requires_grad=True)
+    wa = torch.tensor(1.02, dtype=torch.float64, requires_grad=True)
+    wc = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+    rho0 = torch.from_numpy(W.all_excited_rho(n)).cuda()
+    Od = oracle.atom_population_operator(n, 1)
+    L = tc.EvolveFn.apply(g, wa, wc, rho0, torch.from_numpy(Od).cuda(), dt, steps, 5, 0, precision)
+    L.backward()
+    ref = oracle.grad_forward(n, g0, 1.02, 1.0, dt, steps, W.all_excited_state(n), Od)
+    got = np.concatenate([g.grad.numpy(), [wa.grad.item(), wc.grad.item()]])
+    assert np.max(np.abs(got - ref)) <= 1e-9 * np.max(np.abs(ref))
+    _, obs = oracle.propagate(n, g0, 1.02, 1.0, dt, steps, W.all_excited_state(n))
+    assert abs(L.item() - obs[-1, 0]) < 1e-12
+
+
 def test_gradient_workload_n11(tc, oracle):
     """n = 11, dim 2048, 400 steps, checkpoints every 20: loss = P_1(T)."""
     cfg = W.config_n11_grad()

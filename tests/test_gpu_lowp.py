@@ -233,18 +233,63 @@ def test_zero_steps_round_trip_is_one_fp32_rounding(tc):
         assert a.max() > 0
 
 
+# Max-abs error over all 500 steps of the n = 14 workload against the oracle:
+# the split forms must meet the stated 1e-5 target; single-part TF32 is
+# reported (its operands carry 11 bits) and held to a loose bound only.
+N14_TARGET = {"bf16x3": 1e-5, "tf32x3": 1e-5, "tf32": 1e-3}
+
+
 @pytest.mark.slow
-def test_n14_500_steps_populations_bf16x3(tc, oracle):
-    """The n = 14 workload over all 500 steps (renormalised every 50) against the oracle's
-    pure-state propagation: populations, <p> and P(m) within the stated 1e-5 target."""
+@pytest.mark.parametrize("precision", ["bf16x3", "tf32x3", "tf32"])
+def test_n14_500_steps_against_oracle(tc, oracle, precision):
+    """The n = 14 workload over all 500 steps (renormalised every 50) against the
+    oracle's pure-state propagation: populations, <p> and P(m) of every step,
+    and the final rho on a random sample and the heaviest entries."""
     cfg = W.config_n14()
     n = cfg.n
     p = tc.Params(n, list(map(float, cfg.g)), cfg.omega_a, cfg.omega_c)
     U = tc.expm_model(p, cfg.dt)
     rho0 = torch.zeros((cfg.N, cfg.N), dtype=torch.complex128, device="cuda")
     rho0[-1, -1] = 1.0
-    _, obs = tc.evolve(U, rho0, n, cfg.steps, "bf16x3", renorm_every=cfg.renorm_every, params=p)
+    rho, obs = tc.evolve(U, rho0, n, cfg.steps, precision, renorm_every=cfg.renorm_every, params=p)
     tc.sync_status()
-    _, oobs = oracle.propagate(n, cfg.g, cfg.omega_a, cfg.omega_c, cfg.dt, cfg.steps, W.all_excited_state(n))
+    psi, oobs = oracle.propagate(n, cfg.g, cfg.omega_a, cfg.omega_c, cfg.dt, cfg.steps, W.all_excited_state(n))
     o = obs.cpu().numpy()
-    assert np.max(np.abs(o[:, :2 * n + 2] - oobs[:, :2 * n + 2])) < 1e-5
+    e_pop = float(np.max(np.abs(o[:, :n] - oobs[:, :n])))
+    e_obs = float(np.max(np.abs(o[:, :2 * n + 2] - oobs[:, :2 * n + 2])))
+    rng = np.random.default_rng(14)
+    top = np.argsort(-np.abs(psi))[:48]
+    ii = np.concatenate([rng.integers(0, cfg.N, 20000), np.repeat(top, len(top))])
+    jj = np.concatenate([rng.integers(0, cfg.N, 20000), np.tile(top, len(top))])
+    got = rho[torch.from_numpy(ii).cuda(), torch.from_numpy(jj).cuda()].cpu().numpy()
+    e_rho = float(np.max(np.abs(got - psi[ii] * psi[jj].conj())))
+    print("n=14, 500 steps, %s: populations %.2e, populations/<p>/P(m) %.2e, rho sampled %.2e"
+          % (precision, e_pop, e_obs, e_rho))
+    assert e_obs < N14_TARGET[precision] and e_rho < N14_TARGET[precision]
+
+
+@pytest.mark.slow
+def test_n15_split_bf16_against_oracle(tc, oracle):
+    """n = 15, dim 32768 (the paper's largest dimension; the inner dimension
+    K = 32768 is accumulated in FP32 on the tensor cores), split-BF16, a few
+    steps against the oracle: observables and sampled entries within 1e-5."""
+    cfg = W.config_n15()
+    n, steps = cfg.n, 3
+    p = tc.Params(n, list(map(float, cfg.g)), cfg.omega_a, cfg.omega_c)
+    U = tc.expm_model(p, cfg.dt)
+    rho0 = torch.zeros((cfg.N, cfg.N), dtype=torch.complex128, device="cuda")
+    rho0[-1, -1] = 1.0
+    rho, obs = tc.evolve(U, rho0, n, steps, "bf16x3", renorm_every=cfg.renorm_every, params=p)
+    tc.sync_status()
+    del U
+    psi, oobs = oracle.propagate(n, cfg.g, cfg.omega_a, cfg.omega_c, cfg.dt, steps, W.all_excited_state(n))
+    o = obs.cpu().numpy()
+    e_obs = float(np.max(np.abs(o[:, :2 * n + 3] - oobs[:, :2 * n + 3])))
+    rng = np.random.default_rng(15)
+    top = np.argsort(-np.abs(psi))[:48]
+    ii = np.concatenate([rng.integers(0, cfg.N, 20000), np.repeat(top, len(top))])
+    jj = np.concatenate([rng.integers(0, cfg.N, 20000), np.tile(top, len(top))])
+    got = rho[torch.from_numpy(ii).cuda(), torch.from_numpy(jj).cuda()].cpu().numpy()
+    e_rho = float(np.max(np.abs(got - psi[ii] * psi[jj].conj())))
+    print("n=15, %d steps, bf16x3: observables %.2e, rho sampled %.2e" % (steps, e_obs, e_rho))
+    assert e_obs < 1e-5 and e_rho < 1e-5
