@@ -131,6 +131,8 @@ def test_autograd_forward_runs_no_reverse_pass(tc, monkeypatch):
     request (no_grad, or inputs that need none) the reverse pass is never
     called; backward calls it once."""
     n, steps, dt = 4, 6, 0.3
+    g0 = W.draw_couplings(n, 2) * 8
+    _, loss = _gpu_grad(tc, n, g0, 1.01, 1.0, dt, steps, 3, atom=2)   # reference value, before counting
     calls = []
     real = tc.evolve_backward
 
@@ -141,7 +143,6 @@ def test_autograd_forward_runs_no_reverse_pass(tc, monkeypatch):
     monkeypatch.setattr(tc, "evolve_backward", counting)
     rho0 = torch.from_numpy(W.all_excited_rho(n)).cuda()
     O = torch.from_numpy(((np.arange(1 << n) >> (n - 2)) & 1).astype(np.float64)).cuda()
-    g0 = W.draw_couplings(n, 2) * 8
     g = torch.tensor(g0, dtype=torch.float64)
     L_plain = tc.EvolveFn.apply(g, torch.tensor(1.01, dtype=torch.float64), torch.tensor(1.0, dtype=torch.float64),
                                 rho0, O, dt, steps, 3)
@@ -150,7 +151,6 @@ def test_autograd_forward_runs_no_reverse_pass(tc, monkeypatch):
         L_nograd = tc.EvolveFn.apply(gq, torch.tensor(1.01, dtype=torch.float64),
                                      torch.tensor(1.0, dtype=torch.float64), rho0, O, dt, steps, 3)
     assert calls == [] and not L_plain.requires_grad
-    _, loss = _gpu_grad(tc, n, g0, 1.01, 1.0, dt, steps, 3, atom=2)
     assert abs(L_plain.item() - loss) < 1e-14 and abs(L_nograd.item() - loss) < 1e-14
     gr = torch.tensor(g0, dtype=torch.float64, requires_grad=True)
     L = tc.EvolveFn.apply(gr, torch.tensor(1.01, dtype=torch.float64), torch.tensor(1.0, dtype=torch.float64),
