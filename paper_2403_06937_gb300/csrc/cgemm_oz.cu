@@ -334,6 +334,217 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 constexpr int kSmem = kStages * kStage + 1024 /*align*/ + 256 /*barriers*/;
 
+// ---------------------------------------------------------------------------
+// CTA pairs on the 2-SM MMA (cta_group::2).  The two CTAs of a cluster take
+// the row tiles I = 2p and 2p + 1 of one column tile J.  Each loads into its
+// own shared memory the slice-t panels of its own U_r and U_i rows and one
+// half of the B stack: P_r slice u in the even CTA, P_i slice u in the odd
+// one (12 KB a stage, no operand is loaded twice and nothing is multicast).
+// The even CTA's MMA thread issues M = 256 pair MMAs (its A rows and the odd
+// CTA's, B from both halves) into both CTAs' TMEM, so each CTA's tensor core
+// reads 8 KB of shared memory per MMA instead of 12.  Coordination:
+//   full[s]        (even CTA) stage s of both CTAs landed: the even CTA arms
+//                  it for both CTAs' bytes, the odd CTA's copies complete
+//                  their bytes on it (cta_group::2 copies);
+//   empty[s]       each CTA's stage s released: the MMA thread commits to the
+//                  even CTA's barrier and, by its cluster address, the odd one's;
+//   accum          (both) a pass's accumulators are complete (two commits);
+//   tmem_empty     (even CTA, count 2) both epilogues have read a pass.
+// Every wait is bounded; a timeout raises the abort flag of both CTAs, the
+// copies in flight land (the even CTA waits for its armed stages, the odd
+// one, whose copies complete on the even CTA's barriers, waits a fixed
+// 1 ms), the MMA thread waits for its MMAs, and both meet at a cluster
+// barrier before TMEM is freed and either CTA exits.
+constexpr int kPairStages = 16;
+constexpr int kPairStage = 3 * kATile;   // U_r, U_i slice rows + half of the B stack: 12 KB
+constexpr int kPairGroup = 6;            // row pairs per raster group (a wave: ~12 row x 12 column tiles)
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, 1)
+    cgemm_oz_pair_kernel(const __grid_constant__ CUtensorMap tmU, const __grid_constant__ CUtensorMap tmP, OzEpi ep) {
+    constexpr uint32_t kIdesc = make_idesc(1u, 256u, 256u);   // BF16 x BF16 -> FP32, M 256 (128 per CTA), N 256
+
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + kPairStages * kPairStage);
+    uint64_t* empty = full + kPairStages;
+    uint64_t* accum = empty + kPairStages;
+    uint64_t* tmem_empty = accum + 1;
+    uint64_t* drain = tmem_empty + 1;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint64_t lim = ep.wait_ns ? ep.wait_ns : kWaitLimitNs;
+    const uint32_t rank = cluster_ctarank();
+    int I, J;
+    pair_tile_rows(MODE, ep.tiles, kPairGroup, (int)(blockIdx.x >> 1), (int)rank, I, J);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kPairStages; s++) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(accum, 1);
+        mbar_init(tmem_empty, 2);
+        mbar_init(drain, 1);
+        *abort = 0;
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        tmem_alloc_pair(saddr(tmem_slot), 512);
+        tmem_relinquish_pair();
+    }
+    if (warp == 4 && lane == 0) {
+        prefetch_tmap(&tmU);
+        prefetch_tmap(&tmP);
+    }
+    __syncthreads();
+    cluster_sync();   // both CTAs' barriers exist before either arrives on the other's
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t peer_abort = cluster_addr(saddr(const_cast<int*>(abort)), rank ^ 1u);
+    const int S = ep.slices;
+    const int kmax = 1 << (26 - 2 * ep.bits);
+    const int Kc = ep.Np < kmax ? ep.Np : kmax;
+    const int chunks = ep.Np / Kc;
+    const int KBc = Kc / kKPerStage;
+    const int passes = S * (S + 1) / 2 * chunks;
+
+    if (warp == 4) {
+        // ---------------------------------------------------------- producer (both CTAs)
+        if (lane == 0) {
+            const uint64_t keep = l2_policy_evict_last();
+            const uint32_t lead_full = cluster_addr(saddr(&full[0]), 0u);
+            uint32_t it = 0;
+            bool ok = true;
+            for (int p = 0; p < passes && ok; p++) {
+                int t, u;
+                oz_pair(p / chunks, S, t, u);
+                const int c = p % chunks;
+                for (int kb = 0; kb < KBc; kb++, it++) {
+                    const int s = it % kPairStages;
+                    const uint32_t ph = (it / kPairStages) & 1u;
+                    if (!mbar_wait_bounded(&empty[s], ph ^ 1u, abort, lim, 0)) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t* st = smem + s * kPairStage;
+                    const int kx = c * Kc + kb * kKPerStage;
+                    if (rank == 0) {
+                        mbar_arrive_expect_tx(&full[s], 2 * kPairStage);   // both CTAs' bytes
+                        const uint32_t fb = saddr(&full[s]);
+                        tma_load_3d_hint(saddr(st), &tmU, fb, kx, I * 128, t, keep);                // U_r slice t
+                        tma_load_3d_hint(saddr(st + kATile), &tmU, fb, kx, I * 128, S + t, keep);   // U_i slice t
+                        tma_load_3d(saddr(st + 2 * kATile), &tmP, fb, kx, J * 128, u);              // P_r slice u
+                    } else {
+                        const uint32_t fb = lead_full + 8u * (uint32_t)s;
+                        tma_load_3d_pair_hint(saddr(st), &tmU, fb, kx, I * 128, t, keep);
+                        tma_load_3d_pair_hint(saddr(st + kATile), &tmU, fb, kx, I * 128, S + t, keep);
+                        tma_load_3d_pair(saddr(st + 2 * kATile), &tmP, fb, kx, J * 128, S + u);     // P_i slice u
+                    }
+                }
+            }
+            const uint32_t from = it > (uint32_t)kPairStages ? it - kPairStages : 0u;
+            if (!ok || *abort) {
+                *abort = 1;
+                st_cluster_u32(peer_abort, 1u);
+                // the copies in flight land before the CTAs go away
+                if (rank == 0) {
+                    for (uint32_t k = from; k < it; k++)
+                        (void)mbar_wait_bounded(&full[k % kPairStages], (k / kPairStages) & 1u, nullptr,
+                                                10000000ull, 0);
+                } else {
+                    spin_ns(1000000ull);
+                }
+            } else {
+                // the last releases of this CTA's stages have arrived (no commit of the
+                // pair's MMAs is still on its way to this CTA's barriers)
+                for (uint32_t k = from; k < it; k++)
+                    (void)mbar_wait_bounded(&empty[k % kPairStages], (k / kPairStages) & 1u, abort, lim, 0);
+            }
+        }
+    } else if (warp == 5) {
+        if (lane == 0 && rank == 0) {
+            // ------------------------------------------------------ MMA issuer (even CTA)
+            const uint32_t peer_empty = cluster_addr(saddr(&empty[0]), 1u);
+            const uint32_t peer_accum = cluster_addr(saddr(accum), 1u);
+            uint32_t it = 0;
+            bool ok = true;
+            for (int p = 0; p < passes && ok; p++) {
+                if (p > 0 && !mbar_wait_bounded_cluster(tmem_empty, (uint32_t)(p - 1) & 1u, abort, lim, 0)) break;
+                tc_fence_after();
+                for (int kb = 0; kb < KBc; kb++, it++) {
+                    const int s = it % kPairStages;
+                    const uint32_t ph = (it / kPairStages) & 1u;
+                    if (!mbar_wait_bounded_cluster(&full[s], ph, abort, lim, 0)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    uint8_t* st = smem + s * kPairStage;
+                    const uint64_t bd = desc_kmajor_sw32(saddr(st + 2 * kATile));
+                    umma_pair(tmem, desc_kmajor_sw32(saddr(st)), bd, kIdesc, kb > 0 ? 1u : 0u);
+                    umma_pair(tmem + 256, desc_kmajor_sw32(saddr(st + kATile)), bd, kIdesc, kb > 0 ? 1u : 0u);
+                    umma_commit_pair(saddr(&empty[s]));
+                    umma_commit_pair(peer_empty + 8u * (uint32_t)s);
+                }
+                if (!ok) break;
+                umma_commit_pair(saddr(accum));
+                umma_commit_pair(peer_accum);
+            }
+            // the pair MMAs (into both CTAs' TMEM) complete before either frees it
+            umma_commit_pair(saddr(drain));
+            (void)mbar_wait_bounded(drain, 0u, nullptr, lim, 0);
+            if (*abort) st_cluster_u32(peer_abort, 1u);
+        }
+    } else {
+        // ---------------------------------------------------------- epilogue (both CTAs, own rows)
+        const uint32_t lead_tmem_empty = cluster_addr(saddr(tmem_empty), 0u);
+        for (int p = 0; p < passes; p++) {
+            const bool ok = mbar_wait_bounded_cluster(accum, (uint32_t)p & 1u, abort, lim, 128);
+            tc_fence_after();
+            uint32_t bad = (!ok || *abort) ? 1u : 0u, any;
+            asm volatile(
+                "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+                "bar.red.or.pred q, 1, 128, p;\n\tselp.u32 %0, 1, 0, q;\n}"
+                : "=r"(any)
+                : "r"(bad)
+                : "memory");
+            if (any) {
+                if (threadIdx.x == 0) {
+                    *abort = 1;
+                    st_cluster_u32(peer_abort, 1u);
+                }
+                break;
+            }
+            int t, u;
+            oz_pair(p / chunks, S, t, u);
+            oz_epilogue(tmem, warp, lane, I, J, ep, t + u, p == 0, p == 4 * chunks, p == passes - 1);
+            tc_fence_before();
+            asm volatile("bar.sync 1, 128;" ::: "memory");   // all four epilogue warps have read TMEM
+            if (threadIdx.x == 0) {
+                if (rank == 0)
+                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(tmem_empty)) : "memory");
+                else
+                    mbar_arrive_cluster(lead_tmem_empty);
+            }
+        }
+        if (*abort && threadIdx.x == 0) atomicOr(ep.status, kStatusTimeout);
+    }
+
+    __syncwarp();
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();   // neither CTA frees TMEM or leaves while the other may still use it
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc_pair(tmem, 512);
+    }
+}
+
+constexpr int kPairSmem = kPairStages * kPairStage + 1024 /*align*/ + 512 /*barriers*/;
+
 // One warp per row r < Np: the row exponent over both planes, then the S
 // balanced base-2^b digits of every entry (zero beyond the valid N x N block).
 // INTERLEAVED: re/im interleaved complex128 with row stride ld (complex
@@ -435,11 +646,58 @@ tc_status launch(const CUtensorMap& tmU, const CUtensorMap& tmP, const OzEpi& ep
     return TC_OK;
 }
 
+// Pairs of CTAs (clusters of 2) on the 2-SM MMA: T even; mode 0 T * T / 2
+// pairs, mode 1 sum over row pairs p of (2p + 2).
+template <int MODE>
+tc_status launch_pair(const CUtensorMap& tmU, const CUtensorMap& tmP, const OzEpi& ep, cudaStream_t s) {
+    auto k = cgemm_oz_pair_kernel<MODE>;
+    static bool attr_set[64] = {};
+    int dev = 0;
+    TC_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(TC_ERR_UNSUPPORTED_DEVICE, "device index out of range");
+    if (!attr_set[dev]) {
+        TC_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kPairSmem));
+        attr_set[dev] = true;
+    }
+    const int TP = ep.tiles / 2;
+    const unsigned pairs = MODE == 0 ? (unsigned)(ep.tiles * TP) : (unsigned)(TP * (TP + 1));
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(2 * pairs);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = kPairSmem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    TC_CUDA(cudaLaunchKernelEx(&cfg, k, tmU, tmP, ep));
+    TC_LAUNCH_CHECK();
+    return TC_OK;
+}
+
+// -1: not read yet; else TC_OZ_PAIRS from the environment (0: single CTAs at
+// every size; anything else, or unset: CTA pairs wherever the tile count is
+// even).  Both arrangements give the same bits.
+std::atomic<int> g_oz_pairs{-1};
+
 // -1: not chosen yet (TC_OZ_BITS=6 in the environment: 6-bit digits at every
 // size; else the widest digits K allows)
 std::atomic<int> g_oz_narrow{-1};
 
 }  // namespace
+
+bool oz_use_pairs(int tiles) {
+    int v = g_oz_pairs.load();
+    if (v < 0) {
+        const char* e = std::getenv("TC_OZ_PAIRS");
+        v = e && std::atoi(e) == 0 ? 0 : 1;
+        g_oz_pairs.store(v);
+    }
+    return v != 0 && tiles >= 2 && tiles % 2 == 0;
+}
 
 OzDigits oz_digits(int Np) {
     int narrow = g_oz_narrow.load();
@@ -481,6 +739,10 @@ tc_status cgemm_oz(int mode, const CUtensorMap& tmU, const CUtensorMap& tmP, con
         return fail(TC_ERR_INVALID_ARG, "cgemm_oz: digit width does not match the dimension");
     if (ep.Np > dg.kmax && ep.Np % dg.kmax != 0)
         return fail(TC_ERR_INVALID_ARG, "cgemm_oz: dimension above %d must be a multiple of it", dg.kmax);
+    if (oz_use_pairs(ep.tiles)) {
+        if (mode == 0) return launch_pair<0>(tmU, tmP, ep, s);
+        if (mode == 1) return launch_pair<1>(tmU, tmP, ep, s);
+    }
     if (mode == 0) return launch<0>(tmU, tmP, ep, s);
     if (mode == 1) return launch<1>(tmU, tmP, ep, s);
     return fail(TC_ERR_INVALID_ARG, "cgemm_oz: mode");

@@ -49,6 +49,10 @@ size_t oz_slice_bytes(int Np);
 // Y = U P^H (mode 0: all tiles; mode 1: block-lower tiles, then oz_mirror)
 tc_status cgemm_oz(int mode, const CUtensorMap& tmU, const CUtensorMap& tmP, const OzEpi& ep, cudaStream_t s);
 tc_status oz_mirror(double* yr, double* yi, int Np, cudaStream_t s);
+// True when the product of `tiles` tiles a side runs as CTA pairs on the 2-SM
+// MMA (an even tile count, unless TC_OZ_PAIRS=0 in the environment); else
+// single CTAs.  Both give the same bits.
+bool oz_use_pairs(int tiles);
 
 // One operand of the emulated product: its digit slices, row exponents and
 // TMA map (row r of the operand = row r of A, or row r of B in A B^H).

@@ -40,6 +40,7 @@
 #include <cuda_bf16.h>
 
 #include <atomic>
+#include <cstdlib>
 
 #include "cgemm_dev.cuh"
 #include "cgemm_tc.cuh"
@@ -198,12 +199,244 @@ tc_status launch(const CUtensorMap& tmU, const CUtensorMap& tmP, const CgemmEpi&
     return TC_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// CTA pairs on the 2-SM MMA (cta_group::2).  The two CTAs of a cluster take
+// the row tiles I = 2p and 2p + 1 of one column tile J.  Each loads into its
+// own shared memory all S parts of its own U_r and U_i rows and one half of
+// every B part (P_r parts in the even CTA, P_i parts in the odd one): a stage
+// is 12 S KB instead of 16 S KB, and each CTA's tensor core reads 8 KB of
+// shared memory per MMA instead of 12.  The even CTA arms its full barrier
+// of each stage for both CTAs' bytes; the odd CTA's copies (cta_group::2
+// copies) complete their bytes on it.  The even CTA's MMA thread issues
+// M = 256 pair MMAs into both CTAs' TMEM; the MMA completions release the
+// stages of both CTAs (commits to each CTA's barrier by address).  Nothing
+// is multicast.  Each CTA's epilogue writes its own tile exactly as the
+// single-CTA kernel does; in the Hermitian launch the tile (2p, 2p + 1)
+// above the diagonal is computed and not written (its lower partner writes
+// both).  Every wait is bounded; a timeout raises the abort flag of both
+// CTAs, the copies in flight land (the even CTA waits for its armed stages,
+// the odd one a fixed 1 ms), the MMA thread waits for its MMAs, and both
+// meet at a cluster barrier before TMEM is freed.
+template <int KIND, int S, int STAGES, int MODE>
+__global__ void __launch_bounds__(kThreads, 1)
+    cgemm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmU, const __grid_constant__ CUtensorMap tmP,
+                         CgemmEpi ep) {
+    constexpr int kStage = 3 * S * kATile;   // own U_r, U_i parts + own half of each B part
+    constexpr int kElem = KIND == 0 ? 2 : 4;
+    constexpr int kKPerStage = kRowBytes / kElem;
+    constexpr uint32_t kIdesc = make_idesc(KIND == 0 ? 1u : 2u, 256u, 256u);
+
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * kStage);
+    uint64_t* empty = full + STAGES;
+    uint64_t* accum = empty + STAGES;
+    uint64_t* drain = accum + 1;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint64_t lim = ep.wait_ns ? ep.wait_ns : kWaitLimitNs;
+    const uint32_t rank = cluster_ctarank();
+    int I, J;
+    pair_tile_rows_range(MODE, ep.tiles, ep.group > 1 ? ep.group / 2 : 1, ep.hi > 0 ? ep.lo : 0,
+                         ep.hi > 0 ? ep.hi : ep.tiles, (int)(blockIdx.x >> 1), (int)rank, I, J);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; s++) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(accum, 1);
+        mbar_init(drain, 1);
+        *abort = 0;
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        tmem_alloc_pair(saddr(tmem_slot), 512);
+        tmem_relinquish_pair();
+    }
+    if (warp == 4 && lane == 0) {
+        prefetch_tmap(&tmU);
+        prefetch_tmap(&tmP);
+    }
+    __syncthreads();
+    cluster_sync();   // both CTAs' barriers exist before either arrives on the other's
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t peer_abort = cluster_addr(saddr(const_cast<int*>(abort)), rank ^ 1u);
+    const int KB = ep.Np / kKPerStage;
+
+    if (warp == 4) {
+        // ---------------------------------------------------------- producer (both CTAs)
+        if (lane == 0) {
+            const uint32_t lead_full = cluster_addr(saddr(&full[0]), 0u);
+            int issued = 0;
+            bool ok = true;
+            for (int kb = 0; kb < KB; kb++) {
+                const int s = kb % STAGES;
+                const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+                if (!mbar_wait_bounded(&empty[s], ph ^ 1u, abort, lim, 0)) {
+                    ok = false;
+                    break;
+                }
+                issued = kb + 1;
+                if (ep.withhold && kb == 0) continue;   // injected fault: stage 0 is never filled
+                uint8_t* st = smem + s * kStage;
+                const int kx = kb * kKPerStage;
+                if (rank == 0) {
+                    mbar_arrive_expect_tx(&full[s], 2 * kStage);   // both CTAs' bytes
+                    const uint32_t fb = saddr(&full[s]);
+#pragma unroll
+                    for (int part = 0; part < 2; part++)
+#pragma unroll
+                        for (int a = 0; a < S; a++)
+                            tma_load_3d(saddr(st + (part * S + a) * kATile), &tmU, fb, kx, I * 128, part * S + a);
+#pragma unroll
+                    for (int b = 0; b < S; b++)   // P_r part b
+                        tma_load_3d(saddr(st + (2 * S + b) * kATile), &tmP, fb, kx, J * 128, b);
+                } else {
+                    const uint32_t fb = lead_full + 8u * (uint32_t)s;
+#pragma unroll
+                    for (int part = 0; part < 2; part++)
+#pragma unroll
+                        for (int a = 0; a < S; a++)
+                            tma_load_3d_pair(saddr(st + (part * S + a) * kATile), &tmU, fb, kx, I * 128,
+                                             part * S + a);
+#pragma unroll
+                    for (int b = 0; b < S; b++)   // P_i part b
+                        tma_load_3d_pair(saddr(st + (2 * S + b) * kATile), &tmP, fb, kx, J * 128, S + b);
+                }
+            }
+            const int from = issued - STAGES > 0 ? issued - STAGES : 0;
+            if (!ok || *abort) {
+                *abort = 1;
+                st_cluster_u32(peer_abort, 1u);
+                // the copies in flight land before the CTAs go away
+                if (rank == 0) {
+                    for (int kb = from; kb < issued; kb++)
+                        if (!(ep.withhold && kb == 0))
+                            (void)mbar_wait_bounded(&full[kb % STAGES], (uint32_t)(kb / STAGES) & 1u, nullptr,
+                                                    10000000ull, 0);
+                } else {
+                    spin_ns(1000000ull);
+                }
+            } else {
+                // the last releases of this CTA's stages have arrived
+                for (int kb = from; kb < issued; kb++)
+                    (void)mbar_wait_bounded(&empty[kb % STAGES], (uint32_t)(kb / STAGES) & 1u, abort, lim, 0);
+            }
+        }
+    } else if (warp == 5) {
+        if (lane == 0 && rank == 0) {
+            // ------------------------------------------------------ MMA issuer (even CTA)
+            const uint32_t peer_empty = cluster_addr(saddr(&empty[0]), 1u);
+            for (int kb = 0; kb < KB; kb++) {
+                const int s = kb % STAGES;
+                const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+                if (!mbar_wait_bounded_cluster(&full[s], ph, abort, lim, 0)) break;
+                tc_fence_after();
+                uint8_t* st = smem + s * kStage;
+#pragma unroll
+                for (int p = 0; p < Pairs<S>::n; p++) {
+                    const uint64_t bd = desc_kmajor_sw32(saddr(st + (2 * S + Pairs<S>::b(p)) * kATile));
+#pragma unroll
+                    for (int part = 0; part < 2; part++) {
+                        const uint64_t ad = desc_kmajor_sw32(saddr(st + (part * S + Pairs<S>::a(p)) * kATile));
+                        umma_pair(tmem + part * 256, ad, bd, kIdesc, (kb > 0 || p > 0) ? 1u : 0u);
+                    }
+                }
+                umma_commit_pair(saddr(&empty[s]));
+                umma_commit_pair(peer_empty + 8u * (uint32_t)s);
+            }
+            // always: complete when every pair MMA issued above has finished
+            umma_commit_pair(saddr(accum));
+            umma_commit_pair(cluster_addr(saddr(accum), 1u));
+            umma_commit_pair(saddr(drain));
+            (void)mbar_wait_bounded(drain, 0u, nullptr, lim, 0);
+            if (*abort) st_cluster_u32(peer_abort, 1u);
+        }
+    } else {
+        // ---------------------------------------------------------- epilogue (both CTAs, own tile)
+        const bool ok = mbar_wait_bounded_cluster(accum, 0u, abort, lim, 128);
+        tc_fence_after();
+        if (ok && !*abort && !(MODE == 1 && J > I))
+            cg::epilogue_tile<KIND, S, MODE>(tmem, warp, lane, I, J, ep.Np, ep.pr, ep.pi, ep.parts, ep.yr, ep.yi);
+        if (!ok || *abort) {
+            if (threadIdx.x == 0) {
+                atomicOr(ep.status, kStatusTimeout);
+                st_cluster_u32(peer_abort, 1u);
+            }
+        }
+    }
+
+    __syncwarp();
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();   // neither CTA frees TMEM or leaves while the other may still use it
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc_pair(tmem, 512);
+    }
+}
+
+template <int KIND, int S, int STAGES>
+constexpr int pair_smem_bytes() {
+    return STAGES * 3 * S * kATile + 1024 /*align*/ + 512 /*barriers*/;
+}
+
+template <int KIND, int S, int STAGES, int MODE>
+tc_status launch_pair(const CUtensorMap& tmU, const CUtensorMap& tmP, const CgemmEpi& ep, cudaStream_t s) {
+    auto k = cgemm_tc_pair_kernel<KIND, S, STAGES, MODE>;
+    constexpr int smem = pair_smem_bytes<KIND, S, STAGES>();
+    static bool attr_set[64] = {};
+    int dev = 0;
+    TC_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(TC_ERR_UNSUPPORTED_DEVICE, "device index out of range");
+    if (!attr_set[dev]) {
+        TC_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        attr_set[dev] = true;
+    }
+    const int lo = ep.hi > 0 ? ep.lo : 0, hi = ep.hi > 0 ? ep.hi : ep.tiles;
+    const unsigned pairs = (unsigned)pair_count(MODE, ep.tiles, lo, hi);
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(2 * pairs);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    TC_CUDA(cudaLaunchKernelEx(&cfg, k, tmU, tmP, ep));
+    TC_LAUNCH_CHECK();
+    return TC_OK;
+}
 }  // namespace
 
 namespace {
 std::atomic<int> g_inject_count{0};
 std::atomic<unsigned long long> g_inject_wait{0};
+// -1: not read yet; else TC_GEMM_PAIRS from the environment (0: single CTAs
+// at every size; anything else, or unset: CTA pairs wherever they apply)
+std::atomic<int> g_pairs{-1};
 }  // namespace
+
+bool cgemm_use_pairs(int tiles, int mode, int lo, int hi) {
+    int v = g_pairs.load();
+    if (v < 0) {
+        const char* e = std::getenv("TC_GEMM_PAIRS");
+        v = e && std::atoi(e) == 0 ? 0 : 1;
+        g_pairs.store(v);
+    }
+    if (v == 0 || tiles < 2 || tiles % 2 != 0) return false;
+    // a Hermitian launch over a row band needs whole row pairs
+    return !(mode == 1 && hi > 0 && (lo % 2 != 0 || hi % 2 != 0));
+}
 
 void cgemm_inject_timeout(int count, unsigned long long wait_ns) {
     g_inject_wait.store(wait_ns);
@@ -235,6 +468,22 @@ tc_status cgemm_tc(int precision, int mode, const CUtensorMap& tmU, const CUtens
     const bool alt = stages == cgemm_alt_stages(precision);
     if (!alt && stages != cgemm_default_stages(precision))
         return fail(TC_ERR_INVALID_ARG, "cgemm_tc: %d stages not built for precision %d", stages, precision);
+    if (cgemm_use_pairs(ep.tiles, mode, ep.lo, ep.hi)) {
+        // CTA pairs: rings of {6, 4} (BF16x3), {9, 6} (TF32x3), {18, 12} (TF32) stages of 12 S KB
+        switch (precision) {
+            case TC_BF16X3:
+                if (alt) return mode == 0 ? launch_pair<0, 3, 4, 0>(tmU, tmP, ep, s) : launch_pair<0, 3, 4, 1>(tmU, tmP, ep, s);
+                return mode == 0 ? launch_pair<0, 3, 6, 0>(tmU, tmP, ep, s) : launch_pair<0, 3, 6, 1>(tmU, tmP, ep, s);
+            case TC_TF32:
+                if (alt) return mode == 0 ? launch_pair<1, 1, 12, 0>(tmU, tmP, ep, s) : launch_pair<1, 1, 12, 1>(tmU, tmP, ep, s);
+                return mode == 0 ? launch_pair<1, 1, 18, 0>(tmU, tmP, ep, s) : launch_pair<1, 1, 18, 1>(tmU, tmP, ep, s);
+            case TC_TF32X3:
+                if (alt) return mode == 0 ? launch_pair<1, 2, 6, 0>(tmU, tmP, ep, s) : launch_pair<1, 2, 6, 1>(tmU, tmP, ep, s);
+                return mode == 0 ? launch_pair<1, 2, 9, 0>(tmU, tmP, ep, s) : launch_pair<1, 2, 9, 1>(tmU, tmP, ep, s);
+            default:
+                return fail(TC_ERR_INVALID_ARG, "cgemm_tc: precision %d has no tensor-core form", precision);
+        }
+    }
     switch (precision) {
         case TC_BF16X3:
             if (alt) return mode == 0 ? launch<0, 3, 3, 0>(tmU, tmP, ep, s) : launch<0, 3, 3, 1>(tmU, tmP, ep, s);

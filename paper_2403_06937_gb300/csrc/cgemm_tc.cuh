@@ -37,6 +37,10 @@ struct CgemmEpi {
 tc_status cgemm_tc(int precision, int mode, const CUtensorMap& tmU, const CUtensorMap& tmP, const CgemmEpi& ep,
                    cudaStream_t s, int stages = 0);
 int cgemm_default_stages(int precision);
+// True when a launch of `tiles` tiles a side (and the range lo, hi of
+// CgemmEpi) runs as CTA pairs on the 2-SM MMA: an even tile count, whole row
+// pairs in a Hermitian row band, and TC_GEMM_PAIRS not 0 in the environment.
+bool cgemm_use_pairs(int tiles, int mode, int lo, int hi);
 int cgemm_alt_stages(int precision);
 
 // Test facility: the next `count` launches withhold their first stage (so the

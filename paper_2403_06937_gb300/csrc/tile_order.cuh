@@ -74,23 +74,55 @@ TC_HD inline void tile_of(int mode, int T, int G, int b, int& I, int& J) {
     tile_of_range(mode, T, G, 0, T, b, I, J);
 }
 
-// CTA pairs sharing the P panel: pair q covers tiles (2i, J) and
-// (2i + 1, J), rank r taking I = 2i + r; mode 0 all T columns of each row
-// pair (T even), mode 1 the columns J <= 2i + 1 (the tile (2i, 2i + 1) lies
-// above the diagonal: computed, then overwritten by the mirror).
-TC_HD inline void pair_tile_rows(int mode, int T, int q, int rank, int& I, int& J) {
+// CTA pairs of two row tiles sharing the column tile (the 2-SM MMA: each CTA
+// holds its own 128 rows of U and half of the P panel): pair q covers tiles
+// (2p, J) and (2p + 1, J), rank r taking I = 2p + r.  Row pairs go in groups
+// of G, column by column inside a group, so the pairs that run at the same
+// time read few U and few P panels (L2 reuse).  T even.
+//  mode 0: the columns [lo, hi) of every row pair (T (hi - lo) / 2 pairs);
+//  mode 1: the row pairs of the tile rows [lo, hi) (lo, hi even), each with
+//  its columns J <= 2p + 1 (sum over those p of 2p + 2 pairs; the tile
+//  (2p, 2p + 1) lies above the diagonal: computed, and overwritten or
+//  skipped by the caller).
+TC_HD inline void pair_tile_rows_range(int mode, int T, int G, int lo, int hi, int q, int rank, int& I, int& J) {
+    const int TP = T / 2;
+    if (G < 1) G = 1;
     if (mode == 0) {
-        I = 2 * (q / T) + rank;
-        J = q % T;
+        const int C = hi - lo;
+        const int per_group = G * C;
+        const int g = q / per_group;
+        const int rows = tile_min(G, TP - g * G);
+        const int in = q % per_group;
+        I = 2 * (g * G + in % rows) + rank;
+        J = lo + in / rows;
         return;
     }
-    int i = 0, base = 0;
-    while (base + 2 * i + 2 <= q) {
-        base += 2 * i + 2;
-        i++;
+    const int P1 = hi / 2;
+    for (int p0 = lo / 2; p0 < P1; p0 += G) {
+        const int last = p0 + tile_min(G, P1 - p0) - 1;
+        for (int j = 0; j <= 2 * last + 1; j++) {
+            const int first = p0 > j / 2 ? p0 : j / 2;
+            const int c = last - first + 1;
+            if (q < c) {
+                I = 2 * (first + q) + rank;
+                J = j;
+                return;
+            }
+            q -= c;
+        }
     }
-    I = 2 * i + rank;
-    J = q - base;
+    I = J = 0;   // not reached for q below the launch's pair count
+}
+
+TC_HD inline void pair_tile_rows(int mode, int T, int G, int q, int rank, int& I, int& J) {
+    pair_tile_rows_range(mode, T, G, 0, T, q, rank, I, J);
+}
+
+// Pairs of a launch over the range [lo, hi) (as pair_tile_rows_range).
+TC_HD inline long pair_count(int mode, int T, int lo, int hi) {
+    if (mode == 0) return (long)(T / 2) * (hi - lo);
+    const long p0 = lo / 2, p1 = hi / 2;
+    return p1 * (p1 + 1) - p0 * (p0 + 1);
 }
 
 }  // namespace cg

@@ -37,9 +37,12 @@ def _setup(tc, n):
 
 
 @pytest.mark.parametrize("precision", ["bf16x3", "tf32x3"])
-def test_injected_timeout_is_reported_and_context_survives(tc, precision):
+@pytest.mark.parametrize("n", [7, 8])
+def test_injected_timeout_is_reported_and_context_survives(tc, precision, n):
+    """n = 7: one tile, a single CTA; n = 8: 2 x 2 tiles, CTA pairs on the
+    2-SM MMA (both CTAs of each pair withhold their first stage, the even
+    CTA's MMA thread gives up, the abort reaches the odd CTA)."""
     from paper_2403_06937_gb300 import _abi
-    n = 7
     p, U, r0 = _setup(tc, n)
     _abi.call("tc_fault_inject", 1, 1, 0.05)          # next launch: first stage withheld, 50 ms waits
     tc.evolve(U, r0, n, 1, precision, params=p)

@@ -293,3 +293,38 @@ def test_n15_split_bf16_against_oracle(tc, oracle):
     e_rho = float(np.max(np.abs(got - psi[ii] * psi[jj].conj())))
     print("n=15, %d steps, bf16x3: observables %.2e, rho sampled %.2e" % (steps, e_obs, e_rho))
     assert e_obs < 1e-5 and e_rho < 1e-5
+
+
+def test_cta_pairs_give_the_same_bits_as_single_ctas(tc, tmp_path):
+    """The 2-SM MMA arrangement (CTA pairs of two row tiles, each CTA loading
+    its own U rows and half of every B part) against single CTAs
+    (TC_GEMM_PAIRS=0), every split form: each tile's MMAs take the same
+    operands in the same order, so every output bit is the same.  n = 8, 10,
+    12 (2, 8 and 32 tiles a side), three steps, mixed states."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = {}
+    for mode in ("0", "1"):
+        path = str(tmp_path / ("tc_pairs_%s.npz" % mode))
+        script = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, %r)
+import paper_2403_06937_gb300 as tc, workloads as W
+res = {}
+for prec in ('bf16x3', 'tf32x3', 'tf32'):
+    for n in (8, 10, 12):
+        p = tc.Params(n, list(map(float, W.draw_couplings(n, 11) * 5)), 1.01, 1.0)
+        U = tc.expm_model(p, 0.1)
+        rho0, _, _ = W.random_mixed_state(n, 2, 40 + n)
+        r, o = tc.evolve(U, torch.from_numpy(rho0).cuda(), n, 3, prec, params=p)
+        tc.sync_status()
+        res['rho_%%s_%%d' %% (prec, n)] = r.cpu().numpy()
+        res['obs_%%s_%%d' %% (prec, n)] = o.cpu().numpy()
+np.savez(%r, **res)
+""" % (root, path)
+        subprocess.run([sys.executable, "-c", script], env=dict(os.environ, TC_GEMM_PAIRS=mode), check=True)
+        out[mode] = np.load(path)
+    for key in out["0"].files:
+        assert np.array_equal(out["0"][key], out["1"][key]), key

@@ -273,3 +273,34 @@ np.save(%r, out.cpu().numpy())
         print("n=%d: error / bound %.3f (6-bit digits), %.3f (default)" % (n, r6, rw))
         assert r6 < 1.0 and rw < 1.0
         assert not np.array_equal(six, wide)
+
+
+def test_cta_pairs_give_the_same_bits_as_single_ctas(tc, tmp_path):
+    """The 2-SM MMA arrangement (CTA pairs of two row tiles, each CTA loading
+    its own U rows and half of the P panel) against single CTAs
+    (TC_OZ_PAIRS=0): the integer slice sums are the same, so every output
+    bit is.  n = 8, 10, 12 (2, 8 and 32 tiles a side), three steps each,
+    mixed states, both products of the step."""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = {}
+    for mode in ("0", "1"):
+        path = str(tmp_path / ("pairs_%s.npz" % mode))
+        script = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, %r)
+import paper_2403_06937_gb300 as tc, workloads as W
+res = {}
+for n in (8, 10, 12):
+    p = tc.Params(n, list(map(float, W.draw_couplings(n, 11) * 5)), 1.01, 1.0)
+    U = tc.expm_model(p, 0.1)
+    rho0, _, _ = W.random_mixed_state(n, 2, 40 + n)
+    r, o = tc.evolve(U, torch.from_numpy(rho0).cuda(), n, 3, 'ozaki', params=p)
+    tc.sync_status()
+    res['rho%%d' %% n] = r.cpu().numpy()
+    res['obs%%d' %% n] = o.cpu().numpy()
+np.savez(%r, **res)
+""" % (root, path)
+        subprocess.run([sys.executable, "-c", script], env=dict(os.environ, TC_OZ_PAIRS=mode), check=True)
+        out[mode] = np.load(path)
+    for key in out["0"].files:
+        assert np.array_equal(out["0"][key], out["1"][key]), key

@@ -13,7 +13,9 @@
 
 #include "tile_order.cuh"
 
+using tc::cg::pair_count;
 using tc::cg::pair_tile_rows;
+using tc::cg::pair_tile_rows_range;
 using tc::cg::tile_of;
 using tc::cg::tile_of_range;
 
@@ -65,32 +67,54 @@ static void check_single(int T, int G) {
     }
 }
 
-static void check_pairs(int T) {
+static void check_pairs(int T, int G) {
     for (int mode = 0; mode < 2; mode++) {
-        // sharing P: mode 0 T * T / 2 pairs, mode 1 sum over row pairs i of (2 i + 2)
+        // the whole launch: mode 0 T * T / 2 pairs, mode 1 sum over row pairs i of (2 i + 2)
         long pairs = 0;
         if (mode == 0) {
             pairs = (long)T * (T / 2);
         } else {
             for (int i = 0; i < T / 2; i++) pairs += 2 * i + 2;
         }
+        if (pair_count(mode, T, 0, T) != pairs) fail("pair_count of the whole launch", T, G, mode, 0, 0);
         std::set<std::pair<int, int>> seen;
         for (long q = 0; q < pairs; q++) {
             int I0, J0, I1, J1;
-            pair_tile_rows(mode, T, (int)q, 0, I0, J0);
-            pair_tile_rows(mode, T, (int)q, 1, I1, J1);
-            if (J0 != J1) fail("pair_tile_rows: the pair spans two column tiles", T, 0, mode, J0, J1);
+            pair_tile_rows(mode, T, G, (int)q, 0, I0, J0);
+            pair_tile_rows(mode, T, G, (int)q, 1, I1, J1);
+            if (J0 != J1) fail("pair_tile_rows: the pair spans two column tiles", T, G, mode, J0, J1);
+            if (I1 != I0 + 1 || I0 % 2 != 0) fail("pair_tile_rows: not an even/odd row pair", T, G, mode, I0, I1);
             for (auto t : {std::make_pair(I0, J0), std::make_pair(I1, J1)}) {
                 if (t.first < 0 || t.first >= T || t.second < 0 || t.second >= T)
-                    fail("pair_tile_rows out of range", T, 0, mode, t.first, t.second);
-                if (!seen.insert(t).second) fail("pair_tile_rows visits twice", T, 0, mode, t.first, t.second);
+                    fail("pair_tile_rows out of range", T, G, mode, t.first, t.second);
+                if (!seen.insert(t).second) fail("pair_tile_rows visits twice", T, G, mode, t.first, t.second);
             }
         }
         for (auto t : owned(mode, T))
-            if (!seen.count(t)) fail("pair_tile_rows misses a tile", T, 0, mode, t.first, t.second);
+            if (!seen.count(t)) fail("pair_tile_rows misses a tile", T, G, mode, t.first, t.second);
         for (auto t : seen)
             if (mode == 1 && t.second > t.first && !(t.second == t.first + 1 && t.first % 2 == 0))
-                fail("pair_tile_rows extra tile", T, 0, mode, t.first, t.second);
+                fail("pair_tile_rows extra tile", T, G, mode, t.first, t.second);
+        // split launches over ranges (mode 0: column bands; mode 1: even row bands) cover the same tiles
+        for (int C = 2; C <= 4; C *= 2) {
+            if (T % (2 * C) != 0) continue;
+            std::set<std::pair<int, int>> split;
+            for (int c = 0; c < C; c++) {
+                const int lo = c * T / C, hi = (c + 1) * T / C;
+                const long np = pair_count(mode, T, lo, hi);
+                for (long q = 0; q < np; q++)
+                    for (int r = 0; r < 2; r++) {
+                        int I, J;
+                        pair_tile_rows_range(mode, T, G, lo, hi, (int)q, r, I, J);
+                        const bool in = mode == 0 ? (J >= lo && J < hi) : (I >= lo && I < hi);
+                        if (!in || I < 0 || I >= T || J < 0 || J >= T)
+                            fail("pair_tile_rows_range outside its range", T, G, mode, I, J);
+                        if (!split.insert({I, J}).second)
+                            fail("pair_tile_rows_range visits twice", T, G, mode, I, J);
+                    }
+            }
+            if (split != seen) fail("split pair launches differ from the whole launch", T, G, mode, C, 0);
+        }
     }
 }
 
@@ -100,7 +124,8 @@ int main() {
     for (int T : Ts)
         for (int G : Gs) check_single(T, G);
     for (int T : Ts)
-        if (T % 2 == 0) check_pairs(T);
+        if (T % 2 == 0)
+            for (int G : Gs) check_pairs(T, G);
     if (failures) {
         std::printf("%d failures\n", failures);
         return 1;
