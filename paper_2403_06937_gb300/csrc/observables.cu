@@ -58,6 +58,29 @@ __global__ void obs_partial_kernel(Rho<L> rho, Model m, int has_model, int n, do
         // four independent loads per lane in flight, fixed summation order
         double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
         unsigned c = lane;
+        if (L == kRhoPlanarF32) {
+            // FP32 planes: the squares of a chunk of 16 entries (4 per
+            // accumulator) are summed in FP32 and only the chunk sums are
+            // carried in FP64; per entry FP64 work (GB300's scarce FP64
+            // issue) drops 40-fold, the sum's relative error stays within
+            // ~17 FP32 ulps of a chunk's sum
+            const float* ra = static_cast<const float*>(rho.a) + row;
+            const float* rb = static_cast<const float*>(rho.b) + row;
+            for (; c + 480 < N; c += 512) {
+                float q0 = 0.f, q1 = 0.f, q2 = 0.f, q3 = 0.f;
+#pragma unroll
+                for (int h = 0; h < 4; h++) {
+                    const unsigned b = c + 128 * h;
+                    const float x0 = ra[b], x1 = ra[b + 32], x2 = ra[b + 64], x3 = ra[b + 96];
+                    const float y0 = rb[b], y1 = rb[b + 32], y2 = rb[b + 64], y3 = rb[b + 96];
+                    q0 = fmaf(x0, x0, fmaf(y0, y0, q0));
+                    q1 = fmaf(x1, x1, fmaf(y1, y1, q1));
+                    q2 = fmaf(x2, x2, fmaf(y2, y2, q2));
+                    q3 = fmaf(x3, x3, fmaf(y3, y3, q3));
+                }
+                p0 += (double)((q0 + q1) + (q2 + q3));
+            }
+        }
         for (; c + 96 < N; c += 128) {
             const double x0 = rho.re(row + c), x1 = rho.re(row + c + 32), x2 = rho.re(row + c + 64),
                          x3 = rho.re(row + c + 96);
