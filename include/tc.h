@@ -364,16 +364,20 @@ TC_API tc_status tc_evolve_backward(const tc_params* params, double dt, int step
                                     void* work, size_t work_bytes, void* stream);
 
 /* tc_evolve_host -- tc_evolve with the density matrix and the observables in
- * HOST memory: copies rho_host to the device, runs `steps` steps on the GPU,
- * copies rho and the observable rows back, and synchronises `stream` before
- * returning (the results are in host memory on return).  Page-locked host
- * buffers give the full copy bandwidth; pageable ones work but copy slower.
- * In the tensor-core forms with N >= 2048 the copies overlap the products:
- * rho moves in and out in 2 or 4 row blocks on an internal copy stream,
- * the first product of step 1 runs by column blocks as their rows arrive,
- * and the second product of the last step runs bottom-up by row blocks,
- * each finished block converted and copied out while the rows above are
- * computed; the results are the same bits as tc_evolve's.
+ * HOST memory: brings rho_host to the device, runs `steps` steps on the GPU,
+ * writes rho and the observable rows back, and synchronises `stream` before
+ * returning (the results are in host memory on return).  A page-locked
+ * (pinned) rho_host is read and written by the GPU's SMs directly through
+ * its device mapping, at full link rate also when the host is busy
+ * (copy-engine transfers of host memory, reads above all, were measured to
+ * slow down many-fold after heavy host CPU or memory activity); a pageable
+ * one is copied by the copy engine through a device staging buffer.  In the tensor-core forms
+ * with N >= 2048 the transfers overlap the products: rho moves in and out
+ * in 2 or 4 row blocks on an internal stream, the first product of step 1
+ * runs by column blocks as their rows arrive, and the second product of the
+ * last step runs bottom-up by row blocks, each finished block converted and
+ * written out while the rows above are computed; the results are the same
+ * bits as tc_evolve's.
  *  U        : device, N*N c128 (as tc_evolve), 16-byte aligned.
  *  rho_host : host, N*N c128, in/out.
  *  obs_host : host, (steps + 1) * TC_OBS_STRIDE(n) doubles, or NULL.

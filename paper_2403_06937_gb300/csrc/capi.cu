@@ -460,10 +460,19 @@ TC_API tc_status tc_evolve_host(const void* U, void* rho_host, int n, int steps,
     double* od = obs_host ? obs_dev : nullptr;
     const double* Ud = static_cast<const double*>(U);
     if (precision == TC_FP64 || precision == TC_FP64_OZAKI) {
-        TC_CUDA(cudaMemcpyAsync(rho_dev, rho_host, 16 * N * N, cudaMemcpyHostToDevice, s));
+        // page-locked rho_host: the SMs copy it (copy-engine reads of host memory slow down under host load)
+        const void* mapped = nullptr;
+        TC_TRY(host_mapping(rho_host, &mapped));
+        if (mapped)
+            TC_TRY(copy_by_sms(rho_dev, mapped, 16 * N * N, s));
+        else
+            TC_CUDA(cudaMemcpyAsync(rho_dev, rho_host, 16 * N * N, cudaMemcpyHostToDevice, s));
         TC_TRY(precision == TC_FP64 ? evolve_f64(Ud, rho_dev, n, steps, renorm_every, mp, od, ar, s)
                                     : evolve_oz(Ud, rho_dev, n, steps, renorm_every, mp, od, ar, s));
-        TC_CUDA(cudaMemcpyAsync(rho_host, rho_dev, 16 * N * N, cudaMemcpyDeviceToHost, s));
+        if (mapped)
+            TC_TRY(copy_by_sms(const_cast<void*>(mapped), rho_dev, 16 * N * N, s));
+        else
+            TC_CUDA(cudaMemcpyAsync(rho_host, rho_dev, 16 * N * N, cudaMemcpyDeviceToHost, s));
     } else {
         // copies overlapped with the first and last products (row blocks on a copy stream)
         TC_TRY(evolve_lowp_host(Ud, static_cast<double*>(rho_host), rho_dev, n, steps, precision, renorm_every, mp,

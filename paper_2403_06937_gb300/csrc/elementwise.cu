@@ -23,6 +23,12 @@ unsigned grid_for(size_t work, int per_block = 256) {
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < (count);      \
          i += (size_t)gridDim.x * blockDim.x)
 
+// 16-byte grid-stride copy: the SMs read or write page-locked host memory
+// directly through its device mapping
+__global__ void copy16_kernel(const uint4* __restrict__ src, uint4* __restrict__ dst, size_t count) {
+    GRID_STRIDE(i, count) { dst[i] = src[i]; }
+}
+
 __global__ void split_c128_kernel(const double2* src, double* re, double* im, size_t count) {
     GRID_STRIDE(i, count) {
         double2 v = src[i];
@@ -129,6 +135,29 @@ __global__ void max_sum_kernel(const double* rows, const double* diag, unsigned 
 }
 
 }  // namespace
+
+tc_status host_mapping(const void* host, const void** dev) {
+    *dev = nullptr;
+    cudaPointerAttributes a{};
+    cudaError_t e = cudaPointerGetAttributes(&a, host);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();   // pageable memory on older drivers reports an error: not mapped
+        return TC_OK;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return TC_OK;
+    if (reinterpret_cast<uintptr_t>(a.devicePointer) & 15u) return TC_OK;
+    *dev = a.devicePointer;
+    return TC_OK;
+}
+
+tc_status copy_by_sms(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+    if (((reinterpret_cast<uintptr_t>(dst) | reinterpret_cast<uintptr_t>(src)) & 15u) || (bytes & 15u))
+        return fail(TC_ERR_INVALID_ARG, "copy_by_sms: 16-byte aligned addresses and size required");
+    const size_t count = bytes / 16;
+    copy16_kernel<<<grid_for(count), 256, 0, s>>>(static_cast<const uint4*>(src), static_cast<uint4*>(dst), count);
+    TC_LAUNCH_CHECK();
+    return TC_OK;
+}
 
 tc_status launch_split_c128(const double* src, double* re, double* im, size_t count, cudaStream_t s) {
     split_c128_kernel<<<grid_for(count), 256, 0, s>>>(reinterpret_cast<const double2*>(src), re, im, count);

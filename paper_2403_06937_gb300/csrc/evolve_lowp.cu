@@ -39,26 +39,35 @@ unsigned grid_for(size_t work) {
     return (unsigned)(want < cap ? (want ? want : 1) : cap);
 }
 
-// parts of a double (U): the split is taken in FP64
+// parts of a double (V): v is first held as an FP32 pair hi + lo (hi = v
+// rounded, lo = the rest rounded; |v - hi - lo| <= 2^-48 |v|), then split in
+// FP32 arithmetic: BF16 parts b0 = RN(hi), b1 = RN((hi - b0) + lo),
+// b2 = RN(r - b1) (hi - b0 and r - b1 are exact), TF32 parts likewise.  The
+// parts represent v to about 2^-26 |v|, as an FP64 split would (~2^-27), with
+// three FP64 operations per value instead of two per part.
 template <int KIND, int S>
 __device__ __forceinline__ void split_f64(double v, void* base, size_t plane, size_t idx, int part) {
+    const float hi = (float)v;
+    const float lo = (float)(v - (double)hi);
     if constexpr (KIND == 0) {
         __nv_bfloat16* p = static_cast<__nv_bfloat16*>(base);
-        double r = v;
+        float r = hi;
 #pragma unroll
         for (int s = 0; s < S; s++) {
-            __nv_bfloat16 b = __double2bfloat16(r);
+            __nv_bfloat16 b = __float2bfloat16_rn(r);
             p[(size_t)(part * S + s) * plane + idx] = b;
-            r -= (double)__bfloat162float(b);
+            r -= __bfloat162float(b);
+            if (s == 0) r += lo;
         }
     } else {
         float* p = static_cast<float*>(base);
-        double r = v;
+        float r = hi;
 #pragma unroll
         for (int s = 0; s < S; s++) {
-            float t = tf32_rna((float)r);
+            float t = tf32_rna(r);
             p[(size_t)(part * S + s) * plane + idx] = t;
-            r -= (double)t;
+            r -= t;
+            if (s == 0) r += lo;
         }
     }
 }
@@ -89,41 +98,55 @@ __global__ void unit_phase_kernel(const double2* U, int N, double* out) {
     }
 }
 
-// V = U conj(c) - I (zero in the padding), split into operand parts in FP64
+// V = U conj(c) - I (zero in the padding), formed in FP64 and split into
+// operand parts; blocks take rows, threads columns (no index division)
 template <int KIND, int S>
 __global__ void prep_u_kernel(const double2* U, int N, int Np, const double* phase, void* parts) {
     const size_t plane = (size_t)Np * Np;
     const double cr = phase[0], ci = -phase[1];
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < plane; e += (size_t)gridDim.x * blockDim.x) {
-        const size_t i = e / Np, j = e % Np;
-        double vr = 0.0, vi = 0.0;
-        if (i < (size_t)N && j < (size_t)N) {
-            const double2 u = U[i * N + j];
-            vr = u.x * cr - u.y * ci;
-            vi = u.x * ci + u.y * cr;
-            if (i == j) vr -= 1.0;
+    for (int i = blockIdx.x; i < Np; i += gridDim.x) {
+        for (int j = threadIdx.x; j < Np; j += blockDim.x) {
+            const size_t e = (size_t)i * Np + j;
+            double vr = 0.0, vi = 0.0;
+            if (i < N && j < N) {
+                const double2 u = U[(size_t)i * N + j];
+                vr = u.x * cr - u.y * ci;
+                vi = u.x * ci + u.y * cr;
+                if (i == j) vr -= 1.0;
+            }
+            split_f64<KIND, S>(vr, parts, plane, e, 0);
+            split_f64<KIND, S>(vi, parts, plane, e, 1);
         }
-        split_f64<KIND, S>(vr, parts, plane, e, 0);
-        split_f64<KIND, S>(vi, parts, plane, e, 1);
     }
 }
 
-// rows [r0, r1) of the padded plane
+// rows [r0, r1) of the padded plane; blocks take rows, threads columns, four
+// loads in flight per thread (rho may be page-locked host memory read through
+// its device mapping)
 template <int KIND, int S>
 __global__ void prep_rho_kernel(const double2* rho, int N, int Np, int r0, int r1, float* Rr, float* Ri,
                                 void* parts) {
     const size_t plane = (size_t)Np * Np;
-    const size_t first = (size_t)r0 * Np, count = (size_t)(r1 - r0) * Np;
-    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += (size_t)gridDim.x * blockDim.x) {
-        const size_t e = first + k;
-        const size_t i = e / Np, j = e % Np;
-        double2 v = make_double2(0.0, 0.0);
-        if (i < (size_t)N && j < (size_t)N) v = rho[i * N + j];
-        const float fr = (float)v.x, fi = (float)v.y;
-        Rr[e] = fr;
-        Ri[e] = fi;
-        split_f32<KIND, S>(fr, parts, plane, e, 0);
-        split_f32<KIND, S>(fi, parts, plane, e, 1);
+    for (int i = r0 + blockIdx.x; i < r1; i += gridDim.x) {
+        for (int j0 = threadIdx.x; j0 < Np; j0 += 4 * blockDim.x) {
+            double2 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int j = j0 + u * blockDim.x;
+                v[u] = (i < N && j < N) ? rho[(size_t)i * N + j] : make_double2(0.0, 0.0);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int j = j0 + u * blockDim.x;
+                if (j >= Np) break;
+                const size_t e = (size_t)i * Np + j;
+                const float fr = (float)v[u].x, fi = (float)v[u].y;
+                Rr[e] = fr;
+                Ri[e] = fi;
+                split_f32<KIND, S>(fr, parts, plane, e, 0);
+                split_f32<KIND, S>(fi, parts, plane, e, 1);
+            }
+        }
     }
 }
 
@@ -161,14 +184,12 @@ __global__ void trace_f32_kernel(const float* Rr, int N, int Np, double* out) {
     if (threadIdx.x == 0) out[0] = s[0];
 }
 
-// rows [r0, r1) of the N x N result
+// rows [r0, r1) of the N x N result; blocks take rows, threads columns (rho
+// may be page-locked host memory written through its device mapping)
 __global__ void finish_kernel(const float* Rr, const float* Ri, int N, int Np, int r0, int r1, double2* rho) {
-    const size_t first = (size_t)r0 * N, count = (size_t)(r1 - r0) * N;
-    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += (size_t)gridDim.x * blockDim.x) {
-        const size_t e = first + k;
-        const size_t i = e / N, j = e % N;
-        rho[e] = make_double2((double)Rr[i * Np + j], (double)Ri[i * Np + j]);
-    }
+    for (int i = r0 + blockIdx.x; i < r1; i += gridDim.x)
+        for (int j = threadIdx.x; j < N; j += blockDim.x)
+            rho[(size_t)i * N + j] = make_double2((double)Rr[(size_t)i * Np + j], (double)Ri[(size_t)i * Np + j]);
 }
 
 }  // namespace
@@ -183,15 +204,25 @@ tc_status run_prep_u(const double* U, LowpBufs& b, cudaStream_t s) {
     double* phase = b.scratch;   // consumed by prep_u before any other use of scratch
     unit_phase_kernel<<<1, 1024, 0, s>>>(reinterpret_cast<const double2*>(U), b.N, phase);
     TC_LAUNCH_CHECK();
-    prep_u_kernel<KIND, S><<<grid_for(plane), 256, 0, s>>>(reinterpret_cast<const double2*>(U), b.N, b.Np, phase,
+    const unsigned rows_grid = grid_for(plane) < (unsigned)b.Np ? grid_for(plane) : (unsigned)b.Np;
+    prep_u_kernel<KIND, S><<<rows_grid, 256, 0, s>>>(reinterpret_cast<const double2*>(U), b.N, b.Np, phase,
                                                             b.Uparts);
     TC_LAUNCH_CHECK();
     return TC_OK;
 }
 
+// CTAs over rows: at most grid_for's cap, and at most `cap` when given (the
+// host-memory transfers run beside the products, on a few CTAs per SM)
+unsigned rows_grid(int rows, size_t work, unsigned cap) {
+    unsigned g = grid_for(work);
+    if (g > (unsigned)rows) g = (unsigned)rows;
+    if (cap && g > cap) g = cap;
+    return g ? g : 1u;
+}
+
 template <int KIND, int S>
-tc_status run_prep_rho(const double* rho, LowpBufs& b, int r0, int r1, cudaStream_t s) {
-    prep_rho_kernel<KIND, S><<<grid_for((size_t)(r1 - r0) * b.Np), 256, 0, s>>>(
+tc_status run_prep_rho(const double* rho, LowpBufs& b, int r0, int r1, cudaStream_t s, unsigned cap) {
+    prep_rho_kernel<KIND, S><<<rows_grid(r1 - r0, (size_t)(r1 - r0) * b.Np, cap), 256, 0, s>>>(
         reinterpret_cast<const double2*>(rho), b.N, b.Np, r0, r1, b.Rr, b.Ri, b.Rparts);
     TC_LAUNCH_CHECK();
     return TC_OK;
@@ -200,7 +231,7 @@ tc_status run_prep_rho(const double* rho, LowpBufs& b, int r0, int r1, cudaStrea
 template <int KIND, int S>
 tc_status run_prep(const double* U, const double* rho, LowpBufs& b, cudaStream_t s) {
     TC_TRY((run_prep_u<KIND, S>(U, b, s)));
-    return run_prep_rho<KIND, S>(rho, b, 0, b.Np, s);
+    return run_prep_rho<KIND, S>(rho, b, 0, b.Np, s, 0u);
 }
 
 template <int KIND, int S>
@@ -242,21 +273,22 @@ tc_status lowp_prep_u(int precision, const double* U, LowpBufs& b, cudaStream_t 
     return fail(TC_ERR_INVALID_ARG, "precision");
 }
 
-tc_status lowp_prep_rho(int precision, const double* rho, LowpBufs& b, int r0, int r1, cudaStream_t s) {
+tc_status lowp_prep_rho(int precision, const double* rho, LowpBufs& b, int r0, int r1, cudaStream_t s,
+                        unsigned cap) {
     if (r0 < 0 || r0 >= r1 || r1 > b.Np) return fail(TC_ERR_INVALID_ARG, "prep: row range");
     switch (precision) {
-        case TC_BF16X3: return run_prep_rho<0, 3>(rho, b, r0, r1, s);
-        case TC_TF32: return run_prep_rho<1, 1>(rho, b, r0, r1, s);
-        case TC_TF32X3: return run_prep_rho<1, 2>(rho, b, r0, r1, s);
+        case TC_BF16X3: return run_prep_rho<0, 3>(rho, b, r0, r1, s, cap);
+        case TC_TF32: return run_prep_rho<1, 1>(rho, b, r0, r1, s, cap);
+        case TC_TF32X3: return run_prep_rho<1, 2>(rho, b, r0, r1, s, cap);
     }
     return fail(TC_ERR_INVALID_ARG, "precision");
 }
 
-tc_status lowp_finish(const LowpBufs& b, double* rho, cudaStream_t s, int r0, int r1) {
+tc_status lowp_finish(const LowpBufs& b, double* rho, cudaStream_t s, int r0, int r1, unsigned cap) {
     if (r1 < 0) r1 = b.N;
     if (r0 < 0 || r0 >= r1 || r1 > b.N) return fail(TC_ERR_INVALID_ARG, "finish: row range");
-    finish_kernel<<<grid_for((size_t)(r1 - r0) * b.N), 256, 0, s>>>(b.Rr, b.Ri, b.N, b.Np, r0, r1,
-                                                                    reinterpret_cast<double2*>(rho));
+    finish_kernel<<<rows_grid(r1 - r0, (size_t)(r1 - r0) * b.N, cap), 256, 0, s>>>(b.Rr, b.Ri, b.N, b.Np, r0, r1,
+                                                                                   reinterpret_cast<double2*>(rho));
     TC_LAUNCH_CHECK();
     return TC_OK;
 }
@@ -435,10 +467,24 @@ tc_status evolve_lowp_host_blocks(const double* U, double* rho_host, double* rho
     const size_t N = (size_t)1 << n;
     const size_t bytes = 16 * N * N;
     const int C = steps >= 1 ? lowp_host_chunks(n, precision) : 1;
+    // A page-locked rho_host is read and written by the SMs through its device
+    // mapping (copy-engine transfers of host memory, reads above all, slow down
+    // many-fold after heavy host CPU or memory activity; SM accesses keep
+    // their rate); pageable or misaligned buffers go through the copy engine
+    // and the device staging.
+    const void* mapped_v = nullptr;
+    TC_TRY(host_mapping(rho_host, &mapped_v));
+    double* mapped = const_cast<double*>(static_cast<const double*>(mapped_v));
     if (C == 1) {
-        TC_CUDA(cudaMemcpyAsync(rho_dev, rho_host, bytes, cudaMemcpyHostToDevice, s));
+        if (mapped)
+            TC_TRY(copy_by_sms(rho_dev, mapped, bytes, s));
+        else
+            TC_CUDA(cudaMemcpyAsync(rho_dev, rho_host, bytes, cudaMemcpyHostToDevice, s));
         TC_TRY(evolve_lowp(U, rho_dev, n, steps, precision, renorm_every, m, obs, ar, s));
-        TC_CUDA(cudaMemcpyAsync(rho_host, rho_dev, bytes, cudaMemcpyDeviceToHost, s));
+        if (mapped)
+            TC_TRY(copy_by_sms(mapped, rho_dev, bytes, s));
+        else
+            TC_CUDA(cudaMemcpyAsync(rho_host, rho_dev, bytes, cudaMemcpyDeviceToHost, s));
         return TC_OK;
     }
     LowpBufs b{};
@@ -451,38 +497,77 @@ tc_status evolve_lowp_host_blocks(const double* U, double* rho_host, double* rho
     const size_t chunk = 16 * R * N;         // bytes per chunk
     const int stride = TC_OBS_STRIDE(n);
     TC_TRY(lane.init(2 * C + 2));
-    cudaEvent_t* h2d = lane.ev;              // [C]
-    cudaEvent_t* fin = lane.ev + C;          // [C]
+    cudaEvent_t* in = lane.ev;               // [C] rows of chunk c are in the FP32 planes (or the staging)
+    cudaEvent_t* fin = lane.ev + C;          // [C] rows of chunk c of rho' are final
     cudaEvent_t start = lane.ev[2 * C], done = lane.ev[2 * C + 1];
     auto dev_rows = [&](size_t c) { return reinterpret_cast<char*>(rho_dev) + c * chunk; };
     auto host_rows = [&](size_t c) { return reinterpret_cast<char*>(rho_host) + c * chunk; };
+    auto rows_lo = [&](int c) { return (int)(c * R); };
+    auto rows_hi = [&](int c) { return (int)((c + 1) * R); };
+    // the SM reads of host rows run beside the first products: two CTAs per
+    // SM keep the link busy without crowding the GEMM's CTAs
+    int dev = 0, sms = 148;
+    TC_CUDA(cudaGetDevice(&dev));
+    TC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const unsigned cap = 2u * (unsigned)sms;
+    const unsigned out_cap = (unsigned)sms / 2u > 0u ? (unsigned)sms / 2u : 1u;
 
     char tag[16];
     auto mark = [&](const char* what, int c, cudaStream_t on) {
         std::snprintf(tag, sizeof(tag), c >= 0 ? "%s%d" : "%s", what, c);
         phase_mark(tag, on);
     };
-    // rho in by row blocks on the copy stream (after earlier work on s that may use the staging)
+    // rho in by row blocks on the copy stream (after earlier work on s that may use the planes)
     mark("start", -1, s);
     TC_CUDA(cudaEventRecord(start, s));
     TC_CUDA(cudaStreamWaitEvent(lane.cs, start, 0));
-    for (int c = 0; c < C; c++) {
-        TC_CUDA(cudaMemcpyAsync(dev_rows(c), host_rows(c), chunk, cudaMemcpyHostToDevice, lane.cs));
-        TC_CUDA(cudaEventRecord(h2d[c], lane.cs));
+    auto in_rows = [&](int c) -> tc_status {
+        if (mapped)
+            TC_TRY(lowp_prep_rho(precision, mapped, b, rows_lo(c), rows_hi(c), lane.cs, cap));
+        else
+            TC_CUDA(cudaMemcpyAsync(dev_rows(c), host_rows(c), chunk, cudaMemcpyHostToDevice, lane.cs));
+        TC_CUDA(cudaEventRecord(in[c], lane.cs));
         mark("h2d", c, lane.cs);
-    }
+        return TC_OK;
+    };
+    // all row blocks in at once, beside prep_u and the first product's column
+    // blocks (an SM read beside a GEMM runs at a fraction of the link rate, so
+    // holding the later blocks back made the column blocks wait for them)
+    for (int c = 0; c < C; c++) TC_TRY(in_rows(c));
     TC_TRY(lowp_prep_u(precision, U, b, s));
     mark("prep_u", -1, s);
     // step 1, first product by column blocks: X[:, J] needs only the rows J of rho
     for (int c = 0; c < C; c++) {
-        TC_CUDA(cudaStreamWaitEvent(s, h2d[c], 0));
-        TC_TRY(lowp_prep_rho(precision, rho_dev, b, (int)(c * R), (int)((c + 1) * R), s));
+        TC_CUDA(cudaStreamWaitEvent(s, in[c], 0));
+        if (!mapped) TC_TRY(lowp_prep_rho(precision, rho_dev, b, rows_lo(c), rows_hi(c), s));
         CgemmEpi e = sp.e1;
         e.lo = c * T / C;
         e.hi = (c + 1) * T / C;
         TC_TRY(cgemm_tc(precision, 0, sp.tmU, sp.tmR, e, s, sp.tune.tc_stages));
         mark("x", c, s);
     }
+    // rows of chunk c of rho' out (their products done on s).  A mapped host
+    // buffer is written by the finish kernel on the copy stream, on a few
+    // CTAs while products still run beside it (half a CTA per SM; SM stores to
+    // host memory on more CTAs slowed the products by a quarter); otherwise the
+    // rows are converted on s into the staging and copied by the copy engine.
+    // Copy-engine writes to host memory slow down after heavy host activity
+    // too, though less often than its reads.
+    auto out_rows = [&](int c) -> tc_status {
+        if (mapped) {
+            TC_CUDA(cudaEventRecord(fin[c], s));
+            TC_CUDA(cudaStreamWaitEvent(lane.cs, fin[c], 0));
+            // the top block goes out last, with nothing beside it: the full grid
+            TC_TRY(lowp_finish(b, mapped, lane.cs, rows_lo(c), rows_hi(c), c == 0 ? cap : out_cap));
+        } else {
+            TC_TRY(lowp_finish(b, rho_dev, s, rows_lo(c), rows_hi(c)));
+            TC_CUDA(cudaEventRecord(fin[c], s));
+            TC_CUDA(cudaStreamWaitEvent(lane.cs, fin[c], 0));
+            TC_CUDA(cudaMemcpyAsync(host_rows(c), dev_rows(c), chunk, cudaMemcpyDeviceToHost, lane.cs));
+        }
+        mark("d2h", c, lane.cs);
+        return TC_OK;
+    };
     if (obs) TC_TRY(launch_observables(kRhoPlanarF32, b.Rr, b.Ri, m, n, obs, b.scratch, s, (size_t)b.Np));
     for (int k = 1; k <= steps; k++) {
         if (k > 1) TC_TRY(cgemm_tc(precision, 0, sp.tmU, sp.tmR, sp.e1, s, sp.tune.tc_stages));
@@ -494,14 +579,8 @@ tc_status evolve_lowp_host_blocks(const double* U, double* rho_host, double* rho
                                                s, (size_t)b.Np));
             if (k < steps) continue;
             // last step renormalised: rho' is whole only now; convert and copy out by row blocks
-            for (int c = 0; c < C; c++) {
-                TC_TRY(lowp_finish(b, rho_dev, s, (int)(c * R), (int)((c + 1) * R)));
-                mark("y", c, s);
-                TC_CUDA(cudaEventRecord(fin[c], s));
-                TC_CUDA(cudaStreamWaitEvent(lane.cs, fin[c], 0));
-                TC_CUDA(cudaMemcpyAsync(host_rows(c), dev_rows(c), chunk, cudaMemcpyDeviceToHost, lane.cs));
-                mark("d2h", c, lane.cs);
-            }
+            mark("y", 0, s);
+            for (int c = 0; c < C; c++) TC_TRY(out_rows(c));
             break;
         }
         // last step, second product bottom-up by row blocks: once the tile rows >= lo are done
@@ -511,12 +590,8 @@ tc_status evolve_lowp_host_blocks(const double* U, double* rho_host, double* rho
             e.lo = c * T / C;
             e.hi = (c + 1) * T / C;
             TC_TRY(cgemm_tc(precision, 1, sp.tmU, sp.tmX, e, s, sp.tune.tc_stages));
-            TC_TRY(lowp_finish(b, rho_dev, s, (int)(c * R), (int)((c + 1) * R)));
             mark("y", c, s);
-            TC_CUDA(cudaEventRecord(fin[c], s));
-            TC_CUDA(cudaStreamWaitEvent(lane.cs, fin[c], 0));
-            TC_CUDA(cudaMemcpyAsync(host_rows(c), dev_rows(c), chunk, cudaMemcpyDeviceToHost, lane.cs));
-            mark("d2h", c, lane.cs);
+            TC_TRY(out_rows(c));
         }
         if (obs)
             TC_TRY(launch_observables(kRhoPlanarF32, b.Rr, b.Ri, m, n, obs + (size_t)k * stride, b.scratch, s,

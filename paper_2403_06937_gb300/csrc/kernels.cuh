@@ -15,6 +15,16 @@ tc_status launch_join_c128(const double* re, const double* im, double* dst, size
 tc_status launch_split_c128_f32(const double* src, float* re, float* im, size_t count, cudaStream_t s);
 tc_status launch_join_c128_f32(const float* re, const float* im, double* dst, size_t count, cudaStream_t s);
 
+// ---------------------------------------------------------------- host buffers
+// Device address of page-locked host memory at `host` (16-byte aligned), or
+// nullptr for pageable or misaligned memory.  Through it the SMs read and
+// write the host buffer directly; that path keeps its rate (~190 GB/s each
+// way on GB300) where copy-engine reads of host memory slow down many-fold
+// after heavy host CPU or memory activity.
+tc_status host_mapping(const void* host, const void** dev);
+// dst <- src (bytes, 16-byte aligned, a multiple of 16) by a kernel
+tc_status copy_by_sms(void* dst, const void* src, size_t bytes, cudaStream_t s);
+
 // ---------------------------------------------------------------- FP64 GEMM
 // C = alpha * op(A) op(B) + beta * C on planar row-major operands.
 //   A[m][k] at m*lda + k, B[k][n] at k*ldb + n, C[m][n] at m*ldc + n.

@@ -60,8 +60,10 @@ tc_status lowp_prep(int precision, const double* U, const double* rho, LowpBufs&
 tc_status lowp_renorm(int precision, LowpBufs& b, cudaStream_t s);
 // the two halves of lowp_prep: V parts; rho rows [r0, r1) of the padded planes
 tc_status lowp_prep_u(int precision, const double* U, LowpBufs& b, cudaStream_t s);
-tc_status lowp_prep_rho(int precision, const double* rho, LowpBufs& b, int r0, int r1, cudaStream_t s);
+// (cap > 0: at most `cap` CTAs)
+tc_status lowp_prep_rho(int precision, const double* rho, LowpBufs& b, int r0, int r1, cudaStream_t s,
+                        unsigned cap = 0);
 // FP32 planes -> interleaved complex128 rho (N x N), rows [r0, r1) (r1 < 0: N)
-tc_status lowp_finish(const LowpBufs& b, double* rho, cudaStream_t s, int r0 = 0, int r1 = -1);
+tc_status lowp_finish(const LowpBufs& b, double* rho, cudaStream_t s, int r0 = 0, int r1 = -1, unsigned cap = 0);
 
 }  // namespace tc
