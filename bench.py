@@ -40,10 +40,10 @@ METRIC = "evolution steps/s and complex-GEMM TFLOP/s at n=14 (FP64 vs split-BF16
 
 # DRAM bytes (read + write) per launch of the dominant kernel, keyed by
 # (precision, n): dram__bytes_read.sum + dram__bytes_write.sum averaged over
-# the launches of a one-pass ncu capture at n <= 12, scaled to n by the
-# N^3 units a launch processes.  Empty until such a capture of the current
-# kernel build exists (the line then reports null).
-NCU_TRAFFIC = {}
+# the four launches (two of each product) of a one-pass ncu capture at
+# n = 12 (1.485 GB), scaled to n = 14 by the N^3 units a launch processes;
+# null for any other key.
+NCU_TRAFFIC = {("bf16x3", 14): 1.485e9 * 64}
 
 
 def _args():
@@ -499,8 +499,8 @@ def run_ours(a, cfg):
     achieved = r["kflops"] / (r["kms"] * 1e-3) / 1e12 if r["kms"] > 0 else 0.0
     roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak if peak else None, "traffic": NCU_TRAFFIC.get((prec, n)),
-            "traffic_unit": "DRAM bytes per launch (ncu); compulsory operand bytes per launch %.2e" % (
-                _compulsory_bytes(prec, N)),
+            "traffic_unit": "DRAM bytes per launch (ncu one-pass capture at n=12, scaled by N^3); compulsory "
+                            "operand bytes per launch %.2e" % (_compulsory_bytes(prec, N)),
             "kernel": "complex GEMM (%s), %d launches timed, %.3f ms avg" % (prec, r["klaunch"],
                                                                              r["kms"] / max(r["klaunch"], 1)),
             "peak_source": peak_note,
