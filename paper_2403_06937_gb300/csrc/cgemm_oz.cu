@@ -355,14 +355,30 @@ constexpr int kSmem = kStages * kStage + 1024 /*align*/ + 256 /*barriers*/;
 // one, whose copies complete on the even CTA's barriers, waits a fixed
 // 1 ms), the MMA thread waits for its MMAs, and both meet at a cluster
 // barrier before TMEM is freed and either CTA exits.
-constexpr int kPairStages = 16;
-constexpr int kPairStage = 3 * kATile;   // U_r, U_i slice rows + half of the B stack: 12 KB
+constexpr int kPairRing = 192 * 1024;    // bytes of the TMA ring per CTA
 constexpr int kPairGroup = 6;            // row pairs per raster group (a wave: ~12 row x 12 column tiles)
 
-template <int MODE>
+// RB: bytes of K per operand row in a stage (32, 64 or 128, with the matching
+// TMA swizzle).  A stage holds the CTA's U_r, U_i slice rows and its half of
+// the B stack, 3 x 128 RB bytes, RB / 32 MMA K steps (two pair MMAs each);
+// wider rows move each operand byte in fewer, larger TMA requests and give
+// the barrier and issue overhead of a stage more MMAs.
+template <int RB>
+struct PairRing {
+    static constexpr int kTile = 128 * RB;                  // one 128-row operand tile
+    static constexpr int kStage = 3 * kTile;
+    static constexpr int kStages = kPairRing / kStage;     // 16, 8 or 4
+    static constexpr int kKPer = RB / 2;                    // BF16 K values per stage
+    static constexpr int kSteps = RB / 32;                  // MMA K steps per stage
+};
+
+template <int MODE, int RB>
 __global__ void __launch_bounds__(kThreads, 1)
     cgemm_oz_pair_kernel(const __grid_constant__ CUtensorMap tmU, const __grid_constant__ CUtensorMap tmP, OzEpi ep) {
     constexpr uint32_t kIdesc = make_idesc(1u, 256u, 256u);   // BF16 x BF16 -> FP32, M 256 (128 per CTA), N 256
+    using R = PairRing<RB>;
+    constexpr int kPairStages = R::kStages;
+    constexpr int kPairStage = R::kStage;
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -408,7 +424,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int kmax = 1 << (26 - 2 * ep.bits);
     const int Kc = ep.Np < kmax ? ep.Np : kmax;
     const int chunks = ep.Np / Kc;
-    const int KBc = Kc / kKPerStage;
+    const int KBc = Kc / R::kKPer;
     const int passes = S * (S + 1) / 2 * chunks;
 
     if (warp == 4) {
@@ -430,18 +446,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                         break;
                     }
                     uint8_t* st = smem + s * kPairStage;
-                    const int kx = c * Kc + kb * kKPerStage;
+                    const int kx = c * Kc + kb * R::kKPer;
                     if (rank == 0) {
                         mbar_arrive_expect_tx(&full[s], 2 * kPairStage);   // both CTAs' bytes
                         const uint32_t fb = saddr(&full[s]);
-                        tma_load_3d_hint(saddr(st), &tmU, fb, kx, I * 128, t, keep);                // U_r slice t
-                        tma_load_3d_hint(saddr(st + kATile), &tmU, fb, kx, I * 128, S + t, keep);   // U_i slice t
-                        tma_load_3d(saddr(st + 2 * kATile), &tmP, fb, kx, J * 128, u);              // P_r slice u
+                        tma_load_3d_hint(saddr(st), &tmU, fb, kx, I * 128, t, keep);                  // U_r slice t
+                        tma_load_3d_hint(saddr(st + R::kTile), &tmU, fb, kx, I * 128, S + t, keep);   // U_i slice t
+                        tma_load_3d(saddr(st + 2 * R::kTile), &tmP, fb, kx, J * 128, u);              // P_r slice u
                     } else {
                         const uint32_t fb = lead_full + 8u * (uint32_t)s;
                         tma_load_3d_pair_hint(saddr(st), &tmU, fb, kx, I * 128, t, keep);
-                        tma_load_3d_pair_hint(saddr(st + kATile), &tmU, fb, kx, I * 128, S + t, keep);
-                        tma_load_3d_pair(saddr(st + 2 * kATile), &tmP, fb, kx, J * 128, S + u);     // P_i slice u
+                        tma_load_3d_pair_hint(saddr(st + R::kTile), &tmU, fb, kx, I * 128, S + t, keep);
+                        tma_load_3d_pair(saddr(st + 2 * R::kTile), &tmP, fb, kx, J * 128, S + u);     // P_i slice u
                     }
                 }
             }
@@ -483,9 +499,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     tc_fence_after();
                     uint8_t* st = smem + s * kPairStage;
-                    const uint64_t bd = desc_kmajor_sw32(saddr(st + 2 * kATile));
-                    umma_pair(tmem, desc_kmajor_sw32(saddr(st)), bd, kIdesc, kb > 0 ? 1u : 0u);
-                    umma_pair(tmem + 256, desc_kmajor_sw32(saddr(st + kATile)), bd, kIdesc, kb > 0 ? 1u : 0u);
+                    const uint64_t ar = desc_kmajor<RB>(saddr(st));
+                    const uint64_t ai = desc_kmajor<RB>(saddr(st + R::kTile));
+                    const uint64_t bd = desc_kmajor<RB>(saddr(st + 2 * R::kTile));
+#pragma unroll
+                    for (int ks = 0; ks < R::kSteps; ks++) {
+                        const uint32_t acc = (kb > 0 || ks > 0) ? 1u : 0u;
+                        const uint64_t off = 2u * (uint64_t)ks;   // 32 bytes of K further in each row
+                        umma_pair(tmem, ar + off, bd + off, kIdesc, acc);
+                        umma_pair(tmem + 256, ai + off, bd + off, kIdesc, acc);
+                    }
                     umma_commit_pair(saddr(&empty[s]));
                     umma_commit_pair(peer_empty + 8u * (uint32_t)s);
                 }
@@ -543,7 +566,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
-constexpr int kPairSmem = kPairStages * kPairStage + 1024 /*align*/ + 512 /*barriers*/;
+constexpr int kPairSmem = kPairRing + 1024 /*align*/ + 512 /*barriers*/;
 
 // One warp per row r < Np: the row exponent over both planes, then the S
 // balanced base-2^b digits of every entry (zero beyond the valid N x N block).
@@ -648,9 +671,9 @@ tc_status launch(const CUtensorMap& tmU, const CUtensorMap& tmP, const OzEpi& ep
 
 // Pairs of CTAs (clusters of 2) on the 2-SM MMA: T even; mode 0 T * T / 2
 // pairs, mode 1 sum over row pairs p of (2p + 2).
-template <int MODE>
+template <int MODE, int RB>
 tc_status launch_pair(const CUtensorMap& tmU, const CUtensorMap& tmP, const OzEpi& ep, cudaStream_t s) {
-    auto k = cgemm_oz_pair_kernel<MODE>;
+    auto k = cgemm_oz_pair_kernel<MODE, RB>;
     static bool attr_set[64] = {};
     int dev = 0;
     TC_CUDA(cudaGetDevice(&dev));
@@ -731,7 +754,20 @@ tc_status oz_mirror(double* yr, double* yi, int Np, cudaStream_t s) {
     return TC_OK;
 }
 
-tc_status cgemm_oz(int mode, const CUtensorMap& tmU, const CUtensorMap& tmP, const OzEpi& ep, cudaStream_t s) {
+int oz_pair_rows() {
+    static std::atomic<int> rows{0};
+    int v = rows.load();
+    if (v == 0) {
+        const char* e = std::getenv("TC_OZ_ROWS");
+        v = e ? std::atoi(e) : 128;
+        if (v != 32 && v != 64 && v != 128) v = 128;
+        rows.store(v);
+    }
+    return v;
+}
+
+tc_status cgemm_oz(int mode, const CUtensorMap& tmU, const CUtensorMap& tmP, const CUtensorMap& tmU_w,
+                   const CUtensorMap& tmP_w, const OzEpi& ep, cudaStream_t s) {
     if (ep.Np < 128 || ep.Np % 128 != 0 || ep.tiles * 128 != ep.Np)
         return fail(TC_ERR_INVALID_ARG, "cgemm_oz: padded dimension must be a multiple of 128");
     const OzDigits dg = oz_digits(ep.Np);
@@ -740,8 +776,15 @@ tc_status cgemm_oz(int mode, const CUtensorMap& tmU, const CUtensorMap& tmP, con
     if (ep.Np > dg.kmax && ep.Np % dg.kmax != 0)
         return fail(TC_ERR_INVALID_ARG, "cgemm_oz: dimension above %d must be a multiple of it", dg.kmax);
     if (oz_use_pairs(ep.tiles)) {
-        if (mode == 0) return launch_pair<0>(tmU, tmP, ep, s);
-        if (mode == 1) return launch_pair<1>(tmU, tmP, ep, s);
+        if (mode != 0 && mode != 1) return fail(TC_ERR_INVALID_ARG, "cgemm_oz: mode");
+        switch (oz_pair_rows()) {
+            case 32:
+                return mode == 0 ? launch_pair<0, 32>(tmU_w, tmP_w, ep, s) : launch_pair<1, 32>(tmU_w, tmP_w, ep, s);
+            case 64:
+                return mode == 0 ? launch_pair<0, 64>(tmU_w, tmP_w, ep, s) : launch_pair<1, 64>(tmU_w, tmP_w, ep, s);
+            default:
+                return mode == 0 ? launch_pair<0, 128>(tmU_w, tmP_w, ep, s) : launch_pair<1, 128>(tmU_w, tmP_w, ep, s);
+        }
     }
     if (mode == 0) return launch<0>(tmU, tmP, ep, s);
     if (mode == 1) return launch<1>(tmU, tmP, ep, s);
@@ -760,6 +803,7 @@ tc_status oz_mat_init(OzMat& m, Arena& ar, int Np) {
     m.slices = ar.take<uint8_t>(oz_slice_bytes(Np));
     m.ex = ar.take<int>((size_t)Np);
     if (!m.ex) return fail(TC_ERR_WORKSPACE, "FP64 emulation: workspace too small");
+    TC_TRY(make_part_map_rows(&m.map_w, m.slices, Np, 2 * m.dg.slices, TC_BF16X3, oz_pair_rows()));
     return make_part_map(&m.map, m.slices, Np, 2 * m.dg.slices, TC_BF16X3);
 }
 
@@ -769,6 +813,7 @@ tc_status oz_mat_view(OzMat& view, const OzMat& base, int Np) {
     view = base;
     view.Np = Np;
     view.dg = oz_digits(Np);
+    TC_TRY(make_part_map_rows(&view.map_w, base.slices, Np, 2 * view.dg.slices, TC_BF16X3, oz_pair_rows()));
     return make_part_map(&view.map, base.slices, Np, 2 * view.dg.slices, TC_BF16X3);
 }
 
@@ -793,7 +838,7 @@ tc_status oz_product(int mode, const OzMat& A, const OzMat& B, const OzOut& out,
     ep.bits = A.dg.bits;
     ep.slices = A.dg.slices;
     ep.status = device_status_word();
-    TC_TRY(cgemm_oz(mode, A.map, B.map, ep, s));
+    TC_TRY(cgemm_oz(mode, A.map, B.map, A.map_w, B.map_w, ep, s));
     if (mode == 1) TC_TRY(oz_mirror(out.yr, out.yi, A.Np, s));
     return TC_OK;
 }

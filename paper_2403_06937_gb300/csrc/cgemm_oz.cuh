@@ -46,8 +46,14 @@ struct OzEpi {
 tc_status oz_slice(const double* re, const double* im, bool interleaved, bool conj, int N, size_t ld, int Np,
                    const OzDigits& dg, void* slices, int* ex, cudaStream_t s);
 size_t oz_slice_bytes(int Np);
-// Y = U P^H (mode 0: all tiles; mode 1: block-lower tiles, then oz_mirror)
-tc_status cgemm_oz(int mode, const CUtensorMap& tmU, const CUtensorMap& tmP, const OzEpi& ep, cudaStream_t s);
+// Y = U P^H (mode 0: all tiles; mode 1: block-lower tiles, then oz_mirror);
+// tmU, tmP: 32-byte-row maps (single CTAs), tmU_w, tmP_w: maps of
+// oz_pair_rows()-byte rows (CTA pairs)
+tc_status cgemm_oz(int mode, const CUtensorMap& tmU, const CUtensorMap& tmP, const CUtensorMap& tmU_w,
+                   const CUtensorMap& tmP_w, const OzEpi& ep, cudaStream_t s);
+// Bytes of K per operand row in a stage of the CTA-pair kernel: 128 (TC_OZ_ROWS
+// = 32 or 64 in the environment selects narrower rows)
+int oz_pair_rows();
 tc_status oz_mirror(double* yr, double* yi, int Np, cudaStream_t s);
 // True when the product of `tiles` tiles a side runs as CTA pairs on the 2-SM
 // MMA (an even tile count, unless TC_OZ_PAIRS=0 in the environment); else
@@ -59,7 +65,8 @@ bool oz_use_pairs(int tiles);
 struct OzMat {
     void* slices;
     int* ex;
-    CUtensorMap map;
+    CUtensorMap map;     // 32-byte rows (single-CTA kernel)
+    CUtensorMap map_w;   // oz_pair_rows() bytes per row (CTA-pair kernel)
     int Np;
     OzDigits dg;   // oz_digits(Np)
 };

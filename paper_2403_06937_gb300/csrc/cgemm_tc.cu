@@ -218,13 +218,27 @@ tc_status launch(const CUtensorMap& tmU, const CUtensorMap& tmP, const CgemmEpi&
 // CTAs, the copies in flight land (the even CTA waits for its armed stages,
 // the odd one a fixed 1 ms), the MMA thread waits for its MMAs, and both
 // meet at a cluster barrier before TMEM is freed.
-template <int KIND, int S, int STAGES, int MODE>
+// RB: bytes of K per operand row in a stage (32, 64 or 128, with the matching
+// TMA swizzle): a stage is 3 S tiles of 128 RB bytes and RB / 32 MMA K steps;
+// the ring holds as many stages as fit in kPairRing bytes.
+constexpr int kPairRing = 216 * 1024;
+
+template <int S, int RB>
+constexpr int pair_stages() {
+    return kPairRing / (3 * S * 128 * RB);
+}
+
+template <int KIND, int S, int RB, int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
     cgemm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmU, const __grid_constant__ CUtensorMap tmP,
                          CgemmEpi ep) {
-    constexpr int kStage = 3 * S * kATile;   // own U_r, U_i parts + own half of each B part
+    constexpr int STAGES = pair_stages<S, RB>();
+    static_assert(STAGES >= 2, "ring too small for this row width");
+    constexpr int kTile = 128 * RB;          // one 128-row operand tile
+    constexpr int kStage = 3 * S * kTile;    // own U_r, U_i parts + own half of each B part
     constexpr int kElem = KIND == 0 ? 2 : 4;
-    constexpr int kKPerStage = kRowBytes / kElem;
+    constexpr int kKPerStage = RB / kElem;
+    constexpr int kSteps = RB / 32;          // MMA K steps per stage
     constexpr uint32_t kIdesc = make_idesc(KIND == 0 ? 1u : 2u, 256u, 256u);
 
     extern __shared__ uint8_t smem_raw[];
@@ -292,21 +306,21 @@ __global__ void __launch_bounds__(kThreads, 1)
                     for (int part = 0; part < 2; part++)
 #pragma unroll
                         for (int a = 0; a < S; a++)
-                            tma_load_3d(saddr(st + (part * S + a) * kATile), &tmU, fb, kx, I * 128, part * S + a);
+                            tma_load_3d(saddr(st + (part * S + a) * kTile), &tmU, fb, kx, I * 128, part * S + a);
 #pragma unroll
                     for (int b = 0; b < S; b++)   // P_r part b
-                        tma_load_3d(saddr(st + (2 * S + b) * kATile), &tmP, fb, kx, J * 128, b);
+                        tma_load_3d(saddr(st + (2 * S + b) * kTile), &tmP, fb, kx, J * 128, b);
                 } else {
                     const uint32_t fb = lead_full + 8u * (uint32_t)s;
 #pragma unroll
                     for (int part = 0; part < 2; part++)
 #pragma unroll
                         for (int a = 0; a < S; a++)
-                            tma_load_3d_pair(saddr(st + (part * S + a) * kATile), &tmU, fb, kx, I * 128,
+                            tma_load_3d_pair(saddr(st + (part * S + a) * kTile), &tmU, fb, kx, I * 128,
                                              part * S + a);
 #pragma unroll
                     for (int b = 0; b < S; b++)   // P_i part b
-                        tma_load_3d_pair(saddr(st + (2 * S + b) * kATile), &tmP, fb, kx, J * 128, S + b);
+                        tma_load_3d_pair(saddr(st + (2 * S + b) * kTile), &tmP, fb, kx, J * 128, S + b);
                 }
             }
             const int from = issued - STAGES > 0 ? issued - STAGES : 0;
@@ -339,12 +353,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tc_fence_after();
                 uint8_t* st = smem + s * kStage;
 #pragma unroll
-                for (int p = 0; p < Pairs<S>::n; p++) {
-                    const uint64_t bd = desc_kmajor_sw32(saddr(st + (2 * S + Pairs<S>::b(p)) * kATile));
+                for (int ks = 0; ks < kSteps; ks++) {
+                    const uint64_t off = 2u * (uint64_t)ks;   // 32 bytes of K further in each row
 #pragma unroll
-                    for (int part = 0; part < 2; part++) {
-                        const uint64_t ad = desc_kmajor_sw32(saddr(st + (part * S + Pairs<S>::a(p)) * kATile));
-                        umma_pair(tmem + part * 256, ad, bd, kIdesc, (kb > 0 || p > 0) ? 1u : 0u);
+                    for (int p = 0; p < Pairs<S>::n; p++) {
+                        const uint64_t bd = desc_kmajor<RB>(saddr(st + (2 * S + Pairs<S>::b(p)) * kTile)) + off;
+#pragma unroll
+                        for (int part = 0; part < 2; part++) {
+                            const uint64_t ad =
+                                desc_kmajor<RB>(saddr(st + (part * S + Pairs<S>::a(p)) * kTile)) + off;
+                            umma_pair(tmem + part * 256, ad, bd, kIdesc, (kb > 0 || ks > 0 || p > 0) ? 1u : 0u);
+                        }
                     }
                 }
                 umma_commit_pair(saddr(&empty[s]));
@@ -381,15 +400,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
-template <int KIND, int S, int STAGES>
+template <int S, int RB>
 constexpr int pair_smem_bytes() {
-    return STAGES * 3 * S * kATile + 1024 /*align*/ + 512 /*barriers*/;
+    return pair_stages<S, RB>() * 3 * S * 128 * RB + 1024 /*align*/ + 512 /*barriers*/;
 }
 
-template <int KIND, int S, int STAGES, int MODE>
+template <int KIND, int S, int RB, int MODE>
 tc_status launch_pair(const CUtensorMap& tmU, const CUtensorMap& tmP, const CgemmEpi& ep, cudaStream_t s) {
-    auto k = cgemm_tc_pair_kernel<KIND, S, STAGES, MODE>;
-    constexpr int smem = pair_smem_bytes<KIND, S, STAGES>();
+    auto k = cgemm_tc_pair_kernel<KIND, S, RB, MODE>;
+    constexpr int smem = pair_smem_bytes<S, RB>();
     static bool attr_set[64] = {};
     int dev = 0;
     TC_CUDA(cudaGetDevice(&dev));
@@ -446,8 +465,22 @@ void cgemm_inject_timeout(int count, unsigned long long wait_ns) {
 int cgemm_default_stages(int precision) { return precision == TC_BF16X3 ? 4 : precision == TC_TF32X3 ? 6 : 8; }
 int cgemm_alt_stages(int precision) { return precision == TC_BF16X3 ? 3 : precision == TC_TF32X3 ? 3 : 4; }
 
+int cgemm_pair_rows(int precision) {
+    static std::atomic<int> forced{-1};
+    int f = forced.load();
+    if (f < 0) {
+        const char* e = std::getenv("TC_GEMM_ROWS");
+        f = e ? std::atoi(e) : 0;
+        if (f != 32 && f != 64 && f != 128) f = 0;
+        forced.store(f);
+    }
+    const int dflt = precision == TC_TF32 ? 128 : 64;
+    if (f == 128 && precision == TC_BF16X3) return 64;   // one 144 KB stage would not double-buffer
+    return f ? f : dflt;
+}
+
 tc_status cgemm_tc(int precision, int mode, const CUtensorMap& tmU, const CUtensorMap& tmP, const CgemmEpi& ep_in,
-                   cudaStream_t s, int stages) {
+                   cudaStream_t s, int stages, const CUtensorMap* tmU_w, const CUtensorMap* tmP_w) {
     CgemmEpi ep = ep_in;
     if (g_inject_count.load() > 0 && g_inject_count.fetch_sub(1) > 0) {
         ep.withhold = 1;
@@ -469,20 +502,29 @@ tc_status cgemm_tc(int precision, int mode, const CUtensorMap& tmU, const CUtens
     if (!alt && stages != cgemm_default_stages(precision))
         return fail(TC_ERR_INVALID_ARG, "cgemm_tc: %d stages not built for precision %d", stages, precision);
     if (cgemm_use_pairs(ep.tiles, mode, ep.lo, ep.hi)) {
-        // CTA pairs: rings of {6, 4} (BF16x3), {9, 6} (TF32x3), {18, 12} (TF32) stages of 12 S KB
+        // CTA pairs: rows of cgemm_pair_rows() bytes when the caller gave maps of that width, else of 32 bytes
+        const bool wide = tmU_w && tmP_w && cgemm_pair_rows(precision) != 32;
+        const CUtensorMap& u = wide ? *tmU_w : tmU;
+        const CUtensorMap& p = wide ? *tmP_w : tmP;
+        const int rb = wide ? cgemm_pair_rows(precision) : 32;
+#define TC_PAIR(K, S_, RB_) \
+    return mode == 0 ? launch_pair<K, S_, RB_, 0>(u, p, ep, s) : launch_pair<K, S_, RB_, 1>(u, p, ep, s)
         switch (precision) {
             case TC_BF16X3:
-                if (alt) return mode == 0 ? launch_pair<0, 3, 4, 0>(tmU, tmP, ep, s) : launch_pair<0, 3, 4, 1>(tmU, tmP, ep, s);
-                return mode == 0 ? launch_pair<0, 3, 6, 0>(tmU, tmP, ep, s) : launch_pair<0, 3, 6, 1>(tmU, tmP, ep, s);
+                if (rb == 64) TC_PAIR(0, 3, 64);
+                TC_PAIR(0, 3, 32);
             case TC_TF32:
-                if (alt) return mode == 0 ? launch_pair<1, 1, 12, 0>(tmU, tmP, ep, s) : launch_pair<1, 1, 12, 1>(tmU, tmP, ep, s);
-                return mode == 0 ? launch_pair<1, 1, 18, 0>(tmU, tmP, ep, s) : launch_pair<1, 1, 18, 1>(tmU, tmP, ep, s);
+                if (rb == 128) TC_PAIR(1, 1, 128);
+                if (rb == 64) TC_PAIR(1, 1, 64);
+                TC_PAIR(1, 1, 32);
             case TC_TF32X3:
-                if (alt) return mode == 0 ? launch_pair<1, 2, 6, 0>(tmU, tmP, ep, s) : launch_pair<1, 2, 6, 1>(tmU, tmP, ep, s);
-                return mode == 0 ? launch_pair<1, 2, 9, 0>(tmU, tmP, ep, s) : launch_pair<1, 2, 9, 1>(tmU, tmP, ep, s);
+                if (rb == 128) TC_PAIR(1, 2, 128);
+                if (rb == 64) TC_PAIR(1, 2, 64);
+                TC_PAIR(1, 2, 32);
             default:
                 return fail(TC_ERR_INVALID_ARG, "cgemm_tc: precision %d has no tensor-core form", precision);
         }
+#undef TC_PAIR
     }
     switch (precision) {
         case TC_BF16X3:

@@ -34,8 +34,15 @@ struct CgemmEpi {
 
 // stages: TMA ring depth (0 = the largest that fits); the built depths are
 // BF16x3 {4, 3}, TF32 {8, 4}, TF32x3 {6, 3}.
+// tmU_w, tmP_w (optional): maps of cgemm_pair_rows(precision)-byte rows for
+// the CTA-pair kernel (without them the pairs take the 32-byte-row maps).
 tc_status cgemm_tc(int precision, int mode, const CUtensorMap& tmU, const CUtensorMap& tmP, const CgemmEpi& ep,
-                   cudaStream_t s, int stages = 0);
+                   cudaStream_t s, int stages = 0, const CUtensorMap* tmU_w = nullptr,
+                   const CUtensorMap* tmP_w = nullptr);
+// Bytes of K per operand row in a stage of the CTA-pair kernel: 64 for
+// BF16x3 and TF32x3, 128 for TF32 (TC_GEMM_ROWS = 32, 64 or 128 in the
+// environment overrides, 128 capped at 64 for BF16x3)
+int cgemm_pair_rows(int precision);
 int cgemm_default_stages(int precision);
 // True when a launch of `tiles` tiles a side (and the range lo, hi of
 // CgemmEpi) runs as CTA pairs on the 2-SM MMA: an even tile count, whole row
@@ -54,5 +61,8 @@ size_t cgemm_elem_bytes(int precision);
 // 3-D tensor map over `planes` consecutive Np x Np planes of operand parts:
 // box = 32 bytes of K x 128 rows x 1 plane, 32-byte swizzle.
 tc_status make_part_map(CUtensorMap* map, const void* base, int Np, int planes, int precision);
+// the same with boxes of `row_bytes` (32, 64 or 128) of K per row and the
+// matching swizzle
+tc_status make_part_map_rows(CUtensorMap* map, const void* base, int Np, int planes, int precision, int row_bytes);
 
 }  // namespace tc

@@ -331,6 +331,7 @@ namespace {
 // Tensor maps and epilogues of the two products of a step on the buffers b.
 struct StepPlan {
     CUtensorMap tmU, tmR, tmX;
+    CUtensorMap wU, wR, wX;   // cgemm_pair_rows()-byte rows, for the CTA-pair kernel
     CgemmEpi e1;   // X = rho^H + V rho^H
     CgemmEpi e2;   // rho' = X^H + V X^H
     TuneChoice tune;
@@ -340,6 +341,10 @@ tc_status plan_step(int n, int precision, const LowpBufs& b, StepPlan& p) {
     TC_TRY(make_part_map(&p.tmU, b.Uparts, b.Np, 2 * b.S, precision));
     TC_TRY(make_part_map(&p.tmR, b.Rparts, b.Np, 2 * b.S, precision));
     TC_TRY(make_part_map(&p.tmX, b.Xparts, b.Np, 2 * b.S, precision));
+    const int rows = cgemm_pair_rows(precision);
+    TC_TRY(make_part_map_rows(&p.wU, b.Uparts, b.Np, 2 * b.S, precision, rows));
+    TC_TRY(make_part_map_rows(&p.wR, b.Rparts, b.Np, 2 * b.S, precision, rows));
+    TC_TRY(make_part_map_rows(&p.wX, b.Xparts, b.Np, 2 * b.S, precision, rows));
     p.tune = tune_lookup(n, precision);
     p.e1 = CgemmEpi{};
     p.e1.Np = b.Np;
@@ -381,11 +386,11 @@ tc_status evolve_lowp(const double* U, double* rho, int n, int steps, int precis
     auto one_step = [&](int k, cudaStream_t cs) -> tc_status {
         {
             ProductTimer t(8.0 * N3 * prod, cs);
-            TC_TRY(cgemm_tc(precision, 0, tmU, tmR, e1, cs, tune.tc_stages));
+            TC_TRY(cgemm_tc(precision, 0, tmU, tmR, e1, cs, tune.tc_stages, &sp.wU, &sp.wR));
         }
         {
             ProductTimer t(4.0 * N3 * prod, cs);
-            TC_TRY(cgemm_tc(precision, 1, tmU, tmX, e2, cs, tune.tc_stages));
+            TC_TRY(cgemm_tc(precision, 1, tmU, tmX, e2, cs, tune.tc_stages, &sp.wU, &sp.wX));
         }
         if (renorm_every > 0 && k % renorm_every == 0) TC_TRY(lowp_renorm(precision, b, cs));
         if (obs)
@@ -543,7 +548,7 @@ tc_status evolve_lowp_host_blocks(const double* U, double* rho_host, double* rho
         CgemmEpi e = sp.e1;
         e.lo = c * T / C;
         e.hi = (c + 1) * T / C;
-        TC_TRY(cgemm_tc(precision, 0, sp.tmU, sp.tmR, e, s, sp.tune.tc_stages));
+        TC_TRY(cgemm_tc(precision, 0, sp.tmU, sp.tmR, e, s, sp.tune.tc_stages, &sp.wU, &sp.wR));
         mark("x", c, s);
     }
     // rows of chunk c of rho' out (their products done on s).  A mapped host
@@ -570,10 +575,10 @@ tc_status evolve_lowp_host_blocks(const double* U, double* rho_host, double* rho
     };
     if (obs) TC_TRY(launch_observables(kRhoPlanarF32, b.Rr, b.Ri, m, n, obs, b.scratch, s, (size_t)b.Np));
     for (int k = 1; k <= steps; k++) {
-        if (k > 1) TC_TRY(cgemm_tc(precision, 0, sp.tmU, sp.tmR, sp.e1, s, sp.tune.tc_stages));
+        if (k > 1) TC_TRY(cgemm_tc(precision, 0, sp.tmU, sp.tmR, sp.e1, s, sp.tune.tc_stages, &sp.wU, &sp.wR));
         const bool renorm = renorm_every > 0 && k % renorm_every == 0;
         if (k < steps || renorm) {
-            TC_TRY(cgemm_tc(precision, 1, sp.tmU, sp.tmX, sp.e2, s, sp.tune.tc_stages));
+            TC_TRY(cgemm_tc(precision, 1, sp.tmU, sp.tmX, sp.e2, s, sp.tune.tc_stages, &sp.wU, &sp.wX));
             if (renorm) TC_TRY(lowp_renorm(precision, b, s));
             if (obs) TC_TRY(launch_observables(kRhoPlanarF32, b.Rr, b.Ri, m, n, obs + (size_t)k * stride, b.scratch,
                                                s, (size_t)b.Np));
@@ -589,7 +594,7 @@ tc_status evolve_lowp_host_blocks(const double* U, double* rho_host, double* rho
             CgemmEpi e = sp.e2;
             e.lo = c * T / C;
             e.hi = (c + 1) * T / C;
-            TC_TRY(cgemm_tc(precision, 1, sp.tmU, sp.tmX, e, s, sp.tune.tc_stages));
+            TC_TRY(cgemm_tc(precision, 1, sp.tmU, sp.tmX, e, s, sp.tune.tc_stages, &sp.wU, &sp.wX));
             mark("y", c, s);
             TC_TRY(out_rows(c));
         }

@@ -274,6 +274,23 @@ __device__ __forceinline__ uint64_t desc_kmajor_sw32(uint32_t addr) {
     return d;
 }
 
+// The same for K-major tiles of RB-byte rows (RB = 32, 64 or 128) laid out by
+// TMA with the matching swizzle: core groups of 8 rows x RB bytes, 8 RB apart.
+// The k-th 32-byte K step inside a row starts k x 32 bytes further (add 2 k to
+// the descriptor); the tile must start on an 8 RB boundary.
+template <int RB>
+__device__ __forceinline__ uint64_t desc_kmajor(uint32_t addr) {
+    static_assert(RB == 32 || RB == 64 || RB == 128, "row bytes");
+    constexpr uint64_t kLayout = RB == 32 ? 6u : RB == 64 ? 4u : 2u;   // 32-, 64-, 128-byte swizzle
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1u << 16;                   // leading byte offset (unused: K fits one swizzle atom)
+    d |= (uint64_t)((8u * RB) >> 4) << 32;     // stride byte offset: next group of 8 rows
+    d |= (uint64_t)1u << 46;
+    d |= kLayout << 61;
+    return d;
+}
+
 // Instruction descriptor: FP32 accumulator, A and B of format `fmt`
 // (1 = BF16 for kind::f16, 2 = TF32 for kind::tf32), both K-major, M x N.
 __host__ __device__ constexpr uint32_t make_idesc(uint32_t fmt, uint32_t M, uint32_t N) {

@@ -28,6 +28,12 @@ tc_status get_encode(PFN_cuTensorMapEncodeTiled_v12000* fn) {
 }  // namespace
 
 tc_status make_part_map(CUtensorMap* map, const void* base, int Np, int planes, int precision) {
+    return make_part_map_rows(map, base, Np, planes, precision, 32);
+}
+
+tc_status make_part_map_rows(CUtensorMap* map, const void* base, int Np, int planes, int precision, int row_bytes) {
+    if (row_bytes != 32 && row_bytes != 64 && row_bytes != 128)
+        return fail(TC_ERR_INVALID_ARG, "tensor map: rows of 32, 64 or 128 bytes");
     PFN_cuTensorMapEncodeTiled_v12000 enc;
     TC_TRY(get_encode(&enc));
     const size_t E = cgemm_elem_bytes(precision);
@@ -35,11 +41,13 @@ tc_status make_part_map(CUtensorMap* map, const void* base, int Np, int planes, 
         return fail(TC_ERR_INVALID_ARG, "operand planes must be 16-byte aligned with 16-byte row pitch");
     cuuint64_t dims[3] = {(cuuint64_t)Np, (cuuint64_t)Np, (cuuint64_t)planes};
     cuuint64_t strides[2] = {(cuuint64_t)Np * E, (cuuint64_t)Np * (cuuint64_t)Np * E};
-    cuuint32_t box[3] = {(cuuint32_t)(32 / E), 128u, 1u};
+    cuuint32_t box[3] = {(cuuint32_t)(row_bytes / E), 128u, 1u};
     cuuint32_t estr[3] = {1u, 1u, 1u};
     CUtensorMapDataType dt = E == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     CUresult r = enc(map, dt, 3, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                     CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                     row_bytes == 32 ? CU_TENSOR_MAP_SWIZZLE_32B
+                                     : row_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(TC_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     return TC_OK;
 }

@@ -245,6 +245,11 @@ TC_API tc_status tc_autotune(int n, int precision, void* work, size_t work_bytes
         TC_TRY(make_part_map(&tmU, b.Uparts, b.Np, 2 * b.S, precision));
         TC_TRY(make_part_map(&tmR, b.Rparts, b.Np, 2 * b.S, precision));
         TC_TRY(make_part_map(&tmX, b.Xparts, b.Np, 2 * b.S, precision));
+        CUtensorMap wU, wR, wX;   // the CTA-pair kernel's wider rows
+        const int rows = cgemm_pair_rows(precision);
+        TC_TRY(make_part_map_rows(&wU, b.Uparts, b.Np, 2 * b.S, precision, rows));
+        TC_TRY(make_part_map_rows(&wR, b.Rparts, b.Np, 2 * b.S, precision, rows));
+        TC_TRY(make_part_map_rows(&wX, b.Xparts, b.Np, 2 * b.S, precision, rows));
         CgemmEpi e{};   // X = rho^H + V rho^H
         e.Np = b.Np;
         e.tiles = b.Np / 128;
@@ -267,8 +272,8 @@ TC_API tc_status tc_autotune(int n, int precision, void* work, size_t work_bytes
                 e2.group = group;
                 double ms = 0.0;
                 TC_TRY(time_ms(s, 3, [&]() {
-                    tc_status st = cgemm_tc(precision, 0, tmU, tmR, e, s, stages);
-                    return st == TC_OK ? cgemm_tc(precision, 1, tmU, tmX, e2, s, stages) : st;
+                    tc_status st = cgemm_tc(precision, 0, tmU, tmR, e, s, stages, &wU, &wR);
+                    return st == TC_OK ? cgemm_tc(precision, 1, tmU, tmX, e2, s, stages, &wU, &wX) : st;
                 }, &ms));
                 if (ms < best_ms) {
                     best_ms = ms;
