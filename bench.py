@@ -41,9 +41,9 @@ METRIC = "evolution steps/s and complex-GEMM TFLOP/s at n=14 (FP64 vs split-BF16
 # DRAM bytes (read + write) per launch of the dominant kernel, keyed by
 # (precision, n): dram__bytes_read.sum + dram__bytes_write.sum averaged over
 # the four launches (two of each product) of a one-pass ncu capture at
-# n = 12 (1.485 GB), scaled to n = 14 by the N^3 units a launch processes;
+# n = 12 (1.484 GB), scaled to n = 14 by the N^3 units a launch processes;
 # null for any other key.
-NCU_TRAFFIC = {("bf16x3", 14): 1.485e9 * 64}
+NCU_TRAFFIC = {("bf16x3", 14): 1.484e9 * 64}
 
 
 def _args():
