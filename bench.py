@@ -63,6 +63,8 @@ def _args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--full", action="store_true",
                     help="also run the workload's whole run (500 steps at n=14) and state its error vs the oracle")
+    ap.add_argument("--shapes", action="store_true",
+                    help="batch workload: also time the batch in each tile shape, pinned")
     return ap.parse_args()
 
 
@@ -641,6 +643,14 @@ def run_batch(a):
         r[-1, -1] = 1.0
         rhos.append(r)
         ps.append(p)
+    # the autotuner picks tile shape, raster group and ring depth for every n of the batch (the
+    # per-system calls use them too; the batch takes the choice for its largest n)
+    nmax = max(c.n for c in cfgs)
+    tuned, batch_choice = {}, None
+    if prec not in ("fp64", "ozaki"):
+        for n in sorted({c.n for c in cfgs}):
+            tuned[n] = tc.autotune(n, prec)
+        batch_choice = tc.batch_autotune([c.n for c in cfgs], prec)
     tc.batch_evolve(Us, rhos, 1, prec, params=ps)          # warm (attributes, modules)
     torch.cuda.synchronize()
     l0 = tc.launch_count()
@@ -649,6 +659,19 @@ def run_batch(a):
     torch.cuda.synchronize()
     tb = time.perf_counter() - t0
     launches = tc.launch_count() - l0
+    # the same batch in each tile shape, pinned (the speed the tuner chose from)
+    shapes = {}
+    if batch_choice and a.shapes:
+        # every shape pinned for this batch (the tuner's group), then the tuned choice put back
+        for name, code in (("single", 1), ("pair32", 2), ("pair_wide", 3)):
+            tc.batch_autotune_set([c.n for c in cfgs], prec, batch_choice["tc_group"], code)
+            tc.batch_evolve(Us, rhos, 1, prec, params=ps)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            tc.batch_evolve(Us, rhos, steps, prec, params=ps)
+            torch.cuda.synchronize()
+            shapes[name] = len(cfgs) * steps / (time.perf_counter() - t0)
+        tc.batch_autotune_set([c.n for c in cfgs], prec, batch_choice["tc_group"], batch_choice["tc_shape"])
     t0 = time.perf_counter()
     for U, r, p in zip(Us, rhos, ps):
         tc.evolve(U, r, p.n, steps, prec, params=p)
@@ -667,6 +690,14 @@ def run_batch(a):
             "sequential": {"value": len(cfgs) * steps / ts, "unit": "system-steps/s",
                            "api": "tc_evolve per system, one after another"},
             "speedup_vs_sequential": ts / tb, "gpu_launches": launches}
+    if batch_choice:
+        names = {0: "auto", 1: "single", 2: "pair32", 3: "pair_wide"}
+        line["config"]["tile_shape"] = names[batch_choice["tc_shape"]]
+        line["config"]["raster_group"] = batch_choice["tc_group"]
+        line["config"]["tuning"] = "tc_batch_autotune (batch); tc_autotune per n (the per-system calls)"
+        line["tuned_per_n"] = {str(n): names[t["tc_shape"]] for n, t in tuned.items()}
+    if shapes:
+        line["by_shape"] = shapes
     print(json.dumps(line), flush=True)
     return 0
 

@@ -393,18 +393,26 @@ TC_API tc_status tc_evolve_host(const void* U, void* rho_host, int n, int steps,
 /* tc_autotune -- time every built configuration of the step products for n
  * atoms at `precision` on synthetic operands in `work` and keep the fastest
  * for later calls in this process (tc_evolve, tc_expm, tc_evolve_backward,
- * tc_batch_evolve):
+ * tc_batch_evolve, tc_evolve_open):
  *   FP64: the DMMA GEMM tile, 32 x 32 or 64 x 64 (timed on a K slice);
- *   tensor cores: the raster group G (G row tiles at a time for X = U rho,
- *   G x G super-blocks of the lower triangle for the Hermitian product, so
- *   concurrent CTAs share operand panels in L2; 4, 8, 12, 16) and the TMA
- *   ring depth (two per precision), timed over one whole step.
+ *   tensor cores: the tile shape (1: one CTA per 128 x 128 complex tile;
+ *   2: CTA pairs on the 2-SM MMA, a 256 x 128 tile per pair, 32 bytes of K
+ *   per operand row a stage; 3: CTA pairs with 64-byte rows, 128 for TF32),
+ *   the raster group G (G row tiles at a time for X = U rho, G x G
+ *   super-blocks of the lower triangle for the Hermitian product, so
+ *   concurrent CTAs share operand panels in L2; 4, 8, 12, 16) and, for
+ *   shape 1, the TMA ring depth (two per precision), each timed as the mean
+ *   step over >= 100 ms of back-to-back steps (the clock a configuration
+ *   holds under the power cap depends on its shared-memory and L2 traffic),
+ *   in two passes.  The batched and open-system calls take the shape and group
+ *   chosen for their largest n.
  * The choice is also appended, one JSON object per line, to the file named by
  * the environment variable TC_AUTOTUNE_CACHE (when set), which is read on the
  * first lookup of a process.  Every configuration computes each output in the
  * same order, so tuning changes speed, not results.  Synchronises `stream`.
  *  work   : device, >= tc_workspace_size(n, precision, TC_OP_EVOLVE, 0, 0).
- *  choice : host, 3 ints (f64 tile, raster group, ring depth), or NULL. */
+ *  choice : host, 4 ints (f64 tile, raster group, ring depth, tile shape),
+ *           or NULL. */
 TC_API tc_status tc_autotune(int n, int precision, void* work, size_t work_bytes, void* stream, int* choice);
 
 /* The configuration tc_evolve will use for (n, precision): tuned if tuned in
@@ -412,7 +420,10 @@ TC_API tc_status tc_autotune(int n, int precision, void* work, size_t work_bytes
 TC_API tc_status tc_autotune_lookup(int n, int precision, int* choice);
 
 /* Pin the configuration for (n, precision) in this process (host only):
- * choice = {f64 tile 32 | 64, raster group 1..128, a built ring depth}. */
+ * choice = {f64 tile 32 | 64, raster group 1..128, a built ring depth,
+ * tile shape 0..3 (0: automatic, CTA pairs with wide rows unless
+ * TC_GEMM_PAIRS=0 is in the environment)}.  A pair shape runs as single CTAs
+ * where the tile count is odd (tc_evolve). */
 TC_API tc_status tc_autotune_set(int n, int precision, const int* choice);
 
 /* ------------------------------------------------------------- batching */
@@ -440,6 +451,27 @@ TC_API size_t tc_batch_workspace_size(int count, const int* n, int precision);
 TC_API tc_status tc_batch_evolve(int count, const int* n, const void* const* U, void* const* rho, int steps,
                                  int precision, int renorm_every, const tc_params* params,
                                  double* const* obs, void* work, size_t work_bytes, void* stream);
+
+/* tc_batch_autotune -- choose the tile shape and raster group of the batched
+ * tensor-core products for batches of this composition (the multiset of
+ * n[b]): the batch's workspace is filled with synthetic operands and one
+ * batch step (both persistent launches) is timed in every shape (single CTAs
+ * on 128 x 128 tiles; CTA pairs on the 2-SM MMA, 256 x 128 a pair, with 32-byte
+ * or wide K rows) and raster group (4, 8, 12, 16), as the mean over >= 100 ms
+ * of back-to-back steps, in two passes.  Later tc_batch_evolve calls in this
+ * process on a batch of the same composition and precision use the fastest
+ * (otherwise the tc_autotune choice for the largest n); the choice is also
+ * appended to TC_AUTOTUNE_CACHE when set.  Results do not depend on the
+ * choice.  Synchronises `stream`.  No counterpart in the paper.
+ *  precision : TC_BF16X3, TC_TF32 or TC_TF32X3 (else TC_ERR_INVALID_ARG).
+ *  work      : device, >= tc_batch_workspace_size(count, n, precision).
+ *  choice    : host, 2 ints (raster group, tile shape 1..3), or NULL. */
+TC_API tc_status tc_batch_autotune(int count, const int* n, int precision, void* work, size_t work_bytes,
+                                   void* stream, int* choice);
+
+/* Pin the batch choice for this composition and precision in this process
+ * (host only): choice = {raster group 1..128, tile shape 0..3}. */
+TC_API tc_status tc_batch_autotune_set(int count, const int* n, int precision, const int* choice);
 
 /* ----------------------------------------------------------- measurement */
 

@@ -337,26 +337,56 @@ def autotune(n: int, precision="bf16x3", stream=None, work: Optional[torch.Tenso
     need = workspace_size(n, prec, TC_OP_EVOLVE)
     if work is None or work.numel() < need:
         work = _work(need, "cuda")
-    out = (ctypes.c_int * 3)()
+    out = (ctypes.c_int * 4)()
     _abi.call("tc_autotune", n, prec, _ptr(work), work.numel(), ctypes.c_void_p(_stream(stream)), out)
-    return {"f64_tile": out[0], "tc_group": out[1], "tc_stages": out[2]}
+    return {"f64_tile": out[0], "tc_group": out[1], "tc_stages": out[2], "tc_shape": out[3]}
 
 
 def autotune_lookup(n: int, precision="bf16x3"):
     """tc_autotune_lookup: the configuration in use for (n, precision) (host only)."""
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-    out = (ctypes.c_int * 3)()
+    out = (ctypes.c_int * 4)()
     _abi.call("tc_autotune_lookup", n, prec, out)
-    return {"f64_tile": out[0], "tc_group": out[1], "tc_stages": out[2]}
+    return {"f64_tile": out[0], "tc_group": out[1], "tc_stages": out[2], "tc_shape": out[3]}
 
 
-def autotune_set(n: int, precision="bf16x3", f64_tile: int = 32, tc_group: int = 8, tc_stages: int = 0) -> None:
+# tile shapes of the tensor-core products (tc_autotune_set's tc_shape)
+TILE_SHAPES = {"auto": 0, "single": 1, "pair32": 2, "pair_wide": 3}
+
+
+def autotune_set(n: int, precision="bf16x3", f64_tile: int = 32, tc_group: int = 8, tc_stages: int = 0,
+                 tc_shape=0) -> None:
     """tc_autotune_set: pin the configuration for (n, precision) in this process."""
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     if prec != TC_FP64 and tc_stages == 0:
         tc_stages = {TC_BF16X3: 4, TC_TF32X3: 6, TC_TF32: 8}[prec]
-    arr = (ctypes.c_int * 3)(int(f64_tile), int(tc_group), int(tc_stages))
+    shape = TILE_SHAPES[tc_shape] if isinstance(tc_shape, str) else int(tc_shape)
+    arr = (ctypes.c_int * 4)(int(f64_tile), int(tc_group), int(tc_stages), shape)
     _abi.call("tc_autotune_set", n, prec, arr)
+
+
+def batch_autotune(ns, precision="bf16x3", stream=None, work: Optional[torch.Tensor] = None):
+    """tc_batch_autotune: tile shape and raster group for batches of this composition; returns the choice."""
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    count = len(ns)
+    n_arr = (ctypes.c_int * count)(*[int(x) for x in ns])
+    need = int(_abi.load().tc_batch_workspace_size(count, n_arr, prec))
+    if work is None or work.numel() < need:
+        work = _work(need, "cuda")
+    out = (ctypes.c_int * 2)()
+    _abi.call("tc_batch_autotune", count, n_arr, prec, _ptr(work), work.numel(),
+              ctypes.c_void_p(_stream(stream)), out)
+    return {"tc_group": out[0], "tc_shape": out[1]}
+
+
+def batch_autotune_set(ns, precision="bf16x3", tc_group: int = 8, tc_shape=0) -> None:
+    """tc_batch_autotune_set: pin the batch tile shape and raster group for this composition in this process."""
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    count = len(ns)
+    n_arr = (ctypes.c_int * count)(*[int(x) for x in ns])
+    shape = TILE_SHAPES[tc_shape] if isinstance(tc_shape, str) else int(tc_shape)
+    arr = (ctypes.c_int * 2)(int(tc_group), shape)
+    _abi.call("tc_batch_autotune_set", count, n_arr, prec, arr)
 
 
 def launch_count() -> int:
@@ -399,7 +429,7 @@ def sync_status(stream=None) -> None:
 __all__ = ["Params", "TCError", "build_hamiltonian", "expm", "expm_model", "evolve", "LindbladLayout",
            "lindblad_layout", "lindblad_propagators", "lindblad_evolve", "evolve_host", "observables",
            "expectation_diag",
-           "evolve_backward", "EvolveFn", "batch_evolve", "autotune", "autotune_lookup", "autotune_set",
+           "evolve_backward", "EvolveFn", "batch_evolve", "autotune", "autotune_lookup", "autotune_set", "batch_autotune", "batch_autotune_set",
            "workspace_size", "launch_count", "timing_enable", "timing_read", "phases_enable", "phases_read",
            "device_check", "sync_status", "obs_stride", "PRECISIONS", "TC_FP64", "TC_BF16X3", "TC_TF32",
            "TC_TF32X3", "TC_COUPLING_BOSONIC", "TC_COUPLING_QUBIT_PHOTON", "TC_OP_EXPM", "TC_OP_EVOLVE",

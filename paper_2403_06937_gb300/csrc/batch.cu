@@ -1,6 +1,7 @@
 // batch.cu -- many independent systems of uneven size stepped together
 // (tc_batch_evolve).  The tensor-core forms run each product of a step as one
-// persistent launch over the tiles of every system (cgemm_batch.cu); the FP64
+// persistent launch over the tiles of every system (cgemm_batch.cu; single
+// CTAs or CTA pairs, the autotuner's tile shape); the FP64
 // form runs the systems' DMMA products one after another.  The whole step
 // loop is captured into one CUDA graph on a library stream and launched once.
 #include <algorithm>
@@ -116,7 +117,15 @@ TC_API tc_status tc_batch_evolve(int count, const int* n, const void* const* U, 
     std::vector<F64Sys> fb(count);
     double* f64_partial = nullptr;   // split-K scratch shared by the FP64 products
     std::vector<BatchSys> host(count);
-    int tiles[2] = {0, 0};
+    // tile shape and raster group: tc_batch_autotune's choice for a batch of this composition, else the
+    // autotuner's choice for the largest system (most of the work)
+    BatchPlan plan = batch_plan(precision, n[order[0]]);
+    TuneChoice tuned{};
+    if (precision != TC_FP64 && tune_batch_lookup(count, n, precision, &tuned)) {
+        plan.shape = cgemm_resolve_shape(tuned.tc_shape);
+        plan.group = tuned.tc_group;
+        plan.rb = plan.shape == kShapePairWide ? cgemm_pair_rows(precision) : 32;
+    }
     auto observe = [&](int k, int row) -> tc_status {
         const int b = order[k];
         if (!obs || !obs[b]) return TC_OK;
@@ -152,8 +161,8 @@ TC_API tc_status tc_batch_evolve(int count, const int* n, const void* const* U, 
                     TC_TRY(launch_renormalise(kRhoPlanarF64, f.Rr, f.Ri, f.n, f.scratch, s));
             }
         } else {
-            TC_TRY(cgemm_batch(precision, 0, sys_dev, count, tiles[0], status, s));
-            TC_TRY(cgemm_batch(precision, 1, sys_dev, count, tiles[1], status, s));
+            TC_TRY(cgemm_batch(precision, 0, sys_dev, count, plan, status, s));
+            TC_TRY(cgemm_batch(precision, 1, sys_dev, count, plan, status, s));
             if (renorm_every > 0 && step % renorm_every == 0)
                 for (int k = 0; k < count; k++) TC_TRY(lowp_renorm(precision, lb[k], s));
         }
@@ -190,17 +199,9 @@ TC_API tc_status tc_batch_evolve(int count, const int* n, const void* const* U, 
                 TC_TRY(lowp_prep(precision, static_cast<const double*>(U[b]), static_cast<const double*>(rho[b]), lb[k], s));
                 BatchSys& h = host[k];
                 std::memset(&h, 0, sizeof(h));
-                TC_TRY(make_part_map(&h.tmU, lb[k].Uparts, lb[k].Np, 2 * lb[k].S, precision));
-                TC_TRY(make_part_map(&h.tmR, lb[k].Rparts, lb[k].Np, 2 * lb[k].S, precision));
-                TC_TRY(make_part_map(&h.tmX, lb[k].Xparts, lb[k].Np, 2 * lb[k].S, precision));
+                TC_TRY(batch_plan_add(plan, h, precision, lb[k].Np, lb[k].Uparts, lb[k].Rparts, lb[k].Xparts));
                 h.Rr = lb[k].Rr; h.Ri = lb[k].Ri; h.Rparts = lb[k].Rparts;
                 h.Xr = lb[k].Xr; h.Xi = lb[k].Xi; h.Xparts = lb[k].Xparts;
-                h.Np = lb[k].Np;
-                h.tiles = lb[k].Np / 128;
-                h.tile_begin[0] = tiles[0];
-                h.tile_begin[1] = tiles[1];
-                tiles[0] += h.tiles * h.tiles;
-                tiles[1] += h.tiles * (h.tiles + 1) / 2;
             }
             TC_CUDA(cudaMemcpyAsync(sys_dev, host.data(), sizeof(BatchSys) * count, cudaMemcpyHostToDevice, s));
             TC_CUDA(cudaStreamSynchronize(s));   // host copy of the descriptors may go

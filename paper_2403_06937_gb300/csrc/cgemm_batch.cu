@@ -13,8 +13,15 @@
 // barriers for all its tiles.  The TMA ring and the MMA issue run continuously
 // across tile boundaries; the MMA issuer waits for the epilogue to release
 // TMEM (tmem_empty) before it starts the next tile's accumulation.
+//
+// This file holds the single-CTA shape (128 x 128 tiles, 32-byte K rows) and
+// the dispatch; the CTA-pair shapes are in cgemm_batch_pair.cu.  The shape
+// and the raster group come from the autotuner's choice for the batch's
+// largest n (batch_plan).
 #include "cgemm_batch.cuh"
 #include "cgemm_dev.cuh"
+#include "cgemm_tc.cuh"
+#include "kernels.cuh"
 
 namespace tc {
 namespace {
@@ -231,9 +238,47 @@ tc_status launch(const BatchSys* sys, int nsys, int ntiles, unsigned* status, cu
 
 }  // namespace
 
-tc_status cgemm_batch(int precision, int mode, const BatchSys* sys_dev, int nsys, int ntiles, unsigned* status,
-                      cudaStream_t s) {
+BatchPlan batch_plan(int precision, int n) {
+    const TuneChoice c = tune_lookup(n, precision);
+    BatchPlan p{};
+    p.shape = cgemm_resolve_shape(c.tc_shape);
+    p.group = c.tc_group;
+    p.rb = p.shape == kShapePairWide ? cgemm_pair_rows(precision) : 32;
+    return p;
+}
+
+tc_status batch_plan_add(BatchPlan& plan, BatchSys& h, int precision, int Np, const void* Uparts,
+                         const void* Rparts, const void* Xparts) {
+    if (Np < 128 || Np % 128 != 0) return fail(TC_ERR_INVALID_ARG, "batch: padded dimension %d", Np);
+    const int planes = 2 * cgemm_parts(precision);
+    TC_TRY(make_part_map(&h.tmU, Uparts, Np, planes, precision));
+    TC_TRY(make_part_map(&h.tmR, Rparts, Np, planes, precision));
+    TC_TRY(make_part_map(&h.tmX, Xparts, Np, planes, precision));
+    const int rb = plan.rb == 32 ? cgemm_pair_rows(precision) : plan.rb;   // maps unused at 32 bytes
+    TC_TRY(make_part_map_rows(&h.tmU_w, Uparts, Np, planes, precision, rb));
+    TC_TRY(make_part_map_rows(&h.tmR_w, Rparts, Np, planes, precision, rb));
+    TC_TRY(make_part_map_rows(&h.tmX_w, Xparts, Np, planes, precision, rb));
+    h.Np = Np;
+    h.tiles = Np / 128;
+    for (int mode = 0; mode < 2; mode++) {
+        h.tile_begin[mode] = plan.tiles[mode];
+        h.unit_begin[mode] = plan.units[mode];
+    }
+    plan.tiles[0] += h.tiles * h.tiles;
+    plan.tiles[1] += h.tiles * (h.tiles + 1) / 2;
+    plan.units[0] += (int)pair_units(0, h.tiles);
+    plan.units[1] += (int)pair_units(1, h.tiles);
+    return TC_OK;
+}
+
+tc_status cgemm_batch(int precision, int mode, const BatchSys* sys_dev, int nsys, const BatchPlan& plan,
+                      unsigned* status, cudaStream_t s) {
     if (mode != 0 && mode != 1) return fail(TC_ERR_INVALID_ARG, "cgemm_batch: mode");
+    if (plan.shape == kShapePair32 || plan.shape == kShapePairWide) {
+        const int G = plan.group > 1 ? plan.group / 2 : 1;
+        return cgemm_batch_pairs(precision, mode, plan.rb, sys_dev, nsys, plan.units[mode], G, status, s);
+    }
+    const int ntiles = plan.tiles[mode];
     switch (precision) {
         case TC_BF16X3:
             return mode == 0 ? launch<0, 3, 4, 0>(sys_dev, nsys, ntiles, status, s)

@@ -21,6 +21,20 @@ constexpr int kATile = 128 * kRowBytes;       // 4 KB
 constexpr int kBTile = 256 * kRowBytes;       // 8 KB
 constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s per wait
 
+// CTA pairs on the 2-SM MMA: a stage of each CTA holds its own S parts of
+// U_r and U_i rows and one half of every B part, 3 S tiles of 128 rows x RB
+// bytes of K (RB = 32, 64 or 128, with the matching TMA swizzle), and the
+// ring holds as many stages as fit in kSplitPairRing bytes.
+constexpr int kSplitPairRing = 216 * 1024;
+template <int S, int RB>
+constexpr int split_pair_stages() {
+    return kSplitPairRing / (3 * S * 128 * RB);
+}
+template <int S, int RB>
+constexpr int split_pair_smem() {
+    return split_pair_stages<S, RB>() * 3 * S * 128 * RB + 1024 /*align*/ + 512 /*barriers*/;
+}
+
 template <int S>
 struct Pairs;
 template <>

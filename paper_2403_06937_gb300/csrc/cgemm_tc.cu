@@ -219,20 +219,14 @@ tc_status launch(const CUtensorMap& tmU, const CUtensorMap& tmP, const CgemmEpi&
 // the odd one a fixed 1 ms), the MMA thread waits for its MMAs, and both
 // meet at a cluster barrier before TMEM is freed.
 // RB: bytes of K per operand row in a stage (32, 64 or 128, with the matching
-// TMA swizzle): a stage is 3 S tiles of 128 RB bytes and RB / 32 MMA K steps;
-// the ring holds as many stages as fit in kPairRing bytes.
-constexpr int kPairRing = 216 * 1024;
-
-template <int S, int RB>
-constexpr int pair_stages() {
-    return kPairRing / (3 * S * 128 * RB);
-}
+// TMA swizzle): a stage is 3 S tiles of 128 RB bytes and RB / 32 MMA K steps
+// (split_pair_stages, cgemm_dev.cuh).
 
 template <int KIND, int S, int RB, int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
     cgemm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmU, const __grid_constant__ CUtensorMap tmP,
                          CgemmEpi ep) {
-    constexpr int STAGES = pair_stages<S, RB>();
+    constexpr int STAGES = split_pair_stages<S, RB>();
     static_assert(STAGES >= 2, "ring too small for this row width");
     constexpr int kTile = 128 * RB;          // one 128-row operand tile
     constexpr int kStage = 3 * S * kTile;    // own U_r, U_i parts + own half of each B part
@@ -400,15 +394,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
-template <int S, int RB>
-constexpr int pair_smem_bytes() {
-    return pair_stages<S, RB>() * 3 * S * 128 * RB + 1024 /*align*/ + 512 /*barriers*/;
-}
-
 template <int KIND, int S, int RB, int MODE>
 tc_status launch_pair(const CUtensorMap& tmU, const CUtensorMap& tmP, const CgemmEpi& ep, cudaStream_t s) {
     auto k = cgemm_tc_pair_kernel<KIND, S, RB, MODE>;
-    constexpr int smem = pair_smem_bytes<S, RB>();
+    constexpr int smem = split_pair_smem<S, RB>();
     static bool attr_set[64] = {};
     int dev = 0;
     TC_CUDA(cudaGetDevice(&dev));
@@ -440,19 +429,24 @@ tc_status launch_pair(const CUtensorMap& tmU, const CUtensorMap& tmP, const Cgem
 namespace {
 std::atomic<int> g_inject_count{0};
 std::atomic<unsigned long long> g_inject_wait{0};
-// -1: not read yet; else TC_GEMM_PAIRS from the environment (0: single CTAs
-// at every size; anything else, or unset: CTA pairs wherever they apply)
+// -1: not read yet; else TC_GEMM_PAIRS from the environment (0: kShapeAuto
+// resolves to single CTAs; anything else, or unset: to CTA pairs)
 std::atomic<int> g_pairs{-1};
 }  // namespace
 
-bool cgemm_use_pairs(int tiles, int mode, int lo, int hi) {
+int cgemm_resolve_shape(int shape) {
+    if (shape == kShapeSingle || shape == kShapePair32 || shape == kShapePairWide) return shape;
     int v = g_pairs.load();
     if (v < 0) {
         const char* e = std::getenv("TC_GEMM_PAIRS");
         v = e && std::atoi(e) == 0 ? 0 : 1;
         g_pairs.store(v);
     }
-    if (v == 0 || tiles < 2 || tiles % 2 != 0) return false;
+    return v == 0 ? kShapeSingle : kShapePairWide;
+}
+
+bool cgemm_use_pairs(int tiles, int mode, int lo, int hi) {
+    if (tiles < 2 || tiles % 2 != 0) return false;
     // a Hermitian launch over a row band needs whole row pairs
     return !(mode == 1 && hi > 0 && (lo % 2 != 0 || hi % 2 != 0));
 }
@@ -501,9 +495,13 @@ tc_status cgemm_tc(int precision, int mode, const CUtensorMap& tmU, const CUtens
     const bool alt = stages == cgemm_alt_stages(precision);
     if (!alt && stages != cgemm_default_stages(precision))
         return fail(TC_ERR_INVALID_ARG, "cgemm_tc: %d stages not built for precision %d", stages, precision);
-    if (cgemm_use_pairs(ep.tiles, mode, ep.lo, ep.hi)) {
-        // CTA pairs: rows of cgemm_pair_rows() bytes when the caller gave maps of that width, else of 32 bytes
-        const bool wide = tmU_w && tmP_w && cgemm_pair_rows(precision) != 32;
+    if (ep.shape < kShapeAuto || ep.shape > kShapePairWide)
+        return fail(TC_ERR_INVALID_ARG, "cgemm_tc: tile shape %d", ep.shape);
+    const int shape = cgemm_resolve_shape(ep.shape);
+    if (shape != kShapeSingle && cgemm_use_pairs(ep.tiles, mode, ep.lo, ep.hi)) {
+        // CTA pairs: rows of cgemm_pair_rows() bytes when wide and the caller gave maps of that width,
+        // else of 32 bytes
+        const bool wide = shape == kShapePairWide && tmU_w && tmP_w && cgemm_pair_rows(precision) != 32;
         const CUtensorMap& u = wide ? *tmU_w : tmU;
         const CUtensorMap& p = wide ? *tmP_w : tmP;
         const int rb = wide ? cgemm_pair_rows(precision) : 32;

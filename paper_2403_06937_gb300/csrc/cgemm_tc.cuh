@@ -30,7 +30,23 @@ struct CgemmEpi {
     int lo, hi;                   // hi > 0: only the tile columns [lo, hi) (mode 0) or the
                                   // block-lower tiles of the tile rows [lo, hi) (mode 1; lo a
                                   // multiple of group, hi a multiple of group or tiles)
+    int shape;                    // tile shape (kShape*; 0 = kShapeAuto)
 };
+
+// Tile shape of a tensor-core product launch (the autotuner's choice).  Every
+// shape accumulates each output element in the same order (K slice by K
+// slice, the part products in one fixed order), so the shape changes speed,
+// not results.
+//  kShapeSingle:   one CTA per complex 128 x 128 tile (M = 128 MMAs), 32 bytes
+//                  of K per operand row in a stage;
+//  kShapePair32:   CTA pairs on the 2-SM MMA (M = 256: a 256 x 128 complex
+//                  tile per cluster of two), 32-byte K rows;
+//  kShapePairWide: CTA pairs with cgemm_pair_rows(precision)-byte K rows;
+//  kShapeAuto:     kShapeSingle if TC_GEMM_PAIRS=0 is in the environment,
+//                  else kShapePairWide.
+// A pair shape runs as single CTAs where pairs do not apply (cgemm_use_pairs).
+enum : int { kShapeAuto = 0, kShapeSingle = 1, kShapePair32 = 2, kShapePairWide = 3 };
+int cgemm_resolve_shape(int shape);
 
 // stages: TMA ring depth (0 = the largest that fits); the built depths are
 // BF16x3 {4, 3}, TF32 {8, 4}, TF32x3 {6, 3}.
@@ -45,8 +61,8 @@ tc_status cgemm_tc(int precision, int mode, const CUtensorMap& tmU, const CUtens
 int cgemm_pair_rows(int precision);
 int cgemm_default_stages(int precision);
 // True when a launch of `tiles` tiles a side (and the range lo, hi of
-// CgemmEpi) runs as CTA pairs on the 2-SM MMA: an even tile count, whole row
-// pairs in a Hermitian row band, and TC_GEMM_PAIRS not 0 in the environment.
+// CgemmEpi) can run as CTA pairs on the 2-SM MMA: an even tile count and
+// whole row pairs in a Hermitian row band.
 bool cgemm_use_pairs(int tiles, int mode, int lo, int hi);
 int cgemm_alt_stages(int precision);
 

@@ -39,16 +39,55 @@ unsigned grid_for(size_t work) {
     return (unsigned)(want < cap ? (want ? want : 1) : cap);
 }
 
-// parts of a double (V): v is first held as an FP32 pair hi + lo (hi = v
-// rounded, lo = the rest rounded; |v - hi - lo| <= 2^-48 |v|), then split in
-// FP32 arithmetic: BF16 parts b0 = RN(hi), b1 = RN((hi - b0) + lo),
-// b2 = RN(r - b1) (hi - b0 and r - b1 are exact), TF32 parts likewise.  The
-// parts represent v to about 2^-26 |v|, as an FP64 split would (~2^-27), with
-// three FP64 operations per value instead of two per part.
+// v as an FP32 pair hi + lo read off its bit fields, with no FP64
+// instruction (GB300 issues FP64 at a small fraction of its FP32 rate):
+// hi = v truncated to FP32's 24 significand bits, lo = the 29 bits below
+// them rounded to 24, so |v - hi - lo| <= 2^-47 |v|.  |v| < 2^-126 (zero,
+// the smallest normals and FP64 subnormals) gives a signed zero hi and lo = 0,
+// |v| >= 2^128 an infinite hi, NaN a NaN.
+__device__ __forceinline__ void f64_pair(double v, float& hi, float& lo) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+    const int e = (int)((b >> 52) & 0x7FFu) - 1023;
+    const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+    lo = 0.0f;
+    if (e < -126) {
+        hi = __uint_as_float(sign);
+        return;
+    }
+    if (e > 127) {
+        hi = __uint_as_float(sign | 0x7F800000u | (e == 1024 && m ? 0x400000u : 0u));
+        return;
+    }
+    hi = __uint_as_float(sign | ((unsigned)(e + 127) << 23) | (unsigned)(m >> 29));
+    // bit 0 of m is worth 2^(e - 52): scale by two powers of two, each a normal FP32
+    const int q = (e - 52) >> 1, r = (e - 52) - q;
+    const float low = __uint2float_rn((unsigned)(m & 0x1FFFFFFFu)) * __uint_as_float((unsigned)(q + 127) << 23) *
+                      __uint_as_float((unsigned)(r + 127) << 23);
+    lo = sign ? -low : low;
+}
+
+// a + b = s + err exactly (Knuth's two-sum; no product, so nothing is contracted)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& err) {
+    s = a + b;
+    const float bb = s - a;
+    err = (a - (s - bb)) + (b - bb);
+}
+
+// (ah + al)(bh + bl) = p + e to about 2^-46 relative (al bl dropped); p = RN(ah bh), its
+// rounding error recovered exactly by the FMA
+__device__ __forceinline__ void pair_mul(float ah, float al, float bh, float bl, float& p, float& e) {
+    p = ah * bh;
+    e = fmaf(ah, bh, -p);
+    e = fmaf(ah, bl, e);
+    e = fmaf(al, bh, e);
+}
+
+// parts of a value held as the FP32 pair hi + lo: BF16 parts b0 = RN(hi),
+// b1 = RN((hi - b0) + lo), b2 = RN(r - b1) (hi - b0 and r - b1 exact), TF32
+// parts likewise; they represent hi + lo to about 2^-26 of its size.
 template <int KIND, int S>
-__device__ __forceinline__ void split_f64(double v, void* base, size_t plane, size_t idx, int part) {
-    const float hi = (float)v;
-    const float lo = (float)(v - (double)hi);
+__device__ __forceinline__ void split_pair(float hi, float lo, void* base, size_t plane, size_t idx, int part) {
     if constexpr (KIND == 0) {
         __nv_bfloat16* p = static_cast<__nv_bfloat16*>(base);
         float r = hi;
@@ -98,24 +137,51 @@ __global__ void unit_phase_kernel(const double2* U, int N, double* out) {
     }
 }
 
-// V = U conj(c) - I (zero in the padding), formed in FP64 and split into
-// operand parts; blocks take rows, threads columns (no index division)
+// V = U conj(c) - I (zero in the padding), formed in FP32-pair arithmetic
+// (U's entries and c read off as FP32 pairs, products by FMA, sums by
+// two-sum: about 2^-44 relative, far below the parts' 2^-26) and split into
+// operand parts; blocks take rows, threads columns (no index division), four
+// loads in flight per thread.
 template <int KIND, int S>
 __global__ void prep_u_kernel(const double2* U, int N, int Np, const double* phase, void* parts) {
     const size_t plane = (size_t)Np * Np;
-    const double cr = phase[0], ci = -phase[1];
+    float crh, crl, cih, cil;   // conj(c) = cr + i ci
+    f64_pair(phase[0], crh, crl);
+    f64_pair(-phase[1], cih, cil);
     for (int i = blockIdx.x; i < Np; i += gridDim.x) {
-        for (int j = threadIdx.x; j < Np; j += blockDim.x) {
-            const size_t e = (size_t)i * Np + j;
-            double vr = 0.0, vi = 0.0;
-            if (i < N && j < N) {
-                const double2 u = U[(size_t)i * N + j];
-                vr = u.x * cr - u.y * ci;
-                vi = u.x * ci + u.y * cr;
-                if (i == j) vr -= 1.0;
+        for (int j0 = threadIdx.x; j0 < Np; j0 += 4 * blockDim.x) {
+            double2 u[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const int j = j0 + k * blockDim.x;
+                u[k] = (i < N && j < N) ? U[(size_t)i * N + j] : make_double2(0.0, 0.0);
             }
-            split_f64<KIND, S>(vr, parts, plane, e, 0);
-            split_f64<KIND, S>(vi, parts, plane, e, 1);
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const int j = j0 + k * blockDim.x;
+                if (j >= Np) break;
+                float xh, xl, yh, yl;
+                f64_pair(u[k].x, xh, xl);
+                f64_pair(u[k].y, yh, yl);
+                float p1, e1, p2, e2, p3, e3, p4, e4;
+                pair_mul(xh, xl, crh, crl, p1, e1);   // Re u cr
+                pair_mul(yh, yl, cih, cil, p2, e2);   // Im u ci
+                pair_mul(xh, xl, cih, cil, p3, e3);   // Re u ci
+                pair_mul(yh, yl, crh, crl, p4, e4);   // Im u cr
+                float vr, tr, vi, ti;
+                two_sum(p1, -p2, vr, tr);
+                tr += e1 - e2;
+                two_sum(p3, p4, vi, ti);
+                ti += e3 + e4;
+                if (i == j && i < N) {
+                    float d;
+                    two_sum(vr, -1.0f, vr, d);
+                    tr += d;
+                }
+                const size_t e = (size_t)i * Np + j;
+                split_pair<KIND, S>(vr, tr, parts, plane, e, 0);
+                split_pair<KIND, S>(vi, ti, parts, plane, e, 1);
+            }
         }
     }
 }
@@ -186,9 +252,10 @@ __global__ void trace_f32_kernel(const float* Rr, int N, int Np, double* out) {
 
 // rows [r0, r1) of the N x N result; blocks take rows, threads columns (rho
 // may be page-locked host memory written through its device mapping)
-__global__ void finish_kernel(const float* Rr, const float* Ri, int N, int Np, int r0, int r1, double2* rho) {
+__global__ void finish_kernel(const float* Rr, const float* Ri, int N, int Np, int r0, int r1, int c0, int c1,
+                              double2* rho) {
     for (int i = r0 + blockIdx.x; i < r1; i += gridDim.x)
-        for (int j = threadIdx.x; j < N; j += blockDim.x)
+        for (int j = c0 + threadIdx.x; j < c1; j += blockDim.x)
             rho[(size_t)i * N + j] = make_double2((double)Rr[(size_t)i * Np + j], (double)Ri[(size_t)i * Np + j]);
 }
 
@@ -284,11 +351,13 @@ tc_status lowp_prep_rho(int precision, const double* rho, LowpBufs& b, int r0, i
     return fail(TC_ERR_INVALID_ARG, "precision");
 }
 
-tc_status lowp_finish(const LowpBufs& b, double* rho, cudaStream_t s, int r0, int r1, unsigned cap) {
+tc_status lowp_finish(const LowpBufs& b, double* rho, cudaStream_t s, int r0, int r1, unsigned cap, int c0, int c1) {
     if (r1 < 0) r1 = b.N;
+    if (c1 < 0) c1 = b.N;
     if (r0 < 0 || r0 >= r1 || r1 > b.N) return fail(TC_ERR_INVALID_ARG, "finish: row range");
-    finish_kernel<<<rows_grid(r1 - r0, (size_t)(r1 - r0) * b.N, cap), 256, 0, s>>>(b.Rr, b.Ri, b.N, b.Np, r0, r1,
-                                                                                   reinterpret_cast<double2*>(rho));
+    if (c0 < 0 || c0 >= c1 || c1 > b.N) return fail(TC_ERR_INVALID_ARG, "finish: column range");
+    finish_kernel<<<rows_grid(r1 - r0, (size_t)(r1 - r0) * (c1 - c0), cap), 256, 0, s>>>(
+        b.Rr, b.Ri, b.N, b.Np, r0, r1, c0, c1, reinterpret_cast<double2*>(rho));
     TC_LAUNCH_CHECK();
     return TC_OK;
 }
@@ -350,6 +419,7 @@ tc_status plan_step(int n, int precision, const LowpBufs& b, StepPlan& p) {
     p.e1.Np = b.Np;
     p.e1.tiles = b.Np / 128;
     p.e1.group = p.tune.tc_group;
+    p.e1.shape = p.tune.tc_shape;
     p.e1.pr = b.Rr;
     p.e1.pi = b.Ri;
     p.e1.parts = b.Xparts;
@@ -421,20 +491,36 @@ int lowp_host_chunks(int n, int precision) {
     return T % (4 * G) == 0 ? 4 : T % (2 * G) == 0 ? 2 : 1;
 }
 
+// Row bands of the last Hermitian product of a host-buffer call: more and
+// narrower than the row blocks in, so the bottom band is done (and its rows
+// start out) early and the top band's diagonal block, the only copy left
+// after the last product, is small.  A band holds whole raster groups and
+// whole row pairs.
+int lowp_host_bands(int n, int precision) {
+    const int N = 1 << n;
+    if (N < 2048) return 1;
+    const int T = N / 128;
+    int G = tune_lookup(n, precision).tc_group;
+    G = G < 1 ? 1 : G;
+    for (int C : {8, 4, 2})
+        if (T % (C * G) == 0 && (T / C) % 2 == 0) return C;
+    return 1;
+}
+
 namespace {
 
 // Streams and events of one pipelined call, released when it goes out of scope
 // (the device finishes the queued work first).
 struct CopyLane {
     cudaStream_t cs = nullptr;
-    cudaEvent_t ev[12] = {};
+    cudaEvent_t ev[24] = {};
     int used = 0;
     ~CopyLane() {
         for (int i = 0; i < used; i++) cudaEventDestroy(ev[i]);
         if (cs) cudaStreamDestroy(cs);
     }
     tc_status init(int events) {
-        if (events > 12) return fail(TC_ERR_INVALID_ARG, "copy lane: too many events");
+        if (events > 24) return fail(TC_ERR_INVALID_ARG, "copy lane: too many events");
         TC_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
         for (; used < events; used++) TC_CUDA(cudaEventCreateWithFlags(&ev[used], cudaEventDisableTiming));
         return TC_OK;
@@ -472,6 +558,7 @@ tc_status evolve_lowp_host_blocks(const double* U, double* rho_host, double* rho
     const size_t N = (size_t)1 << n;
     const size_t bytes = 16 * N * N;
     const int C = steps >= 1 ? lowp_host_chunks(n, precision) : 1;
+    const int CY = steps >= 1 ? lowp_host_bands(n, precision) : 1;
     // A page-locked rho_host is read and written by the SMs through its device
     // mapping (copy-engine transfers of host memory, reads above all, slow down
     // many-fold after heavy host CPU or memory activity; SM accesses keep
@@ -480,7 +567,7 @@ tc_status evolve_lowp_host_blocks(const double* U, double* rho_host, double* rho
     const void* mapped_v = nullptr;
     TC_TRY(host_mapping(rho_host, &mapped_v));
     double* mapped = const_cast<double*>(static_cast<const double*>(mapped_v));
-    if (C == 1) {
+    if (C == 1 || CY == 1) {
         if (mapped)
             TC_TRY(copy_by_sms(rho_dev, mapped, bytes, s));
         else
@@ -498,17 +585,20 @@ tc_status evolve_lowp_host_blocks(const double* U, double* rho_host, double* rho
     StepPlan sp{};
     TC_TRY(plan_step(n, precision, b, sp));
     const int T = b.Np / 128;
-    const size_t R = N / C;                  // rows per chunk
-    const size_t chunk = 16 * R * N;         // bytes per chunk
+    const size_t R = N / C;                  // rows per block in
+    const size_t chunk = 16 * R * N;         // bytes per block in
+    const size_t RY = N / CY;                // rows per band out
     const int stride = TC_OBS_STRIDE(n);
-    TC_TRY(lane.init(2 * C + 2));
-    cudaEvent_t* in = lane.ev;               // [C] rows of chunk c are in the FP32 planes (or the staging)
-    cudaEvent_t* fin = lane.ev + C;          // [C] rows of chunk c of rho' are final
-    cudaEvent_t start = lane.ev[2 * C], done = lane.ev[2 * C + 1];
+    TC_TRY(lane.init(C + CY + 2));
+    cudaEvent_t* in = lane.ev;               // [C] rows of block c are in the FP32 planes (or the staging)
+    cudaEvent_t* fin = lane.ev + C;          // [CY] the rows of band c of rho' are final
+    cudaEvent_t start = lane.ev[C + CY], done = lane.ev[C + CY + 1];
     auto dev_rows = [&](size_t c) { return reinterpret_cast<char*>(rho_dev) + c * chunk; };
     auto host_rows = [&](size_t c) { return reinterpret_cast<char*>(rho_host) + c * chunk; };
     auto rows_lo = [&](int c) { return (int)(c * R); };
     auto rows_hi = [&](int c) { return (int)((c + 1) * R); };
+    auto band_lo = [&](int c) { return (int)(c * RY); };
+    auto band_hi = [&](int c) { return (int)((c + 1) * RY); };
     // the SM reads of host rows run beside the first products: two CTAs per
     // SM keep the link busy without crowding the GEMM's CTAs
     int dev = 0, sms = 148;
@@ -551,10 +641,15 @@ tc_status evolve_lowp_host_blocks(const double* U, double* rho_host, double* rho
         TC_TRY(cgemm_tc(precision, 0, sp.tmU, sp.tmR, e, s, sp.tune.tc_stages, &sp.wU, &sp.wR));
         mark("x", c, s);
     }
-    // rows of chunk c of rho' out (their products done on s).  A mapped host
-    // buffer is written by the finish kernel on the copy stream, on a few
-    // CTAs while products still run beside it (half a CTA per SM; SM stores to
-    // host memory on more CTAs slowed the products by a quarter); otherwise the
+    // rho' out once its entries are final (their products done on s).  A
+    // mapped host buffer is written by the finish kernel on the copy stream,
+    // on a few CTAs while products still run beside it (half a CTA per SM; SM
+    // stores to host memory on more CTAs slowed the products by a quarter),
+    // as the blocks that the row band c's product has just made final: its
+    // own rows left of the band's right edge, and the rows above the band in
+    // its columns (the mirrored tiles); the rows of band c right of it were
+    // final, and went out, with the bands below.  So only the top band's
+    // diagonal block is left to copy after the last product.  Otherwise the
     // rows are converted on s into the staging and copied by the copy engine.
     // Copy-engine writes to host memory slow down after heavy host activity
     // too, though less often than its reads.
@@ -562,13 +657,17 @@ tc_status evolve_lowp_host_blocks(const double* U, double* rho_host, double* rho
         if (mapped) {
             TC_CUDA(cudaEventRecord(fin[c], s));
             TC_CUDA(cudaStreamWaitEvent(lane.cs, fin[c], 0));
-            // the top block goes out last, with nothing beside it: the full grid
-            TC_TRY(lowp_finish(b, mapped, lane.cs, rows_lo(c), rows_hi(c), c == 0 ? cap : out_cap));
+            // the top band's block goes out last, with nothing beside it: the full grid
+            const unsigned g = c == 0 ? cap : out_cap;
+            TC_TRY(lowp_finish(b, mapped, lane.cs, band_lo(c), band_hi(c), g, 0, band_hi(c)));
+            if (c > 0) TC_TRY(lowp_finish(b, mapped, lane.cs, 0, band_lo(c), g, band_lo(c), band_hi(c)));
         } else {
-            TC_TRY(lowp_finish(b, rho_dev, s, rows_lo(c), rows_hi(c)));
+            TC_TRY(lowp_finish(b, rho_dev, s, band_lo(c), band_hi(c)));
             TC_CUDA(cudaEventRecord(fin[c], s));
             TC_CUDA(cudaStreamWaitEvent(lane.cs, fin[c], 0));
-            TC_CUDA(cudaMemcpyAsync(host_rows(c), dev_rows(c), chunk, cudaMemcpyDeviceToHost, lane.cs));
+            char* off = reinterpret_cast<char*>(rho_dev) + 16 * (size_t)band_lo(c) * N;
+            char* hoff = reinterpret_cast<char*>(rho_host) + 16 * (size_t)band_lo(c) * N;
+            TC_CUDA(cudaMemcpyAsync(hoff, off, 16 * RY * N, cudaMemcpyDeviceToHost, lane.cs));
         }
         mark("d2h", c, lane.cs);
         return TC_OK;
@@ -585,15 +684,15 @@ tc_status evolve_lowp_host_blocks(const double* U, double* rho_host, double* rho
             if (k < steps) continue;
             // last step renormalised: rho' is whole only now; convert and copy out by row blocks
             mark("y", 0, s);
-            for (int c = 0; c < C; c++) TC_TRY(out_rows(c));
+            for (int c = 0; c < CY; c++) TC_TRY(out_rows(c));
             break;
         }
-        // last step, second product bottom-up by row blocks: once the tile rows >= lo are done
+        // last step, second product bottom-up by row bands: once the tile rows >= lo are done
         // (each tile writes itself and its mirror), the rows >= lo * 128 of rho' are final
-        for (int c = C - 1; c >= 0; c--) {
+        for (int c = CY - 1; c >= 0; c--) {
             CgemmEpi e = sp.e2;
-            e.lo = c * T / C;
-            e.hi = (c + 1) * T / C;
+            e.lo = c * T / CY;
+            e.hi = (c + 1) * T / CY;
             TC_TRY(cgemm_tc(precision, 1, sp.tmU, sp.tmX, e, s, sp.tune.tc_stages, &sp.wU, &sp.wX));
             mark("y", c, s);
             TC_TRY(out_rows(c));

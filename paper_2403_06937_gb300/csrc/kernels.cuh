@@ -59,10 +59,15 @@ size_t gemm_f64_splitk_bytes();
 struct TuneChoice {
     int f64_tile;    // FP64 DMMA GEMM tile: 32 or 64
     int tc_group;    // tensor-core GEMM: row tiles per raster group (L2 reuse of U panels)
-    int tc_stages;   // tensor-core GEMM: TMA ring depth
+    int tc_stages;   // tensor-core GEMM: TMA ring depth (single-CTA shape)
+    int tc_shape;    // tensor-core GEMM: tile shape (kShape* of cgemm_tc.cuh; 0 = automatic)
 };
 TuneChoice tune_lookup(int n, int precision);
+// the choice tc_batch_autotune made for a batch of this composition (false: none)
+bool tune_batch_lookup(int count, const int* n, int precision, TuneChoice* c);
 int tuned_f64_tile(int N);
+// bytes of tc_batch_evolve's workspace (batch.cu)
+size_t batch_bytes(int count, const int* n, int precision);
 
 // ---------------------------------------------------------------- elementwise
 // out = c0*I + sum_j c[j] * M_j (real N x N, up to 4 terms; M_j may alias out)

@@ -542,28 +542,21 @@ tc_status evolve_lowp_t(const Layout& L, const Model& m, int precision, double k
 
     // descriptors, blocks in decreasing size (the longest tiles first)
     std::vector<BatchSys> host(n + 1);
-    int tiles[2] = {0, 0};
+    // the tile shape and raster group the autotuner chose for the whole space's n
+    BatchPlan plan = batch_plan(precision, n);
     double flops = 0.0;
     for (int q = 0; q <= n; q++) {
         const int k = n - q;
         const int Np = bs.ld[k];
         BatchSys& h = host[q];
         std::memset(&h, 0, sizeof(h));
-        TC_TRY(make_part_map(&h.tmU, up.p[k], Np, 2 * S, precision));
-        TC_TRY(make_part_map(&h.tmR, rp.p[k], Np, 2 * S, precision));
-        TC_TRY(make_part_map(&h.tmX, xp.p[k], Np, 2 * S, precision));
+        TC_TRY(batch_plan_add(plan, h, precision, Np, up.p[k], rp.p[k], xp.p[k]));
         h.Rr = Rr + bs.off[k];
         h.Ri = Ri + bs.off[k];
         h.Rparts = rp.p[k];
         h.Xr = Xr + bs.off[k];
         h.Xi = Xi + bs.off[k];
         h.Xparts = xp.p[k];
-        h.Np = Np;
-        h.tiles = Np / 128;
-        h.tile_begin[0] = tiles[0];
-        h.tile_begin[1] = tiles[1];
-        tiles[0] += h.tiles * h.tiles;
-        tiles[1] += h.tiles * (h.tiles + 1) / 2;
         flops += 12.0 * (double)L.dims[k] * L.dims[k] * L.dims[k];
     }
     const double prod = (double)cgemm_products(precision);
@@ -572,11 +565,11 @@ tc_status evolve_lowp_t(const Layout& L, const Model& m, int precision, double k
         if (damp) TC_TRY((launch_damping<float, KIND, S>(L, bs, kappa, 0.5 * dt, t, Rr, Ri, rp, cs)));
         {
             ProductTimer pt(flops * prod * (8.0 / 12.0), cs);   // X_k = U_k rho_k, every block
-            TC_TRY(cgemm_batch(precision, 0, sys_dev, n + 1, tiles[0], status, cs));
+            TC_TRY(cgemm_batch(precision, 0, sys_dev, n + 1, plan, status, cs));
         }
         {
             ProductTimer pt(flops * prod * (4.0 / 12.0), cs);   // rho_k = X_k U_k^dag, Hermitian halves
-            TC_TRY(cgemm_batch(precision, 1, sys_dev, n + 1, tiles[1], status, cs));
+            TC_TRY(cgemm_batch(precision, 1, sys_dev, n + 1, plan, status, cs));
         }
         if (damp) TC_TRY((launch_damping<float, KIND, S>(L, bs, kappa, 0.5 * dt, t, Rr, Ri, rp, cs)));
         if (renorm_every > 0 && k % renorm_every == 0)

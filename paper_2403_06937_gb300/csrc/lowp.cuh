@@ -63,7 +63,9 @@ tc_status lowp_prep_u(int precision, const double* U, LowpBufs& b, cudaStream_t 
 // (cap > 0: at most `cap` CTAs)
 tc_status lowp_prep_rho(int precision, const double* rho, LowpBufs& b, int r0, int r1, cudaStream_t s,
                         unsigned cap = 0);
-// FP32 planes -> interleaved complex128 rho (N x N), rows [r0, r1) (r1 < 0: N)
-tc_status lowp_finish(const LowpBufs& b, double* rho, cudaStream_t s, int r0 = 0, int r1 = -1, unsigned cap = 0);
+// FP32 planes -> interleaved complex128 rho (N x N), rows [r0, r1) (r1 < 0:
+// N), columns [c0, c1) (c1 < 0: N); cap > 0: at most `cap` CTAs
+tc_status lowp_finish(const LowpBufs& b, double* rho, cudaStream_t s, int r0 = 0, int r1 = -1, unsigned cap = 0,
+                      int c0 = 0, int c1 = -1);
 
 }  // namespace tc

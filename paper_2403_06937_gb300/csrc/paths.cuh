@@ -44,13 +44,14 @@ tc_status evolve_lowp(const double* U, double* rho, int n, int steps, int precis
                       const Model* m, double* obs, Arena& ar, cudaStream_t s);
 // tc_evolve_host for the tensor-core forms: rho_host copied in by row blocks
 // (the first product starts on the column blocks whose rows have arrived) and
-// out by row blocks (the last second product runs bottom-up, each finished
-// block converted and copied while the rows above are computed), on a copy
-// stream of its own; rho_dev is the N x N complex128 staging.  Sizes without
-// 4 (or 2) group-aligned blocks, or N < 2048, copy whole around the loop.
+// out by row bands (the last second product runs bottom-up, each band's
+// finished entries converted and copied while the rows above are computed),
+// on a copy stream of its own; rho_dev is the N x N complex128 staging.
+// Sizes without group-aligned blocks, or N < 2048, copy whole around the loop.
 tc_status evolve_lowp_host(const double* U, double* rho_host, double* rho_dev, int n, int steps, int precision,
                            int renorm_every, const Model* m, double* obs, Arena& ar, cudaStream_t s);
-int lowp_host_chunks(int n, int precision);
+int lowp_host_chunks(int n, int precision);   // row blocks in (4, 2 or 1)
+int lowp_host_bands(int n, int precision);    // row bands out (8, 4, 2 or 1)
 
 // Open-system form (packed excitation blocks).
 size_t lindblad_bytes(int n, int precision);

@@ -125,5 +125,48 @@ TC_HD inline long pair_count(int mode, int T, int lo, int hi) {
     return p1 * (p1 + 1) - p0 * (p0 + 1);
 }
 
+// The CTA-pair units of one system in a batched launch, for any T >= 1:
+// row pairs (2p, 2p + 1), p < ceil(T / 2); for an odd T the odd CTA's row
+// 2p + 1 = T of the last pair lies outside the matrix (its operand loads read
+// zeros and its tile is not written).  Row pairs go in groups of G, column by
+// column inside a group (as pair_tile_rows).
+//  mode 0: every column of every row pair;
+//  mode 1: the columns J <= min(2p + 1, T - 1) of row pair p (the tile
+//  (2p, 2p + 1) above the diagonal is computed and not written).
+TC_HD inline long pair_units(int mode, int T) {
+    const long TP = (T + 1) / 2;
+    if (mode == 0) return TP * T;
+    return T % 2 == 0 ? TP * (TP + 1) : (TP - 1) * TP + T;
+}
+
+TC_HD inline void pair_unit(int mode, int T, int G, int q, int rank, int& I, int& J) {
+    const int TP = (T + 1) / 2;
+    if (G < 1) G = 1;
+    if (mode == 0) {
+        const int per_group = G * T;
+        const int g = q / per_group;
+        const int rows = tile_min(G, TP - g * G);
+        const int in = q % per_group;
+        I = 2 * (g * G + in % rows) + rank;
+        J = in / rows;
+        return;
+    }
+    for (int p0 = 0; p0 < TP; p0 += G) {
+        const int last = p0 + tile_min(G, TP - p0) - 1;
+        const int jmax = tile_min(2 * last + 1, T - 1);
+        for (int j = 0; j <= jmax; j++) {
+            const int first = p0 > j / 2 ? p0 : j / 2;
+            const int c = last - first + 1;
+            if (q < c) {
+                I = 2 * (first + q) + rank;
+                J = j;
+                return;
+            }
+            q -= c;
+        }
+    }
+    I = J = 0;   // not reached for q below pair_units(mode, T)
+}
+
 }  // namespace cg
 }  // namespace tc

@@ -1,9 +1,10 @@
 """tc_evolve_host with the tensor-core forms overlaps its transfers with the
 first and last products: rho comes in by row blocks on a copy stream, the
 first product of step 1 runs by column blocks as their rows arrive, and the
-second product of the last step runs bottom-up by row blocks, each finished
-block converted and written out while the rows above are computed (2 or 4
-blocks from n = 11; below that, whole copies around the loop).  A
+second product of the last step runs bottom-up by row bands, the entries
+each band makes final converted and written out while the rows above are
+computed (2 or 4 row blocks in and 2 to 8 row bands out from n = 11; below
+that, whole copies around the loop).  A
 page-locked rho_host is read and written by the SMs through its device
 mapping; a pageable one goes through the copy engine and the device
 staging.  The blocks run the same tile computations as the whole launches,
@@ -38,7 +39,8 @@ def tc():
     (12, "tf32x3", 2, 2, True),      # renormalised at the last step: blocks only for the way out
     (12, "tf32x3", 2, 2, False),
     (12, "tf32", 3, 0, True),
-    (13, "bf16x3", 2, 0, True),
+    (13, "bf16x3", 2, 0, True),      # 4 blocks in, 8 bands out
+    (13, "bf16x3", 1, 0, False),
     (9, "fp64", 2, 0, True),
     (9, "fp64", 2, 0, False),
 ])

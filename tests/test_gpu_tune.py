@@ -39,6 +39,7 @@ def test_tuning_changes_speed_not_results(tc, precision):
     else:
         assert choice["tc_group"] in (4, 8, 12, 16)
         assert choice["tc_stages"] in {"bf16x3": (4, 3), "tf32x3": (6, 3), "tf32": (8, 4)}[precision]
+        assert choice["tc_shape"] in (1, 2, 3)
     after, oa = tc.evolve(U, r0, n, 3, precision, params=p)
     assert torch.equal(before, after) and torch.equal(ob, oa)
 

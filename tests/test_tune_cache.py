@@ -19,12 +19,13 @@ print(json.dumps([tc.autotune_lookup(11, 'bf16x3'), tc.autotune_lookup(11, 'fp64
 def test_cache_file_is_read_on_first_lookup(tmp_path):
     cache = tmp_path / "tune.jsonl"
     # arch 0: the key a process without a CUDA device looks up
-    cache.write_text('{"arch": 0, "n": 11, "precision": 1, "f64_tile": 64, "tc_group": 16, "tc_stages": 3, "ms": 1.0}\n'
+    cache.write_text('{"arch": 0, "n": 11, "precision": 1, "f64_tile": 64, "tc_group": 16, "tc_stages": 3, '
+                     '"tc_shape": 2, "ms": 1.0}\n'
                      '{"arch": 0, "n": 11, "precision": 0, "f64_tile": 64, "tc_group": 8, "tc_stages": 0, "ms": 2.0}\n'
                      'not json\n')
     env = dict(os.environ, TC_AUTOTUNE_CACHE=str(cache))
     out = subprocess.run([sys.executable, "-c", SCRIPT % ROOT], env=env, capture_output=True, text=True, check=True)
     a, b, c = json.loads(out.stdout.strip().splitlines()[-1])
-    assert a == {"f64_tile": 64, "tc_group": 16, "tc_stages": 3}
-    assert b["f64_tile"] == 64
-    assert c["tc_group"] == 8 and c["tc_stages"] == 4      # untuned: the defaults
+    assert a == {"f64_tile": 64, "tc_group": 16, "tc_stages": 3, "tc_shape": 2}
+    assert b["f64_tile"] == 64 and b["tc_shape"] == 0       # a line without a shape: automatic
+    assert c["tc_group"] == 8 and c["tc_stages"] == 4 and c["tc_shape"] == 0   # untuned: the defaults

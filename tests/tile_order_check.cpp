@@ -4,7 +4,9 @@
 // the same tiles as the whole launch.
 //   single CTAs, mode 0: columns [lo, hi) of T x T; mode 1: block-lower tiles
 //     of the tile rows [lo, hi) (lo a multiple of G, hi of G or T);
-//   CTA pairs sharing P (pair_tile_rows): both CTAs in one column tile.
+//   CTA pairs sharing P (pair_tile_rows): both CTAs in one column tile;
+//   the batched CTA-pair units (pair_unit, any T): the written tiles (inside
+//   the grid, not above the diagonal in mode 1) are each tile owned, once.
 // Prints one line per failure and exits 1 if there was any.
 #include <cstdio>
 #include <set>
@@ -16,6 +18,8 @@
 using tc::cg::pair_count;
 using tc::cg::pair_tile_rows;
 using tc::cg::pair_tile_rows_range;
+using tc::cg::pair_unit;
+using tc::cg::pair_units;
 using tc::cg::tile_of;
 using tc::cg::tile_of_range;
 
@@ -118,6 +122,29 @@ static void check_pairs(int T, int G) {
     }
 }
 
+static void check_units(int T, int G) {
+    for (int mode = 0; mode < 2; mode++) {
+        // count by the definition: ceil(T / 2) row pairs, mode 1 with columns J <= min(2p + 1, T - 1)
+        long units = 0;
+        for (int p = 0; p < (T + 1) / 2; p++) units += mode == 0 ? T : (2 * p + 2 < T ? 2 * p + 2 : T);
+        if (pair_units(mode, T) != units) fail("pair_units", T, G, mode, (int)pair_units(mode, T), (int)units);
+        std::set<std::pair<int, int>> written;
+        for (long q = 0; q < units; q++) {
+            int I0, J0, I1, J1;
+            pair_unit(mode, T, G, (int)q, 0, I0, J0);
+            pair_unit(mode, T, G, (int)q, 1, I1, J1);
+            if (J0 != J1 || J0 < 0 || J0 >= T) fail("pair_unit: column tile", T, G, mode, J0, J1);
+            if (I1 != I0 + 1 || I0 % 2 != 0 || I0 < 0 || I0 >= T || I1 > T)
+                fail("pair_unit: not an even/odd row pair inside the grid", T, G, mode, I0, I1);
+            for (auto t : {std::make_pair(I0, J0), std::make_pair(I1, J1)}) {
+                if (t.first >= T || (mode == 1 && t.second > t.first)) continue;   // not written
+                if (!written.insert(t).second) fail("pair_unit writes twice", T, G, mode, t.first, t.second);
+            }
+        }
+        if (written != owned(mode, T)) fail("pair_unit coverage", T, G, mode, 0, 0);
+    }
+}
+
 int main() {
     const std::vector<int> Ts = {1, 2, 3, 4, 8, 16, 32, 64, 128, 256};
     const std::vector<int> Gs = {1, 2, 4, 8, 16};
@@ -126,6 +153,8 @@ int main() {
     for (int T : Ts)
         if (T % 2 == 0)
             for (int G : Gs) check_pairs(T, G);
+    for (int T = 1; T <= 40; T++)
+        for (int G : Gs) check_units(T, G);
     if (failures) {
         std::printf("%d failures\n", failures);
         return 1;
