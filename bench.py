@@ -65,6 +65,11 @@ def _args():
                     help="also run the workload's whole run (500 steps at n=14) and state its error vs the oracle")
     ap.add_argument("--shapes", action="store_true",
                     help="batch workload: also time the batch in each tile shape, pinned")
+    ap.add_argument("--batch-systems", type=int, default=64,
+                    help="batch workload: the first K systems of the 64 (a smaller case for profiling)")
+    ap.add_argument("--batch-steps", type=int, default=200, help="batch workload: steps")
+    ap.add_argument("--no-tune", action="store_true", help="batch workload: no autotuning (default shapes)")
+    ap.add_argument("--no-seq", action="store_true", help="batch workload: skip the per-system comparison")
     return ap.parse_args()
 
 
@@ -626,14 +631,15 @@ def run_ours(a, cfg):
 
 
 def run_batch(a):
-    """64 systems, n ~ U{6..12} (seed 2), 200 steps: one tc_batch_evolve vs per-system tc_evolve."""
+    """64 systems, n ~ U{6..12} (seed 2), 200 steps: one tc_batch_evolve vs per-system tc_evolve
+    (--batch-systems / --batch-steps: the first K systems, S steps)."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
     import paper_2403_06937_gb300 as tc
     tc.device_check()
     prec = a.precision
-    cfgs = W.config_batch(steps=200 if prec != "fp64" else 2)
+    cfgs = W.config_batch(steps=a.batch_steps if prec != "fp64" else 2)[:max(1, min(64, a.batch_systems))]
     steps = cfgs[0].steps
     Us, rhos, ps = [], [], []
     for c in cfgs:
@@ -644,10 +650,10 @@ def run_batch(a):
         rhos.append(r)
         ps.append(p)
     # the autotuner picks tile shape, raster group and ring depth for every n of the batch (the
-    # per-system calls use them too; the batch takes the choice for its largest n)
+    # per-system calls use them), and the batch's own shape and group (tc_batch_autotune)
     nmax = max(c.n for c in cfgs)
     tuned, batch_choice = {}, None
-    if prec not in ("fp64", "ozaki"):
+    if prec not in ("fp64", "ozaki") and not a.no_tune:
         for n in sorted({c.n for c in cfgs}):
             tuned[n] = tc.autotune(n, prec)
         batch_choice = tc.batch_autotune([c.n for c in cfgs], prec)
@@ -672,24 +678,26 @@ def run_batch(a):
             torch.cuda.synchronize()
             shapes[name] = len(cfgs) * steps / (time.perf_counter() - t0)
         tc.batch_autotune_set([c.n for c in cfgs], prec, batch_choice["tc_group"], batch_choice["tc_shape"])
-    t0 = time.perf_counter()
-    for U, r, p in zip(Us, rhos, ps):
-        tc.evolve(U, r, p.n, steps, prec, params=p)
-    torch.cuda.synchronize()
-    ts = time.perf_counter() - t0
+    ts = None
+    if not a.no_seq:
+        t0 = time.perf_counter()
+        for U, r, p in zip(Us, rhos, ps):
+            tc.evolve(U, r, p.n, steps, prec, params=p)
+        torch.cuda.synchronize()
+        ts = time.perf_counter() - t0
     credited = sum(12.0 * c.N ** 3 for c in cfgs) * steps
     value = len(cfgs) * steps / tb
-    line = {"metric": "batched evolution: aggregate system-steps/s (64 systems, n=6..12)", "value": value,
+    line = {"metric": "batched evolution: aggregate system-steps/s (%d systems, n=6..12)" % len(cfgs), "value": value,
             "unit": "system-steps/s", "n_gpus": 1, "steps": steps, "warmup": 1, "ms_per_step": 1e3 * tb / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp64": "f64", "bf16x3": "bf16", "tf32": "tf32", "tf32x3": "tf32", "ozaki": "bf16"}[prec],
             "data": "synthetic",
-            "config": {"workload": "64 systems, n ~ U{6..12} seed 2, own g_i ~ U[0.005,0.015], dt=0.05, %d steps"
-                       % steps, "precision": prec, "ns": [c.n for c in cfgs]},
+            "config": {"workload": "%d systems, n ~ U{6..12} seed 2, own g_i ~ U[0.005,0.015], dt=0.05, %d steps"
+                       % (len(cfgs), steps), "precision": prec, "ns": [c.n for c in cfgs]},
             "credited_tflops": credited / tb / 1e12,
-            "sequential": {"value": len(cfgs) * steps / ts, "unit": "system-steps/s",
-                           "api": "tc_evolve per system, one after another"},
-            "speedup_vs_sequential": ts / tb, "gpu_launches": launches}
+            "sequential": None if ts is None else {"value": len(cfgs) * steps / ts, "unit": "system-steps/s",
+                                                   "api": "tc_evolve per system, one after another"},
+            "speedup_vs_sequential": None if ts is None else ts / tb, "gpu_launches": launches}
     if batch_choice:
         names = {0: "auto", 1: "single", 2: "pair32", 3: "pair_wide"}
         line["config"]["tile_shape"] = names[batch_choice["tc_shape"]]
@@ -786,7 +794,7 @@ def run_open(a):
     credited = sum(12.0 * d ** 3 for d in lay.dims)
     peaks, peak_src = _measured_peaks()
     peak = peaks["bf16_tflops_sustained"] if prec in ("bf16x3", "ozaki") else (
-        peaks["bf16_tflops_sustained"] / 2 if prec in ("tf32", "tf32x3") else _fp64_peak_live(torch))
+        _tf32_peak_live(torch)[1] if prec in ("tf32", "tf32x3") else _fp64_peak_live(torch))
     achieved = kflops / (kms * 1e-3) / 1e12 if kms > 0 else 0.0
     value = a.steps / (ms * 1e-3)
     line = {"metric": "open-system split steps/s (Eq. 5 with photon leakage)", "value": value, "unit": "steps/s",
@@ -802,7 +810,9 @@ def run_open(a):
                          "frac": achieved / peak if peak else None, "traffic": None,
                          "kernel": "batched complex GEMM over the excitation blocks (%s), %d launches, %.3f ms avg"
                                    % (prec, klaunch, kms / max(klaunch, 1)),
-                         "peak_source": peak_src},
+                         "peak_source": peak_src if prec in ("bf16x3", "ozaki") else (
+                             "TF32: cuBLAS TF32 GEMM 8192^3 measured live in this run, sustained"
+                             if prec in ("tf32", "tf32x3") else "FP64: cuBLAS DGEMM 4096^3 measured live")},
             "clocks": ck, "gpu_launches": launches,
             "error": {"kind": "conserved total trace after %d steps (oracle-free)" % (a.warmup + a.steps),
                       "trace": float(abs(o[-1, 2 * n + 2] - 1.0)),

@@ -394,7 +394,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint64_t lim = ep.wait_ns ? ep.wait_ns : kWaitLimitNs;
     const uint32_t rank = cluster_ctarank();
     int I, J;
-    pair_tile_rows(MODE, ep.tiles, kPairGroup, (int)(blockIdx.x >> 1), (int)rank, I, J);
+    pair_unit(MODE, ep.tiles, kPairGroup, (int)(blockIdx.x >> 1), (int)rank, I, J);
+    const bool own_rows = I < ep.tiles;   // false for the odd CTA of the last row pair of an odd T
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kPairStages; s++) {
@@ -543,7 +544,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             int t, u;
             oz_pair(p / chunks, S, t, u);
-            oz_epilogue(tmem, warp, lane, I, J, ep, t + u, p == 0, p == 4 * chunks, p == passes - 1);
+            if (own_rows)   // rows past an odd T: loads read zeros, nothing is written
+                oz_epilogue(tmem, warp, lane, I, J, ep, t + u, p == 0, p == 4 * chunks, p == passes - 1);
             tc_fence_before();
             asm volatile("bar.sync 1, 128;" ::: "memory");   // all four epilogue warps have read TMEM
             if (threadIdx.x == 0) {
@@ -682,8 +684,7 @@ tc_status launch_pair(const CUtensorMap& tmU, const CUtensorMap& tmP, const OzEp
         TC_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kPairSmem));
         attr_set[dev] = true;
     }
-    const int TP = ep.tiles / 2;
-    const unsigned pairs = MODE == 0 ? (unsigned)(ep.tiles * TP) : (unsigned)(TP * (TP + 1));
+    const unsigned pairs = (unsigned)pair_units(MODE, ep.tiles);
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(2 * pairs);
     cfg.blockDim = dim3(kThreads);
@@ -702,8 +703,9 @@ tc_status launch_pair(const CUtensorMap& tmU, const CUtensorMap& tmP, const OzEp
 }
 
 // -1: not read yet; else TC_OZ_PAIRS from the environment (0: single CTAs at
-// every size; anything else, or unset: CTA pairs wherever the tile count is
-// even).  Both arrangements give the same bits.
+// every size; anything else, or unset: CTA pairs from two tiles a side; an
+// odd tile count leaves the odd CTA of the last row pair without rows).
+// Both arrangements give the same bits.
 std::atomic<int> g_oz_pairs{-1};
 
 // -1: not chosen yet (TC_OZ_BITS=6 in the environment: 6-bit digits at every
@@ -719,7 +721,7 @@ bool oz_use_pairs(int tiles) {
         v = e && std::atoi(e) == 0 ? 0 : 1;
         g_oz_pairs.store(v);
     }
-    return v != 0 && tiles >= 2 && tiles % 2 == 0;
+    return v != 0 && tiles >= 2;
 }
 
 OzDigits oz_digits(int Np) {

@@ -56,8 +56,9 @@ tc_status cgemm_oz(int mode, const CUtensorMap& tmU, const CUtensorMap& tmP, con
 int oz_pair_rows();
 tc_status oz_mirror(double* yr, double* yi, int Np, cudaStream_t s);
 // True when the product of `tiles` tiles a side runs as CTA pairs on the 2-SM
-// MMA (an even tile count, unless TC_OZ_PAIRS=0 in the environment); else
-// single CTAs.  Both give the same bits.
+// MMA (two tiles a side or more, unless TC_OZ_PAIRS=0 in the environment;
+// for an odd count the odd CTA of the last row pair has no rows); else single
+// CTAs.  Both give the same bits.
 bool oz_use_pairs(int tiles);
 
 // One operand of the emulated product: its digit slices, row exponents and

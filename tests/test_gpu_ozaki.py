@@ -304,3 +304,38 @@ np.savez(%r, **res)
         out[mode] = np.load(path)
     for key in out["0"].files:
         assert np.array_equal(out["0"][key], out["1"][key]), key
+
+
+def test_cta_pairs_with_odd_tile_counts_give_the_same_bits(tc, tmp_path):
+    """The open system's excitation blocks at n = 9 have 1, 3 and 4 tiles a
+    side; with an odd count the odd CTA of the last row pair has no rows (its
+    U loads read zeros, it writes nothing).  Pairs against single CTAs
+    (TC_OZ_PAIRS=0), three split steps with photon leakage: every bit equal."""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = {}
+    for mode in ("0", "1"):
+        path = str(tmp_path / ("odd_%s.npz" % mode))
+        script = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, %r)
+import paper_2403_06937_gb300 as tc, workloads as W
+n = 9
+p = tc.Params(n, list(map(float, W.draw_couplings(n, 13) * 5)), 1.002, 1.0)
+U = tc.lindblad_propagators(p, 0.05)
+lay = tc.lindblad_layout(n)
+assert any((-(-d // 128)) %% 2 == 1 and d > 128 for d in lay.dims)
+rho = torch.zeros(lay.total, dtype=torch.complex128, device='cuda')
+rng = np.random.default_rng(17)
+for blk in lay.blocks(rho):
+    d = blk.shape[0]
+    A = rng.standard_normal((d, d)) + 1j * rng.standard_normal((d, d))
+    M = A @ A.conj().T
+    blk.copy_(torch.from_numpy(M / np.trace(M).real / (n + 1)))
+r, o = tc.lindblad_evolve(p, 0.05, 0.05, U, rho, 3, 'ozaki')
+tc.sync_status()
+np.savez(%r, rho=r.cpu().numpy(), obs=o.cpu().numpy())
+""" % (root, path)
+        subprocess.run([sys.executable, "-c", script], env=dict(os.environ, TC_OZ_PAIRS=mode), check=True)
+        out[mode] = np.load(path)
+    for key in out["0"].files:
+        assert np.array_equal(out["0"][key], out["1"][key]), key
