@@ -13,6 +13,16 @@ PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 std::mutex g_mu;
 
 tc_status get_encode(PFN_cuTensorMapEncodeTiled_v12000* fn) {
+    // The encoder is a driver call and wants the device's context current on
+    // this thread.  A thread that has made no runtime call that binds it yet
+    // (a framework's worker thread, say) gets it bound here, once.
+    thread_local bool bound = false;
+    if (!bound) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaSetDevice(dev) != cudaSuccess)
+            return fail(TC_ERR_CUDA, "no CUDA device for the tensor-map encoder");
+        bound = true;
+    }
     std::lock_guard<std::mutex> lk(g_mu);
     if (!g_encode) {
         void* p = nullptr;
