@@ -473,6 +473,12 @@ TC_API tc_status tc_batch_autotune(int count, const int* n, int precision, void*
  * (host only): choice = {raster group 1..128, tile shape 0..3}. */
 TC_API tc_status tc_batch_autotune_set(int count, const int* n, int precision, const int* choice);
 
+/* The batch choice for this composition and precision, if tuned or pinned in
+ * this process or found in TC_AUTOTUNE_CACHE (host only): *found = 1 and
+ * choice = {raster group, tile shape}; else *found = 0 and tc_batch_evolve
+ * takes the tc_autotune choice for its largest n. */
+TC_API tc_status tc_batch_autotune_lookup(int count, const int* n, int precision, int* choice, int* found);
+
 /* ----------------------------------------------------------- measurement */
 
 /* Number of kernels this library has launched in this process. */

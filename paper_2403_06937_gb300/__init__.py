@@ -389,6 +389,17 @@ def batch_autotune_set(ns, precision="bf16x3", tc_group: int = 8, tc_shape=0) ->
     _abi.call("tc_batch_autotune_set", count, n_arr, prec, arr)
 
 
+def batch_autotune_lookup(ns, precision="bf16x3"):
+    """tc_batch_autotune_lookup: the batch choice for this composition, or None (host only)."""
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    count = len(ns)
+    n_arr = (ctypes.c_int * count)(*[int(x) for x in ns])
+    out = (ctypes.c_int * 2)()
+    found = ctypes.c_int(0)
+    _abi.call("tc_batch_autotune_lookup", count, n_arr, prec, out, ctypes.byref(found))
+    return {"tc_group": out[0], "tc_shape": out[1]} if found.value else None
+
+
 def launch_count() -> int:
     """Kernels launched by libtc in this process."""
     return int(_abi.load().tc_launch_count())
@@ -429,7 +440,7 @@ def sync_status(stream=None) -> None:
 __all__ = ["Params", "TCError", "build_hamiltonian", "expm", "expm_model", "evolve", "LindbladLayout",
            "lindblad_layout", "lindblad_propagators", "lindblad_evolve", "evolve_host", "observables",
            "expectation_diag",
-           "evolve_backward", "EvolveFn", "batch_evolve", "autotune", "autotune_lookup", "autotune_set", "batch_autotune", "batch_autotune_set",
+           "evolve_backward", "EvolveFn", "batch_evolve", "autotune", "autotune_lookup", "autotune_set", "batch_autotune", "batch_autotune_set", "batch_autotune_lookup",
            "workspace_size", "launch_count", "timing_enable", "timing_read", "phases_enable", "phases_read",
            "device_check", "sync_status", "obs_stride", "PRECISIONS", "TC_FP64", "TC_BF16X3", "TC_TF32",
            "TC_TF32X3", "TC_COUPLING_BOSONIC", "TC_COUPLING_QUBIT_PHOTON", "TC_OP_EXPM", "TC_OP_EVOLVE",

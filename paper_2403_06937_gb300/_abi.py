@@ -68,6 +68,7 @@ SIGNATURES = {
     "tc_autotune_set": (I, [I, I, ctypes.POINTER(I)]),
     "tc_batch_autotune": (I, [I, ctypes.POINTER(I), I, VP, SZ, VP, ctypes.POINTER(I)]),
     "tc_batch_autotune_set": (I, [I, ctypes.POINTER(I), I, ctypes.POINTER(I)]),
+    "tc_batch_autotune_lookup": (I, [I, ctypes.POINTER(I), I, ctypes.POINTER(I), ctypes.POINTER(I)]),
     "tc_batch_workspace_size": (SZ, [I, ctypes.POINTER(I), I]),
     "tc_batch_evolve": (I, [I, ctypes.POINTER(I), ctypes.POINTER(VP), ctypes.POINTER(VP), I, I, I,
                             ctypes.POINTER(tc_params), ctypes.POINTER(VP), VP, SZ, VP]),

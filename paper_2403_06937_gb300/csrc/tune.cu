@@ -426,6 +426,17 @@ TC_API tc_status tc_autotune(int n, int precision, void* work, size_t work_bytes
     return TC_OK;
 }
 
+TC_API tc_status tc_batch_autotune_lookup(int count, const int* n, int precision, int* choice, int* found) {
+    if (count < 1 || !n || !choice || !found) return fail(TC_ERR_INVALID_ARG, "tc_batch_autotune_lookup: bad argument");
+    if (precision != TC_BF16X3 && precision != TC_TF32 && precision != TC_TF32X3)
+        return fail(TC_ERR_INVALID_ARG, "batch tuning applies to the tensor-core forms (precision %d)", precision);
+    TuneChoice c{};
+    *found = tune_batch_lookup(count, n, precision, &c) ? 1 : 0;
+    choice[0] = *found ? c.tc_group : 0;
+    choice[1] = *found ? c.tc_shape : 0;
+    return TC_OK;
+}
+
 TC_API tc_status tc_batch_autotune_set(int count, const int* n, int precision, const int* choice) {
     if (count < 1 || !n || !choice) return fail(TC_ERR_INVALID_ARG, "tc_batch_autotune_set: bad argument");
     if (precision != TC_BF16X3 && precision != TC_TF32 && precision != TC_TF32X3)
