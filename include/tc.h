@@ -435,10 +435,13 @@ TC_API size_t tc_batch_workspace_size(int count, const int* n, int precision);
  * each, own U and rho), each stepped `steps` times by rho <- U rho U^dag
  * (Eq. 6) as in tc_evolve.  The tensor-core forms run each product of a step
  * as ONE persistent launch over the tiles of all systems (systems in
- * decreasing size, static round-robin over the SMs); TC_FP64 runs the
- * systems' DMMA products one after another.  Steps 2..K are captured into one
- * CUDA graph on a library-owned stream and launched once; the call returns
- * after the batch has finished.  Every system's result (rho, observables) is
+ * decreasing size, static round-robin over the SMs; single CTAs or CTA
+ * pairs, see tc_batch_autotune); TC_FP64 runs the systems' DMMA products one
+ * after another; TC_FP64_OZAKI runs each system's step loop, with buffers of
+ * its own, on one of eight concurrent branches of the graph (library-owned
+ * streams, one such call at a time per device).  The step loop is captured
+ * into one CUDA graph on a library-owned stream and launched once; the call
+ * returns after the batch has finished.  Every system's result (rho, observables) is
  * bitwise the result of tc_evolve on that system alone with the same
  * precision.
  *  n, U, rho, params, obs : host arrays of `count` entries.  U[b] and rho[b]

@@ -5,16 +5,19 @@
 // form runs the systems' DMMA products one after another.  The whole step
 // loop is captured into one CUDA graph on a library stream and launched once.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <mutex>
 #include <numeric>
 #include <vector>
 
 #include "cgemm_batch.cuh"
+#include "cgemm_oz.cuh"
 #include "graph.cuh"
 #include "cgemm_tc.cuh"
 #include "lowp.cuh"
 #include "paths.cuh"
+#include "timing.cuh"
 
 namespace tc {
 namespace {
@@ -36,17 +39,98 @@ struct F64Sys {
     double *Ur, *Ui, *Rr, *Ri, *Xr, *Xi, *scratch;
 };
 
+// Streams on which the systems of an FP64-emulated batch run side by side
+// (one pool per device, created on first use), with a fork event and one join
+// event per lane.
+constexpr int kOzLanes = 8;
+struct OzLanes {
+    cudaStream_t s[kOzLanes] = {};
+    cudaEvent_t join[kOzLanes] = {};
+    cudaEvent_t fork = nullptr;
+};
+std::mutex g_lanes_mu;
+OzLanes g_lanes[64];
+
+tc_status oz_lanes(OzLanes** out) {
+    int dev = 0;
+    TC_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(TC_ERR_UNSUPPORTED_DEVICE, "device index out of range");
+    std::lock_guard<std::mutex> lk(g_lanes_mu);
+    OzLanes& l = g_lanes[dev];
+    if (!l.fork) {
+        for (int i = 0; i < kOzLanes; i++) {
+            TC_CUDA(cudaStreamCreateWithFlags(&l.s[i], cudaStreamNonBlocking));
+            TC_CUDA(cudaEventCreateWithFlags(&l.join[i], cudaEventDisableTiming));
+        }
+        TC_CUDA(cudaEventCreateWithFlags(&l.fork, cudaEventDisableTiming));
+    }
+    *out = &l;
+    return TC_OK;
+}
+
+// FP64 emulated on the BF16 tensor cores: every system with its own buffers;
+// the step loops run on up to kOzLanes concurrent lanes (systems assigned
+// largest first to the lane with the least work, N^3 each), captured into
+// one graph (fork from the capture stream, join back before its end), so
+// the small systems' launches fill the SMs the large products leave idle.
+// Each system's launches keep their order, so its results are bitwise those
+// of tc_evolve on it alone.
+tc_status batch_oz(int count, const int* n, const void* const* U, void* const* rho, int steps, int renorm_every,
+                   const Model* models, double* const* obs, void* work, size_t work_bytes, cudaStream_t us) {
+    std::vector<int> order(count);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return n[a] > n[b]; });
+    Arena ar{static_cast<char*>(work), work_bytes, 0};
+    std::vector<OzSystem> z(count);
+    for (int b : order) TC_TRY(z[b].carve(n[b], ar));
+    const int L = count < kOzLanes ? count : kOzLanes;
+    std::vector<std::vector<int>> lane(L);
+    std::vector<double> load(L, 0.0);
+    for (int b : order) {
+        const int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        lane[l].push_back(b);
+        load[l] += std::pow(2.0, 3.0 * n[b]);
+    }
+    OzLanes* ls = nullptr;
+    TC_TRY(oz_lanes(&ls));
+    auto first = [&](cudaStream_t cs) -> tc_status {
+        for (int b : order)
+            TC_TRY(z[b].first(static_cast<const double*>(U[b]), static_cast<const double*>(rho[b]),
+                              models ? &models[b] : nullptr, obs ? obs[b] : nullptr, renorm_every, cs));
+        return TC_OK;
+    };
+    auto rest = [&](cudaStream_t cs) -> tc_status {
+        TC_CUDA(cudaEventRecord(ls->fork, cs));
+        for (int l = 0; l < L; l++) TC_CUDA(cudaStreamWaitEvent(ls->s[l], ls->fork, 0));
+        tc_status st = TC_OK;
+        for (int l = 0; l < L && st == TC_OK; l++)
+            for (int b : lane[l])
+                for (int k = 1; k <= steps && st == TC_OK; k++) st = z[b].step(k, ls->s[l]);
+        // every lane joins back, also after a failure (a capture ends only with its streams joined)
+        for (int l = 0; l < L; l++) {
+            cudaEventRecord(ls->join[l], ls->s[l]);
+            cudaStreamWaitEvent(cs, ls->join[l], 0);
+        }
+        return st;
+    };
+    auto tail = [&](cudaStream_t cs) -> tc_status {
+        for (int b : order) TC_TRY(z[b].tail(static_cast<double*>(rho[b]), cs));
+        return TC_OK;
+    };
+    return run_captured(us, first, rest, tail, steps >= 1 && !timing_enabled());
+}
+
 }  // namespace
 
 size_t batch_bytes(int count, const int* n, int precision) {
     if (precision == TC_FP64_OZAKI) {
-        // the systems run one after another through one workspace
-        size_t most = 0;
+        // each system has its own buffers (the systems run side by side)
+        size_t total = 256;
         for (int b = 0; b < count; b++) {
             if (n[b] < 1 || n[b] > kMaxAtoms) return 0;
-            most = std::max(most, evolve_oz_bytes(n[b]));
+            total += evolve_oz_bytes(n[b]);
         }
-        return most + 256;
+        return total;
     }
     size_t total = 256 + round256(sizeof(BatchSys) * (size_t)count) + 64;
     for (int b = 0; b < count; b++) {
@@ -93,16 +177,8 @@ TC_API tc_status tc_batch_evolve(int count, const int* n, const void* const* U, 
     if (work_bytes < need) return fail(TC_ERR_WORKSPACE, "work has %zu bytes, need %zu", work_bytes, need);
     TC_TRY(check_device());
     cudaStream_t us = as_stream(stream);
-    if (precision == TC_FP64_OZAKI) {
-        // FP64 emulated on the BF16 tensor cores: each system's step loop in turn
-        // (one graph per system), all through the same workspace
-        for (int b = 0; b < count; b++) {
-            Arena ar{static_cast<char*>(work), work_bytes, 0};
-            TC_TRY(evolve_oz(static_cast<const double*>(U[b]), static_cast<double*>(rho[b]), n[b], steps,
-                             renorm_every, params ? &models[b] : nullptr, obs ? obs[b] : nullptr, ar, us));
-        }
-        return TC_OK;
-    }
+    if (precision == TC_FP64_OZAKI) return batch_oz(count, n, U, rho, steps, renorm_every, params ? models.data() : nullptr,
+                                                    obs, work, work_bytes, us);
 
     // systems in decreasing size: the longest tiles first in the persistent schedule
     std::vector<int> order(count);

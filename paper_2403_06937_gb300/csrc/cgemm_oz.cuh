@@ -86,4 +86,22 @@ tc_status oz_mat_load(OzMat& m, const double* re, const double* im, bool interle
 // Y = A B^H at FP64 accuracy; mode 1 (Hermitian result): block-lower tiles and the mirror.
 tc_status oz_product(int mode, const OzMat& A, const OzMat& B, const OzOut& out, int group, cudaStream_t s);
 
+// The FP64-accurate step loop of one system (evolve_oz.cu): its slices,
+// FP64 planes of rho and X (stride Np = max(N, 128)) and int64 scratch, carved
+// from an arena; first() slices U and pads rho in, step(k) is one step
+// (observable row k when obs is given), tail() writes rho back interleaved.
+struct OzSystem {
+    int n = 0, N = 0, Np = 0, group = 8, renorm_every = 0;
+    OzMat Us{}, Ps{};
+    double *Rr = nullptr, *Ri = nullptr, *Xr = nullptr, *Xi = nullptr, *scratch = nullptr;
+    long long *Lr = nullptr, *Li = nullptr;
+    const Model* m = nullptr;
+    double* obs = nullptr;
+    tc_status carve(int n, Arena& ar);
+    tc_status first(const double* U, const double* rho, const Model* m, double* obs, int renorm_every,
+                    cudaStream_t cs);
+    tc_status step(int k, cudaStream_t cs);
+    tc_status tail(double* rho, cudaStream_t cs);
+};
+
 }  // namespace tc

@@ -86,65 +86,84 @@ size_t evolve_oz_bytes(int n) {
     return 2 * oz_mat_bytes((int)Np) + 6 * round256(Np * Np * sizeof(double)) + observables_scratch_bytes(n) + 512;
 }
 
-tc_status evolve_oz(const double* U, double* rho, int n, int steps, int renorm_every, const Model* m, double* obs,
-                    Arena& ar, cudaStream_t s) {
-    const int N = 1 << n;
-    const int Np = padded_dim(n);
+tc_status OzSystem::carve(int n_, Arena& ar) {
+    n = n_;
+    N = 1 << n;
+    Np = padded_dim(n);
     const size_t NN = (size_t)Np * Np;
-    OzMat Us{}, Ps{};
     TC_TRY(oz_mat_init(Us, ar, Np));
     TC_TRY(oz_mat_init(Ps, ar, Np));
-    double* Rr = ar.take<double>(NN);
-    double* Ri = ar.take<double>(NN);
-    double* Xr = ar.take<double>(NN);
-    double* Xi = ar.take<double>(NN);
-    long long* Lr = ar.take<long long>(NN);   // low-level integer sums of the products
-    long long* Li = ar.take<long long>(NN);
-    double* scratch = ar.take<double>(observables_scratch_bytes(n) / sizeof(double));
+    Rr = ar.take<double>(NN);
+    Ri = ar.take<double>(NN);
+    Xr = ar.take<double>(NN);
+    Xi = ar.take<double>(NN);
+    Lr = ar.take<long long>(NN);   // low-level integer sums of the products
+    Li = ar.take<long long>(NN);
+    scratch = ar.take<double>(observables_scratch_bytes(n) / sizeof(double));
     if (!scratch) return fail(TC_ERR_WORKSPACE, "evolve: workspace too small");
-    const int group = tune_lookup(n, TC_BF16X3).tc_group;
-    const OzOut X{Xr, Xi, Lr, Li}, R{Rr, Ri, Lr, Li};
+    group = tune_lookup(n, TC_BF16X3).tc_group;
+    return TC_OK;
+}
 
-    const int stride = TC_OBS_STRIDE(n);
+tc_status OzSystem::first(const double* U, const double* rho, const Model* m_, double* obs_, int renorm_every_,
+                          cudaStream_t cs) {
+    m = m_;
+    obs = obs_;
+    renorm_every = renorm_every_;
+    const size_t NN = (size_t)Np * Np;
+    TC_TRY(oz_mat_load(Us, U, nullptr, true, false, N, (size_t)N, cs));
+    split_pad_kernel<<<grid_for(NN), 256, 0, cs>>>(reinterpret_cast<const double2*>(rho), N, Np, Rr, Ri);
+    TC_LAUNCH_CHECK();
+    if (obs) TC_TRY(launch_observables(kRhoPlanarF64, Rr, Ri, m, n, obs, scratch, cs, (size_t)Np));
+    return TC_OK;
+}
+
+tc_status OzSystem::step(int k, cudaStream_t cs) {
+    const size_t NN = (size_t)Np * Np;
     const double N3 = (double)N * N * N;
-    auto one_step = [&](int k, cudaStream_t cs) -> tc_status {
-        TC_TRY(oz_mat_load(Ps, Rr, Ri, false, false, N, (size_t)Np, cs));
-        {
-            ProductTimer t(8.0 * N3 * Us.dg.pairs, cs);   // X = U rho^H
-            TC_TRY(oz_product(0, Us, Ps, X, group, cs));
-        }
-        TC_TRY(oz_mat_load(Ps, Xr, Xi, false, false, N, (size_t)Np, cs));
-        {
-            ProductTimer t(4.0 * N3 * Us.dg.pairs, cs);   // rho' = U X^H, Hermitian half + mirror
-            TC_TRY(oz_product(1, Us, Ps, R, group, cs));
-        }
-        if (renorm_every > 0 && k % renorm_every == 0) {
-            trace_pad_kernel<<<1, 1024, 0, cs>>>(Rr, N, Np, scratch);
-            TC_LAUNCH_CHECK();
-            scale_pad_kernel<<<grid_for(NN), 256, 0, cs>>>(Rr, Ri, Np, scratch, device_status_word());
-            TC_LAUNCH_CHECK();
-        }
-        if (obs)
-            TC_TRY(launch_observables(kRhoPlanarF64, Rr, Ri, m, n, obs + (size_t)k * stride, scratch, cs, (size_t)Np));
-        return TC_OK;
-    };
-    auto first = [&](cudaStream_t cs) -> tc_status {
-        TC_TRY(oz_mat_load(Us, U, nullptr, true, false, N, (size_t)N, cs));
-        split_pad_kernel<<<grid_for(NN), 256, 0, cs>>>(reinterpret_cast<const double2*>(rho), N, Np, Rr, Ri);
+    const OzOut X{Xr, Xi, Lr, Li}, R{Rr, Ri, Lr, Li};
+    TC_TRY(oz_mat_load(Ps, Rr, Ri, false, false, N, (size_t)Np, cs));
+    {
+        ProductTimer t(8.0 * N3 * Us.dg.pairs, cs);   // X = U rho^H
+        TC_TRY(oz_product(0, Us, Ps, X, group, cs));
+    }
+    TC_TRY(oz_mat_load(Ps, Xr, Xi, false, false, N, (size_t)Np, cs));
+    {
+        ProductTimer t(4.0 * N3 * Us.dg.pairs, cs);   // rho' = U X^H, Hermitian half + mirror
+        TC_TRY(oz_product(1, Us, Ps, R, group, cs));
+    }
+    if (renorm_every > 0 && k % renorm_every == 0) {
+        trace_pad_kernel<<<1, 1024, 0, cs>>>(Rr, N, Np, scratch);
         TC_LAUNCH_CHECK();
-        if (obs) TC_TRY(launch_observables(kRhoPlanarF64, Rr, Ri, m, n, obs, scratch, cs, (size_t)Np));
-        if (steps >= 1) TC_TRY(one_step(1, cs));
+        scale_pad_kernel<<<grid_for(NN), 256, 0, cs>>>(Rr, Ri, Np, scratch, device_status_word());
+        TC_LAUNCH_CHECK();
+    }
+    if (obs)
+        TC_TRY(launch_observables(kRhoPlanarF64, Rr, Ri, m, n, obs + (size_t)k * TC_OBS_STRIDE(n), scratch, cs,
+                                  (size_t)Np));
+    return TC_OK;
+}
+
+tc_status OzSystem::tail(double* rho, cudaStream_t cs) {
+    join_pad_kernel<<<grid_for((size_t)N * N), 256, 0, cs>>>(Rr, Ri, N, Np, reinterpret_cast<double2*>(rho));
+    TC_LAUNCH_CHECK();
+    return TC_OK;
+}
+
+tc_status evolve_oz(const double* U, double* rho, int n, int steps, int renorm_every, const Model* m, double* obs,
+                    Arena& ar, cudaStream_t s) {
+    OzSystem z;
+    TC_TRY(z.carve(n, ar));
+    auto first = [&](cudaStream_t cs) -> tc_status {
+        TC_TRY(z.first(U, rho, m, obs, renorm_every, cs));
+        if (steps >= 1) TC_TRY(z.step(1, cs));
         return TC_OK;
     };
     auto rest = [&](cudaStream_t cs) -> tc_status {
-        for (int k = 2; k <= steps; k++) TC_TRY(one_step(k, cs));
+        for (int k = 2; k <= steps; k++) TC_TRY(z.step(k, cs));
         return TC_OK;
     };
-    auto tail = [&](cudaStream_t cs) -> tc_status {
-        join_pad_kernel<<<grid_for((size_t)N * N), 256, 0, cs>>>(Rr, Ri, N, Np, reinterpret_cast<double2*>(rho));
-        TC_LAUNCH_CHECK();
-        return TC_OK;
-    };
+    auto tail = [&](cudaStream_t cs) -> tc_status { return z.tail(rho, cs); };
     return run_captured(s, first, rest, tail, steps > 2 && !timing_enabled());
 }
 
