@@ -85,7 +85,7 @@ typedef enum tc_status {
  *              2^-48 of the row and column scales per product term (worst
  *              case); rho stored in FP64.  tc_evolve, tc_evolve_host,
  *              tc_lindblad_evolve, tc_evolve_backward and tc_batch_evolve
- *              (there the systems run one after another).
+ *              (there the systems run side by side on concurrent branches).
  * In the BF16/TF32 forms U is computed in FP64 and rho is stored in FP32
  * between steps. */
 typedef enum tc_precision {

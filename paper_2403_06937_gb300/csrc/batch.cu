@@ -1,9 +1,10 @@
 // batch.cu -- many independent systems of uneven size stepped together
 // (tc_batch_evolve).  The tensor-core forms run each product of a step as one
 // persistent launch over the tiles of every system (cgemm_batch.cu; single
-// CTAs or CTA pairs, the autotuner's tile shape); the FP64
-// form runs the systems' DMMA products one after another.  The whole step
-// loop is captured into one CUDA graph on a library stream and launched once.
+// CTAs or CTA pairs, the autotuner's tile shape); the FP64 form runs the
+// systems' DMMA products one after another, the FP64-emulated form each
+// system's step loop on one of eight concurrent lanes.  The whole step loop
+// is captured into one CUDA graph on a library stream and launched once.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
