@@ -439,22 +439,43 @@ def _oracle_trajectories(cfg, upto):
     return np.array(rows), psis, t / max(done, 1)
 
 
-def _error_vs_oracle(r, n, rows, psis):
+def _dicke_pm(cfg, steps):
+    """Equal couplings only: P(m) of every step up to `steps` by the oracle's
+    second route, the (n+1) x (n+1) Dicke tridiagonal of the symmetric
+    subspace diagonalised (Jacobi) and evolved exactly; else None."""
+    if not np.all(np.asarray(cfg.g) == cfg.g[0]):
+        return None
+    import oracle
+    oracle.build()
+    n = cfg.n
+    w, V = oracle.jacobi_eig(oracle.dicke_matrix(n, float(cfg.g[0]), cfg.omega_a, cfg.omega_c))
+    e0 = np.zeros(n + 1)
+    e0[0] = 1.0
+    c = V.T @ e0
+    return np.array([np.abs(V @ (np.exp(-1j * w * cfg.dt * k) * c)) ** 2 for k in range(steps + 1)])
+
+
+def _error_vs_oracle(r, n, rows, psis, dicke=None):
     """Max-abs error of a form's results against the oracle over the steps it
     ran: populations P_i, mean photon number <p>, photon-number
-    probabilities P(m) (Eq. 13) and the sampled rho entries."""
+    probabilities P(m) (Eq. 13) and the sampled rho entries; with equal
+    couplings also P(m) against the Dicke route."""
     o = r["obs"]
     first, k = r["first"], r["steps"]
     ref = rows[first:first + k + 1]
     ii, jj, vals = r["sample"]
     psi = psis[first + k]
     want = psi[ii] * psi[jj].conj()
-    return {"steps": "%d..%d" % (first, first + k),
-            "populations": float(np.max(np.abs(o[:, :n] - ref[:, :n]))),
-            "mean_photons": float(np.max(np.abs(o[:, n] - ref[:, n]))),
-            "photon_number_probabilities": float(np.max(np.abs(o[:, n + 1:2 * n + 2] - ref[:, n + 1:2 * n + 2]))),
-            "rho_sampled": float(np.max(np.abs(vals - want))),
-            "rho_entries_sampled": int(len(ii))}
+    out = {"steps": "%d..%d" % (first, first + k),
+           "populations": float(np.max(np.abs(o[:, :n] - ref[:, :n]))),
+           "mean_photons": float(np.max(np.abs(o[:, n] - ref[:, n]))),
+           "photon_number_probabilities": float(np.max(np.abs(o[:, n + 1:2 * n + 2] - ref[:, n + 1:2 * n + 2]))),
+           "rho_sampled": float(np.max(np.abs(vals - want))),
+           "rho_entries_sampled": int(len(ii))}
+    if dicke is not None:
+        out["photon_number_probabilities_vs_dicke"] = float(
+            np.max(np.abs(o[:, n + 1:2 * n + 2] - dicke[first:first + k + 1])))
+    return out
 
 
 def run_ours(a, cfg):
@@ -616,12 +637,13 @@ def run_ours(a, cfg):
                                                       "what": "O-psi: psi <- e^{-iH dt} psi by the Taylor series to "
                                                               "convergence with the sparse H, plus one observable "
                                                               "row per step"}}
-        line["error"]["vs_oracle"] = _error_vs_oracle(forms[prec], n, rows, psis)
+        dicke = _dicke_pm(cfg, max(upto))
+        line["error"]["vs_oracle"] = _error_vs_oracle(forms[prec], n, rows, psis, dicke)
         for p2, f in forms.items():
             if p2 != prec and p2 in line.get("other_forms", {}):
-                line["other_forms"][p2]["error"]["vs_oracle"] = _error_vs_oracle(f, n, rows, psis)
+                line["other_forms"][p2]["error"]["vs_oracle"] = _error_vs_oracle(f, n, rows, psis, dicke)
         if full is not None:
-            line["full_run"]["error"]["vs_oracle"] = _error_vs_oracle(full, n, rows, psis)
+            line["full_run"]["error"]["vs_oracle"] = _error_vs_oracle(full, n, rows, psis, dicke)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -706,6 +728,24 @@ def run_batch(a):
         line["tuned_per_n"] = {str(n): names[t["tc_shape"]] for n, t in tuned.items()}
     if shapes:
         line["by_shape"] = shapes
+    if not a.no_cpu and obs is not None:
+        # the stated error: every system's observable rows (all steps) against the oracle's
+        # pure-state propagation of that system (O-psi)
+        import oracle
+        oracle.build()
+        worst = {"populations": 0.0, "mean_photons": 0.0, "photon_number_probabilities": 0.0}
+        t0 = time.perf_counter()
+        for c, ob in zip(cfgs, obs):
+            n = c.n
+            _, ref = oracle.propagate(n, c.g, c.omega_a, c.omega_c, c.dt, steps, W.all_excited_state(n))
+            o = ob.cpu().numpy()
+            worst["populations"] = max(worst["populations"], float(np.max(np.abs(o[:, :n] - ref[:, :n]))))
+            worst["mean_photons"] = max(worst["mean_photons"], float(np.max(np.abs(o[:, n] - ref[:, n]))))
+            worst["photon_number_probabilities"] = max(
+                worst["photon_number_probabilities"],
+                float(np.max(np.abs(o[:, n + 1:2 * n + 2] - ref[:, n + 1:2 * n + 2]))))
+        line["error"] = {"vs_oracle": dict(worst, systems=len(cfgs), steps="0..%d" % steps,
+                                           oracle_seconds=time.perf_counter() - t0)}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -739,6 +779,36 @@ def run_grad(a):
             "config": {"workload": cfg.description,
                        "products": "FP64 DMMA" if gprec == "fp64" else "FP64 emulated on the BF16 tensor cores"},
             "loss": loss, "grad": grad.tolist(), "fp64_tflops": flops / t / 1e12}
+    if not a.no_cpu:
+        # the stated errors: against the oracle's forward-mode tangent (all 13 components) and
+        # central differences of the oracle's forward run (h = 1e-6; g_1, g_6 and omega_a)
+        import oracle
+        oracle.build()
+        Od = O.cpu().numpy()
+        psi0 = W.all_excited_state(n)
+        t0 = time.perf_counter()
+        ref = oracle.grad_forward(n, cfg.g, cfg.omega_a, cfg.omega_c, cfg.dt, cfg.steps, psi0, Od)
+        t_tan = time.perf_counter() - t0
+        g_np = np.asarray(grad.tolist())
+        h = 1e-6
+
+        def L(g_, wa_, wc_):
+            q, _ = oracle.propagate(n, g_, wa_, wc_, cfg.dt, cfg.steps, psi0, observe=False)
+            return float(np.real(np.vdot(q, Od * q)))
+
+        fd = {}
+        for j in (0, 5):
+            gp, gm = np.array(cfg.g, dtype=float), np.array(cfg.g, dtype=float)
+            gp[j] += h
+            gm[j] -= h
+            fd[j] = (L(gp, cfg.omega_a, cfg.omega_c) - L(gm, cfg.omega_a, cfg.omega_c)) / (2 * h)
+        fd[n] = (L(cfg.g, cfg.omega_a + h, cfg.omega_c) - L(cfg.g, cfg.omega_a - h, cfg.omega_c)) / (2 * h)
+        scale = max(abs(v) for v in fd.values())
+        line["error"] = {
+            "vs_oracle_tangent": float(np.max(np.abs(g_np - ref)) / np.max(np.abs(ref))),
+            "vs_central_differences": float(max(abs(g_np[j] - v) / max(abs(v), scale) for j, v in fd.items())),
+            "fd": {"h": h, "components": ["g_1", "g_6", "omega_a"]},
+            "oracle_tangent_seconds": t_tan}
     print(json.dumps(line), flush=True)
     return 0
 

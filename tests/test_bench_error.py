@@ -39,3 +39,21 @@ def test_error_of_the_oracle_itself_is_zero_and_planted_errors_show(oracle):
     assert abs(e["mean_photons"] - 2e-7) < 1e-12
     assert abs(e["photon_number_probabilities"] - 5e-8) < 1e-12
     assert abs(e["rho_sampled"] - 4e-6) < 1e-12
+
+
+def test_dicke_route_of_the_n8_workload(oracle):
+    """c1 has equal couplings: the bench's second route for P(m), the Dicke
+    tridiagonal evolved exactly, agrees with the full-space oracle to 1e-12 and
+    reports a planted P(m) deviation; unequal couplings have no such route."""
+    cfg = W.config_n8()
+    rows, psis, _ = bench._oracle_trajectories(cfg, [6])
+    dicke = bench._dicke_pm(cfg, 6)
+    n = cfg.n
+    assert dicke.shape == (7, n + 1)
+    assert np.max(np.abs(dicke - rows[:, n + 1:2 * n + 2])) < 1e-12
+    rng = np.random.default_rng(1)
+    f = _fake_form(cfg, rows, psis, 2, 4, rng)
+    f["obs"][3, n + 1 + 5] -= 7e-8      # P(5) after step 5
+    e = bench._error_vs_oracle(f, n, rows, psis, dicke)
+    assert abs(e["photon_number_probabilities_vs_dicke"] - 7e-8) < 1e-11
+    assert bench._dicke_pm(W.config_n12(), 3) is None
