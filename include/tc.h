@@ -402,10 +402,11 @@ TC_API tc_status tc_evolve_host(const void* U, void* rho_host, int n, int steps,
  *   super-blocks of the lower triangle for the Hermitian product, so
  *   concurrent CTAs share operand panels in L2; 4, 8, 12, 16) and, for
  *   shape 1, the TMA ring depth (two per precision), each timed as the mean
- *   step over >= 100 ms of back-to-back steps (the clock a configuration
- *   holds under the power cap depends on its shared-memory and L2 traffic),
- *   in two passes.  The batched and open-system calls take the shape and group
- *   chosen for their largest n.
+ *   step over windows of 8 back-to-back steps (150 ms to 1.2 s; the clock a
+ *   configuration holds under the power cap depends on its shared-memory and
+ *   L2 traffic), in two passes in opposite orders.  The open-system call
+ *   takes the shape and group chosen for its n; tc_batch_evolve those of
+ *   tc_batch_autotune, else those chosen for its largest n.
  * The choice is also appended, one JSON object per line, to the file named by
  * the environment variable TC_AUTOTUNE_CACHE (when set), which is read on the
  * first lookup of a process.  Every configuration computes each output in the
@@ -460,8 +461,8 @@ TC_API tc_status tc_batch_evolve(int count, const int* n, const void* const* U, 
  * n[b]): the batch's workspace is filled with synthetic operands and one
  * batch step (both persistent launches) is timed in every shape (single CTAs
  * on 128 x 128 tiles; CTA pairs on the 2-SM MMA, 256 x 128 a pair, with 32-byte
- * or wide K rows) and raster group (4, 8, 12, 16), as the mean over >= 100 ms
- * of back-to-back steps, in two passes.  Later tc_batch_evolve calls in this
+ * or wide K rows) and raster group (4, 8, 12, 16), as tc_autotune times its
+ * configurations.  Later tc_batch_evolve calls in this
  * process on a batch of the same composition and precision use the fastest
  * (otherwise the tc_autotune choice for the largest n); the choice is also
  * appended to TC_AUTOTUNE_CACHE when set.  Results do not depend on the

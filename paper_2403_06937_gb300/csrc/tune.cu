@@ -3,8 +3,9 @@
 // For one (n, precision) it times every built configuration of the kernels a
 // step launches, on synthetic operands laid out exactly as tc_evolve lays
 // them out in the caller's workspace, and keeps the fastest (tensor cores:
-// the mean over a window of >= 100 ms of back-to-back steps, so that the
-// clock each configuration holds under the power cap counts):
+// the mean over windows of 8 back-to-back steps, at least 150 ms and at
+// most 1.2 s, in two passes, so that the clock each configuration holds
+// under the power cap counts):
 //   FP64:         the DMMA GEMM tile (32 x 32 or 64 x 64 complex elements);
 //   tensor cores: the tile shape (single CTAs on 128 x 128 tiles; CTA
 //                 pairs on the 2-SM MMA, 256 x 128 per pair, with 32-byte
@@ -239,6 +240,30 @@ tc_status time_window(cudaStream_t s, double window_ms, F launch, double* mean) 
     return st;
 }
 
+// Scores of `count` configurations (the mean step time of each over two
+// passes).  The window of a timing is 8 steps of the first configuration,
+// within [150 ms, 1.2 s]: long enough that the clock settles to what the
+// configuration draws under the power cap.  The GPU first runs the last
+// configuration for a window; the second pass takes the configurations in
+// reverse order, so a slow drift of the clock weighs on all of them alike.
+template <typename F>
+tc_status score_configs(cudaStream_t s, int count, F step, std::vector<double>& score) {
+    double one = 0.0;
+    TC_TRY(time_ms(s, 1, [&]() { return step(0); }, &one));
+    double window = 8.0 * one;
+    window = window < 150.0 ? 150.0 : window > 1200.0 ? 1200.0 : window;
+    double ms = 0.0;
+    TC_TRY(time_window(s, window, [&]() { return step(count - 1); }, &ms));
+    score.assign(count, 0.0);
+    for (int pass = 0; pass < 2; pass++)
+        for (int i = 0; i < count; i++) {
+            const int c = pass == 0 ? i : count - 1 - i;
+            TC_TRY(time_window(s, window, [&]() { return step(c); }, &ms));
+            score[c] += 0.5 * ms;
+        }
+    return TC_OK;
+}
+
 }  // namespace
 
 TuneChoice tune_lookup(int n, int precision) {
@@ -391,16 +416,9 @@ TC_API tc_status tc_autotune(int n, int precision, void* work, size_t work_bytes
             tc_status st = cgemm_tc(precision, 0, tmU, tmR, e, s, cd.stages, &wU, &wR);
             return st == TC_OK ? cgemm_tc(precision, 1, tmU, tmX, e2, s, cd.stages, &wU, &wX) : st;
         };
-        // the GPU first runs one configuration for a window (the timings start from the power and
-        // clock of a long run), then every configuration is timed over a sustained window, in two
-        // round-robin passes (the better mean of the two)
-        double ms = 0.0;
-        TC_TRY(time_window(s, 200.0, [&]() { return step(cands.back()); }, &ms));
-        for (int pass = 0; pass < 2; pass++)
-            for (Cand& cd : cands) {
-                TC_TRY(time_window(s, 100.0, [&]() { return step(cd); }, &ms));
-                if (ms < cd.ms) cd.ms = ms;
-            }
+        std::vector<double> score;
+        TC_TRY(score_configs(s, (int)cands.size(), [&](int i) { return step(cands[i]); }, score));
+        for (size_t i = 0; i < cands.size(); i++) cands[i].ms = score[i];
         for (const Cand& cd : cands)
             if (cd.ms < best_ms) {
                 best_ms = cd.ms;
@@ -501,13 +519,9 @@ TC_API tc_status tc_batch_autotune(int count, const int* n, int precision, void*
         tc_status st = cgemm_batch(precision, 0, sys_dev, count, p, status, s);
         return st == TC_OK ? cgemm_batch(precision, 1, sys_dev, count, p, status, s) : st;
     };
-    double ms = 0.0;
-    TC_TRY(time_window(s, 200.0, [&]() { return step(cands.back()); }, &ms));
-    for (int pass = 0; pass < 2; pass++)
-        for (Cand& cd : cands) {
-            TC_TRY(time_window(s, 100.0, [&]() { return step(cd); }, &ms));
-            if (ms < cd.ms) cd.ms = ms;
-        }
+    std::vector<double> score;
+    TC_TRY(score_configs(s, (int)cands.size(), [&](int i) { return step(cands[i]); }, score));
+    for (size_t i = 0; i < cands.size(); i++) cands[i].ms = score[i];
     TC_CUDA(cudaStreamSynchronize(s));
     TuneChoice best{0, 8, cgemm_default_stages(precision), kShapeAuto};
     double best_ms = 1e30;
