@@ -32,6 +32,7 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "cgemm_batch.cuh"
@@ -301,19 +302,37 @@ __global__ void obs_partial_kernel(BlockSet bs, Model m, int has_model, const in
         // four independent loads per lane in flight, fixed summation order
         double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
         unsigned c = lane;
-        for (; c + 96 < d; c += 128) {
-            const double x0 = (double)re[row + c], x1 = (double)re[row + c + 32], x2 = (double)re[row + c + 64],
-                         x3 = (double)re[row + c + 96];
-            const double y0 = (double)im[row + c], y1 = (double)im[row + c + 32], y2 = (double)im[row + c + 64],
-                         y3 = (double)im[row + c + 96];
-            p0 += x0 * x0 + y0 * y0;
-            p1 += x1 * x1 + y1 * y1;
-            p2 += x2 * x2 + y2 * y2;
-            p3 += x3 * x3 + y3 * y3;
-        }
-        for (; c < d; c += 32) {
-            const double x = (double)re[row + c], y = (double)im[row + c];
-            p0 += x * x + y * y;
+        if constexpr (std::is_same<T, float>::value) {
+            // FP32 planes: the squares of each group of four entries summed in FP32
+            // (fused multiply-adds), the group sums carried in FP64 (GB300 issues FP64
+            // at a small fraction of its FP32 rate)
+            for (; c + 96 < d; c += 128) {
+                const float x0 = re[row + c], x1 = re[row + c + 32], x2 = re[row + c + 64], x3 = re[row + c + 96];
+                const float y0 = im[row + c], y1 = im[row + c + 32], y2 = im[row + c + 64], y3 = im[row + c + 96];
+                const float q01 = fmaf(y1, y1, fmaf(x1, x1, fmaf(y0, y0, x0 * x0)));
+                const float q23 = fmaf(y3, y3, fmaf(x3, x3, fmaf(y2, y2, x2 * x2)));
+                p0 += (double)q01;
+                p2 += (double)q23;
+            }
+            for (; c < d; c += 32) {
+                const float x = re[row + c], y = im[row + c];
+                p1 += (double)fmaf(y, y, x * x);
+            }
+        } else {
+            for (; c + 96 < d; c += 128) {
+                const double x0 = (double)re[row + c], x1 = (double)re[row + c + 32], x2 = (double)re[row + c + 64],
+                             x3 = (double)re[row + c + 96];
+                const double y0 = (double)im[row + c], y1 = (double)im[row + c + 32], y2 = (double)im[row + c + 64],
+                             y3 = (double)im[row + c + 96];
+                p0 += x0 * x0 + y0 * y0;
+                p1 += x1 * x1 + y1 * y1;
+                p2 += x2 * x2 + y2 * y2;
+                p3 += x3 * x3 + y3 * y3;
+            }
+            for (; c < d; c += 32) {
+                const double x = (double)re[row + c], y = (double)im[row + c];
+                p0 += x * x + y * y;
+            }
         }
         pur += (p0 + p1) + (p2 + p3);
         const unsigned s = (unsigned)order[i];
