@@ -141,6 +141,12 @@ typedef struct tc_expm_opts {
 #define TC_OP_EVOLVE_HOST 16
 #define TC_OP_EXPM_MODEL 32
 #define TC_OP_LINDBLAD 64
+/* tc_evolve_host with a page-locked rho_host: in the tensor-core forms with
+ * at least one step and N >= 2048 (row blocks in, row bands out) the SMs read
+ * and write the host rows and no device copy of rho is kept, which is what
+ * lets n = 16 (64 GiB per complex128 matrix) fit beside U; elsewhere the
+ * same as TC_OP_EVOLVE_HOST. */
+#define TC_OP_EVOLVE_HOST_PINNED 128
 
 /* ------------------------------------------------------------------ misc */
 

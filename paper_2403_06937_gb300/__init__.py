@@ -216,7 +216,9 @@ def evolve_host(U: torch.Tensor, rho_host: torch.Tensor, n: int, steps: int, pre
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     N = 1 << n
     assert rho_host.device.type == "cpu" and rho_host.dtype == torch.complex128 and rho_host.shape == (N, N)
-    need = workspace_size(n, prec, _abi.TC_OP_EVOLVE_HOST, steps)
+    # a page-locked buffer lets the pipelined tensor-core forms skip the device copy of rho
+    op = _abi.TC_OP_EVOLVE_HOST_PINNED if rho_host.is_pinned() else _abi.TC_OP_EVOLVE_HOST
+    need = workspace_size(n, prec, op, steps)
     if work is None or work.numel() < need:
         work = _work(need, U.device)
     p = params.c() if params is not None else None

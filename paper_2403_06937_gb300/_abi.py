@@ -22,6 +22,7 @@ TC_FP64, TC_BF16X3, TC_TF32, TC_TF32X3, TC_FP64_OZAKI = 0, 1, 2, 3, 4
 TC_COUPLING_BOSONIC, TC_COUPLING_QUBIT_PHOTON = 0, 1
 TC_OP_EXPM, TC_OP_EVOLVE, TC_OP_OBSERVABLES, TC_OP_BACKWARD, TC_OP_EVOLVE_HOST, TC_OP_EXPM_MODEL = 1, 2, 4, 8, 16, 32
 TC_OP_LINDBLAD = 64
+TC_OP_EVOLVE_HOST_PINNED = 128
 
 
 class TCError(RuntimeError):

@@ -106,6 +106,19 @@ size_t evolve_host_extra(int n, int steps) {
     return mat_bytes(n, 16) + round256((size_t)(steps + 1) * (2 * n + 5) * sizeof(double));
 }
 
+// True when tc_evolve_host with a page-locked rho_host runs without a device
+// copy of rho: a tensor-core form, at least one step, and the products cut in
+// row blocks in and row bands out (the SMs read and write the host rows)
+bool host_without_staging(int n, int steps, int precision) {
+    if (precision != TC_BF16X3 && precision != TC_TF32 && precision != TC_TF32X3) return false;
+    return steps >= 1 && lowp_host_chunks(n, precision) > 1 && lowp_host_bands(n, precision) > 1;
+}
+
+size_t evolve_host_pinned_extra(int n, int steps, int precision) {
+    const size_t rows = round256((size_t)(steps + 1) * (2 * n + 5) * sizeof(double));
+    return host_without_staging(n, steps, precision) ? rows + 256 : evolve_host_extra(n, steps);
+}
+
 // ------------------------------------------------------------------ expm plan
 // Real GEMMs to evaluate a degree-d polynomial in Y by Horner in Y^q blocks
 // (Paterson-Stockmeyer), given Y^1..Y^q.
@@ -356,6 +369,7 @@ TC_API size_t tc_workspace_size(int n, int precision, int ops, int steps, int ck
     if (ops & TC_OP_EXPM_MODEL) upd(expm_model_bytes(n));
     if (ops & TC_OP_LINDBLAD) upd(lindblad_bytes(n, precision));
     if (ops & TC_OP_EVOLVE_HOST) upd(evolve_bytes(n, precision) + evolve_host_extra(n, steps));
+    if (ops & TC_OP_EVOLVE_HOST_PINNED) upd(evolve_bytes(n, precision) + evolve_host_pinned_extra(n, steps, precision));
     if (ops & TC_OP_BACKWARD) upd(backward_bytes(n, steps, ckpt_every, precision));
     return need;
 }
@@ -450,12 +464,18 @@ TC_API tc_status tc_evolve_host(const void* U, void* rho_host, int n, int steps,
         if (m.n != n) return fail(TC_ERR_INVALID_ARG, "params->n != n");
         mp = &m;
     }
-    TC_TRY(check_work(work, work_bytes, evolve_bytes(n, precision) + evolve_host_extra(n, steps)));
     TC_TRY(check_device());
+    // a page-locked rho_host in the pipelined tensor-core forms needs no device copy of rho
+    const void* mapped_rho = nullptr;
+    TC_TRY(host_mapping(rho_host, &mapped_rho));
+    const bool no_staging = mapped_rho && host_without_staging(n, steps, precision);
+    TC_TRY(check_work(work, work_bytes,
+                      evolve_bytes(n, precision) +
+                          (no_staging ? evolve_host_pinned_extra(n, steps, precision) : evolve_host_extra(n, steps))));
     cudaStream_t s = as_stream(stream);
     const size_t N = (size_t)1 << n;
     Arena ar{static_cast<char*>(work), work_bytes, 0};
-    double* rho_dev = ar.take<double>(2 * N * N);
+    double* rho_dev = no_staging ? nullptr : ar.take<double>(2 * N * N);
     double* obs_dev = ar.take<double>((size_t)(steps + 1) * (2 * n + 5));
     double* od = obs_host ? obs_dev : nullptr;
     const double* Ud = static_cast<const double*>(U);

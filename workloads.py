@@ -72,6 +72,13 @@ def config_n15() -> TCConfig:
                     description="n=15, dim 32768, g~U[0.005,0.015] seed 0, detuning 0.002, dt=0.05, renorm every 50")
 
 
+def config_n16() -> TCConfig:
+    """n = 16, dim 65536 (64 GiB per complex128 matrix): g seed 0, split-BF16 through the host-buffer call."""
+    return TCConfig("n16_precision", 16, draw_couplings(16, 0), 1.002, 1.0, 0.05, 500,
+                    renorm_every=50,
+                    description="n=16, dim 65536, g~U[0.005,0.015] seed 0, detuning 0.002, dt=0.05, renorm every 50")
+
+
 def config_open(n: int = 14, kappa: float = 0.02) -> TCConfig:
     """Open system (photon leakage at rate kappa): g seed 0, detuning 0.002, dt = 0.05, renorm every 50."""
     return TCConfig("open%d" % n, n, draw_couplings(n, 0), 1.002, 1.0, 0.05, 500, renorm_every=50,
