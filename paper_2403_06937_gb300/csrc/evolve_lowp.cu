@@ -585,6 +585,8 @@ tc_status evolve_lowp_host_blocks(const double* U, double* rho_host, double* rho
     StepPlan sp{};
     TC_TRY(plan_step(n, precision, b, sp));
     const int T = b.Np / 128;
+    // executed FLOPs of one 128 x 128 complex output tile (K = Np, every part product)
+    const double tile_flops = 8.0 * 128.0 * 128.0 * (double)b.Np * (double)cgemm_products(precision);
     const size_t R = N / C;                  // rows per block in
     const size_t chunk = 16 * R * N;         // bytes per block in
     const size_t RY = N / CY;                // rows per band out
@@ -638,7 +640,10 @@ tc_status evolve_lowp_host_blocks(const double* U, double* rho_host, double* rho
         CgemmEpi e = sp.e1;
         e.lo = c * T / C;
         e.hi = (c + 1) * T / C;
-        TC_TRY(cgemm_tc(precision, 0, sp.tmU, sp.tmR, e, s, sp.tune.tc_stages, &sp.wU, &sp.wR));
+        {
+            ProductTimer t(tile_flops * (double)T * (e.hi - e.lo), s);
+            TC_TRY(cgemm_tc(precision, 0, sp.tmU, sp.tmR, e, s, sp.tune.tc_stages, &sp.wU, &sp.wR));
+        }
         mark("x", c, s);
     }
     // rho' out once its entries are final (their products done on s).  A
@@ -674,10 +679,16 @@ tc_status evolve_lowp_host_blocks(const double* U, double* rho_host, double* rho
     };
     if (obs) TC_TRY(launch_observables(kRhoPlanarF32, b.Rr, b.Ri, m, n, obs, b.scratch, s, (size_t)b.Np));
     for (int k = 1; k <= steps; k++) {
-        if (k > 1) TC_TRY(cgemm_tc(precision, 0, sp.tmU, sp.tmR, sp.e1, s, sp.tune.tc_stages, &sp.wU, &sp.wR));
+        if (k > 1) {
+            ProductTimer t(tile_flops * (double)T * T, s);
+            TC_TRY(cgemm_tc(precision, 0, sp.tmU, sp.tmR, sp.e1, s, sp.tune.tc_stages, &sp.wU, &sp.wR));
+        }
         const bool renorm = renorm_every > 0 && k % renorm_every == 0;
         if (k < steps || renorm) {
-            TC_TRY(cgemm_tc(precision, 1, sp.tmU, sp.tmX, sp.e2, s, sp.tune.tc_stages, &sp.wU, &sp.wX));
+            {
+                ProductTimer t(tile_flops * 0.5 * T * (T + 1.0), s);
+                TC_TRY(cgemm_tc(precision, 1, sp.tmU, sp.tmX, sp.e2, s, sp.tune.tc_stages, &sp.wU, &sp.wX));
+            }
             if (renorm) TC_TRY(lowp_renorm(precision, b, s));
             if (obs) TC_TRY(launch_observables(kRhoPlanarF32, b.Rr, b.Ri, m, n, obs + (size_t)k * stride, b.scratch,
                                                s, (size_t)b.Np));
@@ -693,7 +704,11 @@ tc_status evolve_lowp_host_blocks(const double* U, double* rho_host, double* rho
             CgemmEpi e = sp.e2;
             e.lo = c * T / CY;
             e.hi = (c + 1) * T / CY;
-            TC_TRY(cgemm_tc(precision, 1, sp.tmU, sp.tmX, e, s, sp.tune.tc_stages, &sp.wU, &sp.wX));
+            {
+                // the block-lower tiles of rows [lo, hi)
+                ProductTimer t(tile_flops * 0.5 * ((double)e.hi * (e.hi + 1) - (double)e.lo * (e.lo + 1)), s);
+                TC_TRY(cgemm_tc(precision, 1, sp.tmU, sp.tmX, e, s, sp.tune.tc_stages, &sp.wU, &sp.wX));
+            }
             mark("y", c, s);
             TC_TRY(out_rows(c));
         }
