@@ -55,6 +55,26 @@ def test_version_and_workspace_sizes(lib):
     assert both == max(ev, ex)
 
 
+def test_pinned_host_workspace_skips_the_device_copy_of_rho(lib):
+    """TC_OP_EVOLVE_HOST_PINNED: in the pipelined split forms (N >= 2048, a
+    step or more) the host-buffer call on page-locked memory keeps no device
+    copy of rho (16 N^2 bytes less); elsewhere it sizes the staging as
+    TC_OP_EVOLVE_HOST does.  At n = 16 that is what fits beside U in HBM."""
+    from paper_2403_06937_gb300 import _abi
+    host, pinned = _abi.TC_OP_EVOLVE_HOST, _abi.TC_OP_EVOLVE_HOST_PINNED
+    for n in (11, 12, 14, 16):
+        for prec in (_abi.TC_BF16X3, _abi.TC_TF32, _abi.TC_TF32X3):
+            full = lib.tc_workspace_size(n, prec, host, 2, 0)
+            lean = lib.tc_workspace_size(n, prec, pinned, 2, 0)
+            assert full - lean >= 16 * (1 << n) ** 2 - 256, (n, prec)
+            assert lean >= lib.tc_workspace_size(n, prec, _abi.TC_OP_EVOLVE, 0, 0)
+    for n, prec, steps in ((10, _abi.TC_BF16X3, 2), (12, _abi.TC_FP64, 2), (12, _abi.TC_FP64_OZAKI, 2),
+                           (12, _abi.TC_BF16X3, 0)):
+        assert lib.tc_workspace_size(n, prec, pinned, steps, 0) == lib.tc_workspace_size(n, prec, host, steps, 0)
+    # n = 16, split-BF16: U (64 GiB) and the lean workspace stay below 290 GB
+    assert 16 * (1 << 16) ** 2 + lib.tc_workspace_size(16, _abi.TC_BF16X3, pinned, 2, 0) < 290e9
+
+
 def test_invalid_arguments_are_rejected_before_any_launch(lib):
     from paper_2403_06937_gb300 import _abi
     p = _abi.make_params(0, [], 1.0, 1.0)
