@@ -71,8 +71,11 @@ def test_pinned_host_workspace_skips_the_device_copy_of_rho(lib):
     for n, prec, steps in ((10, _abi.TC_BF16X3, 2), (12, _abi.TC_FP64, 2), (12, _abi.TC_FP64_OZAKI, 2),
                            (12, _abi.TC_BF16X3, 0)):
         assert lib.tc_workspace_size(n, prec, pinned, steps, 0) == lib.tc_workspace_size(n, prec, host, steps, 0)
-    # n = 16, split-BF16: U (64 GiB) and the lean workspace stay below 290 GB
-    assert 16 * (1 << 16) ** 2 + lib.tc_workspace_size(16, _abi.TC_BF16X3, pinned, 2, 0) < 290e9
+    # n = 16, split-BF16: U (64 GiB) and the lean workspace stay below the 298 GB of HBM (284,208 MiB)
+    # less the context, where the full host-buffer workspace does not
+    U16 = 16 * (1 << 16) ** 2
+    assert U16 + lib.tc_workspace_size(16, _abi.TC_BF16X3, pinned, 2, 0) < 296e9
+    assert U16 + lib.tc_workspace_size(16, _abi.TC_BF16X3, host, 2, 0) > 298e9
 
 
 def test_invalid_arguments_are_rejected_before_any_launch(lib):
