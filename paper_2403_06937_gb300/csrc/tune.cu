@@ -396,7 +396,8 @@ TC_API tc_status tc_autotune(int n, int precision, void* work, size_t work_bytes
         e2.yr = b.Rr;
         e2.yi = b.Ri;
         // one whole step (both launches) per configuration: single CTAs with either ring depth, then the
-        // CTA-pair shapes (their ring depth is fixed by the shared memory); pairs need an even tile count
+        // CTA-pair shapes (their ring depth is fixed by the shared memory); the single-system pair kernel
+        // needs an even tile count
         struct Cand {
             int shape, stages, group;
             double ms;
