@@ -377,18 +377,20 @@ TC_API tc_status tc_evolve_backward(const tc_params* params, double dt, int step
  * its device mapping, at full link rate also when the host is busy
  * (copy-engine transfers of host memory, reads above all, were measured to
  * slow down many-fold after heavy host CPU or memory activity); a pageable
- * one is copied by the copy engine through a device staging buffer.  In the tensor-core forms
- * with N >= 2048 the transfers overlap the products: rho moves in and out
- * in 2 or 4 row blocks on an internal stream, the first product of step 1
- * runs by column blocks as their rows arrive, and the second product of the
- * last step runs bottom-up by row blocks, each finished block converted and
- * written out while the rows above are computed; the results are the same
- * bits as tc_evolve's.
+ * one is copied by the copy engine through a device staging buffer.  In the
+ * tensor-core forms with N >= 2048 the transfers overlap the products: rho
+ * comes in by 2 or 4 row blocks on an internal stream while the first product
+ * of step 1 runs by column blocks as their rows arrive, and the second
+ * product of the last step runs bottom-up by 2 to 8 row bands, the entries
+ * each band makes final converted and written out while the rows above are
+ * computed; a page-locked rho then needs no device copy at all
+ * (TC_OP_EVOLVE_HOST_PINNED).  The results are the same bits as tc_evolve's.
  *  U        : device, N*N c128 (as tc_evolve), 16-byte aligned.
  *  rho_host : host, N*N c128, in/out.
  *  obs_host : host, (steps + 1) * TC_OBS_STRIDE(n) doubles, or NULL.
  *  work     : device, >= tc_workspace_size(n, precision, TC_OP_EVOLVE_HOST,
- *             steps, 0) bytes (includes the device copies of rho and obs).
+ *             steps, 0) bytes (includes the device copies of rho and obs);
+ *             for a page-locked rho_host TC_OP_EVOLVE_HOST_PINNED suffices.
  *  Errors: as tc_evolve. */
 TC_API tc_status tc_evolve_host(const void* U, void* rho_host, int n, int steps, int precision,
                                 int renorm_every, const tc_params* params, double* obs_host,
