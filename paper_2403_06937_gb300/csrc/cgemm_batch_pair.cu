@@ -16,8 +16,9 @@
 // for RB bytes of K per row; the even CTA arms its full barrier for both
 // CTAs' bytes and the odd CTA's copies (cta_group::2) complete on it; the
 // even CTA's MMA thread issues the part products as M = 256 pair MMAs into
-// both CTAs' TMEM and commits each stage back to both CTAs.  Nothing is
-// multicast.  TMEM (two 128 x 256 FP32 accumulators per CTA) holds one unit:
+// both CTAs' TMEM and commits each stage back to both CTAs.  Each CTA's
+// copies land in its own shared memory only.  TMEM (two 128 x 256 FP32
+// accumulators per CTA) holds one unit:
 // after each unit both epilogues read their own tile and arrive on the even
 // CTA's tmem_empty (count 2) before the next unit's MMAs start; the TMA ring
 // runs on across units.  Each output element is accumulated in the order of

@@ -339,7 +339,8 @@ constexpr int kSmem = kStages * kStage + 1024 /*align*/ + 256 /*barriers*/;
 // the row tiles I = 2p and 2p + 1 of one column tile J.  Each loads into its
 // own shared memory the slice-t panels of its own U_r and U_i rows and one
 // half of the B stack: P_r slice u in the even CTA, P_i slice u in the odd
-// one (12 KB a stage, no operand is loaded twice and nothing is multicast).
+// one (12 KB a stage; no operand is loaded twice, and each CTA's copies land
+// in its own shared memory only).
 // The even CTA's MMA thread issues M = 256 pair MMAs (its A rows and the odd
 // CTA's, B from both halves) into both CTAs' TMEM, so each CTA's tensor core
 // reads 8 KB of shared memory per MMA instead of 12.  Coordination:

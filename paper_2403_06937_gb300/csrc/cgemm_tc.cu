@@ -210,8 +210,9 @@ tc_status launch(const CUtensorMap& tmU, const CUtensorMap& tmP, const CgemmEpi&
 // of each stage for both CTAs' bytes; the odd CTA's copies (cta_group::2
 // copies) complete their bytes on it.  The even CTA's MMA thread issues
 // M = 256 pair MMAs into both CTAs' TMEM; the MMA completions release the
-// stages of both CTAs (commits to each CTA's barrier by address).  Nothing
-// is multicast.  Each CTA's epilogue writes its own tile exactly as the
+// stages of both CTAs (commits to each CTA's barrier by address).  Each
+// CTA's copies land in its own shared memory only.  Each CTA's epilogue
+// writes its own tile exactly as the
 // single-CTA kernel does; in the Hermitian launch the tile (2p, 2p + 1)
 // above the diagonal is computed and not written (its lower partner writes
 // both).  Every wait is bounded; a timeout raises the abort flag of both
