@@ -329,7 +329,8 @@ TC_API tc_status tc_lindblad_propagators(const tc_params* params, double dt, voi
  * same dt.  Second order in dt; kappa = 0 is the closed evolution of Eq. 6.
  * The block products run on the DMMA GEMM (TC_FP64) or on the tcgen05
  * tensor cores (split forms, as tc_evolve: one persistent launch over the
- * tiles of every block per product, rho stored FP32 between steps).
+ * tiles of every block per product, CTA pairs by default, rho stored FP32
+ * between steps; FP64 emulated: the blocks one after another on CTA pairs).
  *  U, rho      : device packed complex128; rho in/out (Hermitian blocks).
  *  precision   : TC_FP64, TC_BF16X3, TC_TF32, TC_TF32X3, TC_FP64_OZAKI.
  *  renorm_every: 0 = never; else after every renorm_every-th step all
@@ -400,8 +401,8 @@ TC_API tc_status tc_evolve_host(const void* U, void* rho_host, int n, int steps,
 
 /* tc_autotune -- time every built configuration of the step products for n
  * atoms at `precision` on synthetic operands in `work` and keep the fastest
- * for later calls in this process (tc_evolve, tc_expm, tc_evolve_backward,
- * tc_batch_evolve, tc_evolve_open):
+ * for later calls in this process (tc_evolve, tc_evolve_host, tc_expm,
+ * tc_evolve_backward, tc_batch_evolve, tc_lindblad_evolve):
  *   FP64: the DMMA GEMM tile, 32 x 32 or 64 x 64 (timed on a K slice);
  *   tensor cores: the tile shape (1: one CTA per 128 x 128 complex tile;
  *   2: CTA pairs on the 2-SM MMA, a 256 x 128 tile per pair, 32 bytes of K
