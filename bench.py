@@ -3,7 +3,8 @@
 system (arXiv 2403.06937, Eq. 6) on one GB300, through libtc's C ABI.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--precision bf16x3|tf32x3|tf32|fp64] [--workload n14|n15|n12|n8|batch|grad]
+                    [--precision bf16x3|tf32x3|tf32|fp64|ozaki]
+                    [--workload n14|n15|n16|n12|n8|batch|grad|open14|open12]
 
 One "step" is one pass of the step loop: X = U rho, rho' = X U^dag (Hermitian
 half) and the observable row (populations, photon-number probabilities,
@@ -17,6 +18,12 @@ value = all ranks' steps / max-over-ranks time.
 --impl reference times the CPU oracle (test infrastructure, plain C) on the
 host cores for the same workload, on a bounded sample of rows of the dense
 step, extrapolated to steps/s.
+
+Every line states its error against the oracle (the O-psi trajectory of the
+workload; for the batch, every system's; for the gradient, the oracle's
+forward-mode tangent and central differences).  n16 runs through the
+host-buffer call with rho in page-locked host memory (U and the workspace
+fill HBM), so its value is an end-to-end figure.
 """
 from __future__ import annotations
 
